@@ -1,0 +1,414 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test checks an oracle function against one of: a closed form, brute force
+on tiny inputs in pure Python integers, a big-integer CRT identity, a library
+routine (sympy), or a decryption-error bound.  Together they are meant to fail
+on a dropped term, a wrong sign or index, or a transposed operand anywhere in
+``oracle/``.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from oracle.client import Client
+
+sympy = pytest.importorskip("sympy")
+
+
+def brv(x, bits):
+    return int(format(x, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+def make_ctx(logN, nq, q_bits, nk, p_bits, dnum):
+    q = oracle.find_primes(logN, q_bits, nq)
+    p = oracle.find_primes(logN, p_bits, nk, exclude=q)
+    return oracle.Context(logN, q, p, dnum)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    # N = 16, four 30-bit q, two 40-bit p, dnum = 2 (alpha = 2)
+    return make_ctx(4, 4, 30, 2, 40, 2)
+
+
+@pytest.fixture(scope="module")
+def small():
+    P = si.SMALL
+    return make_ctx(P.logN, P.nq, P.q_bits, P.nk, P.p_bits, P.dnum)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    P = si.MID
+    return make_ctx(P.logN, P.nq, P.q_bits, P.nk, P.p_bits, P.dnum)
+
+
+# ---------------------------------------------------------------- modmul
+def test_mul_mod_edges_and_random():
+    rng = random.Random(1)
+    for q in [3, 97, (1 << 40) - 87, 1152921504606830593, (1 << 61) - 1]:
+        vals = [0, 1, q - 1, q - 2, q // 2, 2 * q - 1 if 2 * q - 1 < 2**64 else q]
+        for a in vals:
+            for b in vals:
+                assert oracle.mul_mod(a, b, q) == (a * b) % q
+        for _ in range(2000):
+            a, b = rng.randrange(2**64), rng.randrange(2**64)
+            assert oracle.mul_mod(a, b, q) == (a * b) % q
+
+
+# ---------------------------------------------------------------- primes
+def test_is_prime_matches_sympy():
+    rng = random.Random(2)
+    cands = [561, 1105, 1729, 2465, 2821, 6601, 3215031751, 2**61 - 1, 2**64 - 59, 2**62 + 1]
+    cands += [rng.randrange(2**64) | 1 for _ in range(300)]
+    for n in cands:
+        assert oracle.is_prime(n) == sympy.isprime(n), n
+
+
+@pytest.mark.parametrize("logN,bits,count", [(12, 40, 3), (12, 50, 1), (16, 54, 30), (16, 60, 10)])
+def test_find_primes_is_the_downward_walk(logN, bits, count):
+    ps = oracle.find_primes(logN, bits, count)
+    step = 2 << logN
+    # brute force: every candidate of the form k*2N+1 below 2^bits, descending
+    want, q = [], (1 << bits) - step + 1
+    while len(want) < count:
+        if sympy.isprime(q):
+            want.append(q)
+        q -= step
+    assert ps == want
+    for q in ps:
+        assert q % step == 1 and q.bit_length() == bits
+
+
+def test_smallest_generator_matches_sympy():
+    for q in [97, 257, 7681, 12289] + oracle.find_primes(12, 40, 2) + oracle.find_primes(16, 54, 2):
+        assert oracle.smallest_generator(q) == sympy.primitive_root(q)
+
+
+def test_psi_is_primitive_2n_root(small, mid):
+    for ctx in (small, mid):
+        for i, q in enumerate(ctx.primes):
+            psi = ctx.psi(i)
+            g = sympy.primitive_root(q)
+            assert psi == pow(g, (q - 1) // (2 * ctx.N), q)
+            assert pow(psi, ctx.N, q) == q - 1
+
+
+# ---------------------------------------------------------------- NTT
+def _eval_at(a, x, q):
+    acc = 0
+    for c in reversed(a):
+        acc = (acc * x + c) % q
+    return acc
+
+
+def test_ntt_is_evaluation_at_odd_roots(tiny):
+    """NTT slot j = a(psi^(2 brv(j)+1)) (bit-reversed order), by Horner."""
+    rng = random.Random(3)
+    N, bits = tiny.N, tiny.logN
+    for i, q in enumerate(tiny.primes):
+        a = [rng.randrange(q) for _ in range(N)]
+        psi = tiny.psi(i)
+        want = [_eval_at(a, pow(psi, 2 * brv(j, bits) + 1, q), q) for j in range(N)]
+        assert tiny.ntt_naive(np.array(a, dtype=np.uint64), i).tolist() == want
+        assert tiny.ntt(np.array(a, dtype=np.uint64), i).tolist() == want
+
+
+@pytest.mark.parametrize("logN", [6, 8, 10])
+def test_radix2_ntt_matches_definition(logN):
+    ctx = make_ctx(logN, 2, 50, 1, 59, 1)
+    st = si.Stream(5, logN)
+    for i, q in enumerate(ctx.primes):
+        a = st.uniform_mod(q, ctx.N)
+        A = ctx.ntt_naive(a, i)
+        assert np.array_equal(ctx.ntt(a, i), A)
+        assert np.array_equal(ctx.intt_naive(A, i), a)
+        assert np.array_equal(ctx.intt(A, i), a)
+
+
+def _negacyclic(a, b, q):
+    N = len(a)
+    c = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                c[k] += a[i] * b[j]
+            else:
+                c[k - N] -= a[i] * b[j]
+    return [x % q for x in c]
+
+
+@pytest.mark.parametrize("logN", [4, 6])
+def test_convolution_theorem(logN):
+    """INTT(NTT(a) . NTT(b)) equals the schoolbook product mod X^N + 1."""
+    ctx = make_ctx(logN, 2, 40, 1, 50, 1)
+    st = si.Stream(7, logN)
+    for i, q in enumerate(ctx.primes):
+        a, b = st.uniform_mod(q, ctx.N), st.uniform_mod(q, ctx.N)
+        A, B = ctx.ntt(a, i), ctx.ntt(b, i)
+        C = np.array([(int(x) * int(y)) % q for x, y in zip(A, B)], dtype=np.uint64)
+        assert ctx.intt(C, i).tolist() == _negacyclic(a.tolist(), b.tolist(), q)
+
+
+def test_ntt_special_inputs(small):
+    N = small.N
+    for i, q in enumerate(small.primes):
+        one = np.zeros(N, dtype=np.uint64); one[0] = 1
+        assert np.all(small.ntt(one, i) == 1)
+        x = np.zeros(N, dtype=np.uint64); x[1] = 1
+        psi = small.psi(i)
+        want = [pow(psi, 2 * brv(j, small.logN) + 1, q) for j in range(N)]
+        assert small.ntt(x, i).tolist() == want
+        # inverse at full size is an identity on random data
+        a = si.Stream(9, i).uniform_mod(q, N)
+        assert np.array_equal(small.intt(small.ntt(a, i), i), a)
+
+
+# ---------------------------------------------------------------- base conversion
+def _crt_int(res, primes):
+    return oracle.crt(np.asarray(res, dtype=np.uint64).reshape(len(primes), -1), primes)
+
+
+def test_bconv_is_x_plus_u_Q(mid):
+    """y_p = x + u Q_src (mod p) with one integer 0 <= u < |src| for all p."""
+    st = si.Stream(11)
+    src = [0, 1, 2, 3]
+    dst = list(range(4, len(mid.primes)))
+    x = si.uniform_poly(st, [mid.primes[i] for i in src], mid.N)
+    y = mid.bconv(x, src, dst)
+    sp = [mid.primes[i] for i in src]
+    Qs = 1
+    for q in sp:
+        Qs *= q
+    X = oracle.crt(x, sp)
+    for n in range(0, mid.N, 97):
+        us = set()
+        for k, di in enumerate(dst):
+            p = mid.primes[di]
+            # find u in [0, |src|) with X + u Qs = y (mod p)
+            cand = [u for u in range(len(src)) if (X[n] + u * Qs - int(y[k, n])) % p == 0]
+            assert len(cand) == 1
+            us.add(cand[0])
+        assert len(us) == 1
+
+
+def _coeff(ctx, x, pidx):
+    return ctx.intt_limbs(x, pidx)
+
+
+def test_modup_digits(mid):
+    nl = 11                                 # ragged: digits of 4, 4 and 3 limbs
+    st = si.Stream(12)
+    d = si.uniform_poly(st, mid.q[:nl], mid.N)
+    ext = mid.modup(d)
+    alpha = mid.alpha
+    assert alpha == 4 and ext.shape == (3, nl + mid.nk, mid.N)
+    dc = _coeff(mid, d, list(range(nl)))
+    ep = list(range(nl)) + [mid.nq + k for k in range(mid.nk)]
+    for j in range(3):
+        lo, hi = j * alpha, min((j + 1) * alpha, nl)
+        assert np.array_equal(ext[j, lo:hi], d[lo:hi])      # digit limbs copied
+        ec = _coeff(mid, ext[j], ep)
+        sp = mid.q[lo:hi]
+        Qj = 1
+        for q in sp:
+            Qj *= q
+        X = oracle.crt(dc[lo:hi], sp)
+        for n in range(0, mid.N, 131):
+            for z in range(nl + mid.nk):
+                if lo <= z < hi:
+                    continue
+                p = mid.primes[ep[z]]
+                assert any((X[n] + u * Qj - int(ec[z, n])) % p == 0 for u in range(hi - lo))
+
+
+def test_moddown_is_floor_division_by_P(mid):
+    nl = 7
+    st = si.Stream(13)
+    ep = list(range(nl)) + [mid.nq + k for k in range(mid.nk)]
+    x = si.uniform_poly(st, [mid.primes[i] for i in ep], mid.N)
+    out = mid.moddown(x)
+    xc = _coeff(mid, x, ep)
+    oc = _coeff(mid, out, list(range(nl)))
+    Ql, P = 1, 1
+    for q in mid.q[:nl]:
+        Ql *= q
+    for p in mid.p:
+        P *= p
+    X = oracle.crt(xc, mid.q[:nl] + mid.p)
+    xP = oracle.crt(xc[nl:], mid.p)
+    O = oracle.crt(oc, mid.q[:nl])
+    for n in range(mid.N):
+        assert (X[n] - xP[n]) % P == 0
+        u = ((X[n] - xP[n]) // P - O[n]) % Ql
+        assert 0 <= u < mid.nk
+
+
+def test_rescale_is_exact_floor(mid):
+    nl = 9
+    st = si.Stream(14)
+    a = np.stack([si.uniform_poly(st, mid.q[:nl], mid.N) for _ in range(2)])
+    out = mid.rescale(a)
+    ql = mid.q[nl - 1]
+    for poly in range(2):
+        X = oracle.crt(_coeff(mid, a[poly], list(range(nl))), mid.q[:nl])
+        O = oracle.crt(_coeff(mid, out[poly], list(range(nl - 1))), mid.q[:nl - 1])
+        assert O == [x // ql for x in X]
+
+
+# ---------------------------------------------------------------- automorphism
+def test_automorphism_coeff_is_substitution(tiny):
+    N = tiny.N
+    st = si.Stream(15)
+    a = si.uniform_poly(st, tiny.q, N)
+    for steps in [1, 2, 3, -1]:
+        g = tiny.galois_elt(steps)
+        assert g == pow(5, steps % (N // 2), 2 * N)
+        out = tiny.automorph_coeff(a, g)
+        for z, q in enumerate(tiny.q):
+            want = [0] * N
+            for i in range(N):
+                e = (i * g) % (2 * N)
+                if e < N:
+                    want[e] = (want[e] + int(a[z, i])) % q
+                else:
+                    want[e - N] = (want[e - N] - int(a[z, i])) % q
+            assert out[z].tolist() == want
+
+
+def test_automorphism_eval_matches_coeff(small):
+    st = si.Stream(16)
+    a = si.uniform_poly(st, small.q, small.N)
+    idx = list(range(small.nq))
+    A = small.ntt_limbs(a, idx)
+    for steps in [1, 5, 1000, -3]:
+        g = small.galois_elt(steps)
+        assert np.array_equal(small.automorph_eval(A, g), small.ntt_limbs(small.automorph_coeff(a, g), idx))
+    assert small.galois_elt(small.N // 2) == 1
+
+
+# ---------------------------------------------------------------- encoding
+def test_encode_fft_matches_direct_and_roundtrips():
+    N = 256
+    z = si.Stream(17).complex_slots(N // 2)
+    m = oracle.encode(z, N, 2.0**40)
+    assert np.array_equal(m, oracle.encode_direct(z, N, 2.0**40))
+    assert np.max(np.abs(oracle.decode(m, N, 2.0**40) - z)) < 2.0**-30
+    assert np.max(np.abs(oracle.decode(m, N, 2.0**40) - oracle.decode_direct(m, N, 2.0**40))) < 2.0**-40
+
+
+def test_encode_is_multiplicative_and_rotates():
+    N = 64
+    st = si.Stream(18)
+    z1, z2 = st.complex_slots(N // 2), st.complex_slots(N // 2)
+    m1, m2 = oracle.encode(z1, N, 2.0**30), oracle.encode(z2, N, 2.0**30)
+    prod = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                prod[k] += int(m1[i]) * int(m2[j])
+            else:
+                prod[k - N] -= int(m1[i]) * int(m2[j])
+    assert np.max(np.abs(oracle.decode(prod, N, 2.0**60) - z1 * z2)) < 2.0**-20
+    # m(X^5) holds the slots rotated left by one
+    rot = [0] * N
+    for i in range(N):
+        e = (5 * i) % (2 * N)
+        if e < N:
+            rot[e] += int(m1[i])
+        else:
+            rot[e - N] -= int(m1[i])
+    assert np.max(np.abs(oracle.decode(rot, N, 2.0**30) - np.roll(z1, -1))) < 2.0**-20
+
+
+# ---------------------------------------------------------------- scheme level
+def _rel_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(1.0, np.max(np.abs(ref))))
+
+
+@pytest.fixture(scope="module")
+def small_client(small):
+    return Client(small, seed=si.workload_seed(0))
+
+
+def test_encrypt_decrypt_roundtrip(small, small_client):
+    z = small_client.random_slots()
+    ct = small_client.encrypt(z, small.nq, 2.0**40)
+    assert _rel_err(small_client.decrypt(ct, 2.0**40), z) < 2.0**-25
+
+
+def test_keyswitch_noise_bound(small, small_client):
+    """decrypt(KeySwitch(d)) - d s' is small: bounded by
+    K (1 + ||s||_1) + N alpha B_e max_j Q_j / P (B_e = 6 sigma, rounded up)."""
+    c = small
+    rk = small_client.rotation_key(1)
+    g = c.galois_elt(1)
+    sp = c.automorph_eval(small_client.s_eval, g)
+    nl = c.nq
+    d = si.uniform_poly(si.Stream(19), c.q[:nl], c.N)
+    ks0, ks1 = c.keyswitch(d, rk)
+    # ks0 + ks1 s - d s' in coefficient form, centred
+    idx = list(range(nl))
+    lhs = np.stack([ks0, ks1])
+    dec = oracle.crt(small_client.ctx.decrypt_residues(lhs, small_client.s_eval[:nl]), c.q[:nl])
+    dsp = oracle.crt(c.intt_limbs(c.pointwise_mul(d, sp[:nl], idx), idx), c.q[:nl])
+    Q = 1
+    for q in c.q[:nl]:
+        Q *= q
+    diff = oracle.centered([(a - b) % Q for a, b in zip(dec, dsp)], Q)
+    P = 1
+    for p in c.p:
+        P *= p
+    Qj = max(c.q[j * c.alpha] for j in range(c.beta(nl)))   # alpha = 1 here
+    s1 = int(np.sum(np.abs(small_client.s_coeff)))
+    bound = c.nk * (1 + s1) + c.N * c.alpha * 20 * Qj // P + 1
+    worst = max(abs(x) for x in diff)
+    assert worst <= bound, (worst, bound)
+
+
+def test_hmult_relin_decrypts_to_product(small, small_client):
+    z1, z2 = small_client.random_slots(), small_client.random_slots()
+    a = small_client.encrypt(z1, small.nq, 2.0**40)
+    b = small_client.encrypt(z2, small.nq, 2.0**40)
+    rlk = small_client.relin_key()
+    out = small.hmult(a, b, rlk)
+    assert _rel_err(small_client.decrypt(out, 2.0**80), z1 * z2) < 2.0**-20
+    # and after Rescale by q_2 (scale 2^80 / q_2)
+    rs = small.rescale(out)
+    assert _rel_err(small_client.decrypt(rs, 2.0**80 / small.q[2]), z1 * z2) < 2.0**-20
+
+
+def test_hmult_relin_catches_a_wrong_key(small, small_client):
+    """A rotation key in place of the relinearisation key must not decrypt."""
+    z1, z2 = small_client.random_slots(), small_client.random_slots()
+    a = small_client.encrypt(z1, small.nq, 2.0**40)
+    b = small_client.encrypt(z2, small.nq, 2.0**40)
+    out = small.hmult(a, b, small_client.rotation_key(1))
+    assert _rel_err(small_client.decrypt(out, 2.0**80), z1 * z2) > 1.0
+
+
+def test_hrotate_decrypts_to_rotation(small, small_client):
+    z = small_client.random_slots()
+    ct = small_client.encrypt(z, small.nq, 2.0**40)
+    r1, r2, r3 = small_client.rotation_key(1), small_client.rotation_key(2), small_client.rotation_key(3)
+    o1 = small.rotate(ct, 1, r1)
+    assert _rel_err(small_client.decrypt(o1, 2.0**40), np.roll(z, -1)) < 2.0**-20
+    o12 = small.rotate(o1, 2, r2)
+    o3 = small.rotate(ct, 3, r3)
+    assert _rel_err(small_client.decrypt(o12, 2.0**40), small_client.decrypt(o3, 2.0**40)) < 2.0**-20
+    assert _rel_err(small_client.decrypt(o3, 2.0**40), np.roll(z, -3)) < 2.0**-20
+
+
+def test_lower_level_hmult(mid):
+    """Ragged digits: HMult at 5 of 12 limbs (digits of 4 and 1 limbs)."""
+    cl = Client(mid, seed=21)
+    z1, z2 = cl.random_slots(), cl.random_slots()
+    a = cl.encrypt(z1, 5, 2.0**40)
+    b = cl.encrypt(z2, 5, 2.0**40)
+    out = mid.hmult(a, b, cl.relin_key())
+    assert _rel_err(cl.decrypt(out, 2.0**80), z1 * z2) < 2.0**-20
