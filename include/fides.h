@@ -1,0 +1,169 @@
+/*
+ * fides.h -- C ABI of the GB300 CKKS key-switching engine.
+ *
+ * The engine implements the server-side hot path of CKKS described in
+ * "FIDESlib: A Fully-Fledged Open-Source FHE Library for Efficient CKKS on
+ * GPUs" (arXiv 2507.04775): the 64-bit negacyclic (i)NTT over RNS limbs
+ * (Sec. III-E4), fast base conversion (Sec. III-E3, Eq. 1), ModUp / ModDown,
+ * the key inner product and hybrid key switching (Sec. II), HMult with
+ * relinearisation, HRotate and Rescale (Table I; fusions of Sec. III-E5).
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ *  - Residues are uint64_t in canonical form [0, q).  Inputs outside [0, q)
+ *    give unspecified (but memory-safe) results.
+ *  - Polynomials are limb-major: limb z of an n-limb polynomial occupies
+ *    words [z*N, (z+1)*N).  Limb i of a ciphertext-level polynomial lives
+ *    modulo q_i.  An "extended" polynomial at nl limbs has nl + K limbs: q_0 ..
+ *    q_{nl-1} followed by the K special primes p_0 .. p_{K-1}.
+ *  - Evaluation ("NTT") form: word j of a limb holds a(psi^(2 brv(j) + 1)) mod
+ *    q, psi = g^((q-1)/2N) with g the smallest generator of Z_q^*; i.e. the
+ *    forward transform maps natural order to bit-reversed order (Sec. III-E4).
+ *  - A ciphertext is two polynomials (c0, c1) stored back to back:
+ *    [2][nl][N], evaluation form, decrypting to c0 + c1 s.
+ *  - A switching key is [dnum][2][L + K][N] (component 0 = b, 1 = a),
+ *    evaluation form, at the full level; at nl limbs the first nl q-limbs and
+ *    the K special limbs are read.  Digit j covers q-limbs [j*alpha,
+ *    min((j+1)*alpha, nl)), alpha = ceil(L / dnum).
+ *  - Pointers named dev_* are device pointers owned by the caller; they must be
+ *    8-byte aligned and must stay valid until the work queued on `stream`
+ *    completes.  Outputs may not alias inputs unless the entry point says so.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every compute
+ *    entry point is asynchronous with respect to the host.
+ *  - Calls on one context use the context's scratch memory and must not run
+ *    concurrently (issue them on one stream, or create one context per stream).
+ *  - Return value: FIDES_OK (0) or a negative FIDES_ERR_* code; the message of
+ *    the last error on the calling thread is available from fides_last_error().
+ *    Argument errors are detected before anything is queued.
+ */
+#ifndef FIDES_H
+#define FIDES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIDES_OK 0
+#define FIDES_ERR_ARG (-1)          /* bad argument (null pointer, size, level) */
+#define FIDES_ERR_UNSUPPORTED (-2)  /* parameter set outside what the kernels handle */
+#define FIDES_ERR_NOMEM (-3)        /* device or host allocation failed */
+#define FIDES_ERR_CUDA (-4)         /* a CUDA call failed */
+#define FIDES_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define FIDES_ERR_PRIME (-6)        /* a modulus is not an NTT-friendly prime */
+
+typedef struct fides_ctx fides_ctx;
+
+/* A ciphertext descriptor: `data` is a device buffer [2][n_limbs][N]. The
+ * scale is tracked on the host (Sec. II: scaling factors are tracked per
+ * level); the library updates it in outputs. */
+typedef struct {
+    uint64_t *data;
+    int n_limbs;
+    double scale;
+} fides_ct;
+
+/* Last error message of the calling thread ("" if none). */
+const char *fides_last_error(void);
+
+/* Library version string. */
+const char *fides_version(void);
+
+/*
+ * NTT-friendly primes (Table II: word-sized q_i ~ Delta): walks downward from
+ * 2^bits over q = 1 (mod 2N) and writes the first `count` primes that are not
+ * in exclude[0..n_exclude).  Host only.  bits in [logN + 2, 61].
+ */
+int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, int n_exclude,
+                      uint64_t *out);
+
+/*
+ * Creates a context on the current CUDA device (Sec. III-D "Precomputation":
+ * per-prime constants are computed once at context creation).
+ *   logN   : ring degree N = 2^logN; this build supports logN in {12, 16}.
+ *   L      : number of q-primes (maximum ciphertext limbs), 1 <= L.
+ *   K      : number of special primes, 1 <= K, L + K <= 64.
+ *   dnum   : number of key-switching digits, 1 <= dnum <= L.
+ *   primes : host array of L q-primes then K special primes, each prime,
+ *            = 1 mod 2N, < 2^61, all distinct.
+ * Owns device tables (twiddles with Shoup companions, base-conversion
+ * matrices) and a scratch pool sized for one operation at the top level.
+ */
+int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out);
+void fides_ctx_destroy(fides_ctx *ctx);
+
+/* Number of digits in use at n_limbs limbs: ceil(n_limbs / alpha). */
+int fides_ctx_beta(const fides_ctx *ctx, int n_limbs);
+/* psi of prime index i (0..L+K-1), or 0 for a bad index. */
+uint64_t fides_ctx_psi(const fides_ctx *ctx, int prime_index);
+/* Galois element of a left rotation by `steps` slots: 5^steps mod 2N. */
+uint64_t fides_galois_elt(const fides_ctx *ctx, int64_t steps);
+
+/*
+ * Forward / inverse negacyclic NTT (Sec. III-E4), in place, on `batch`
+ * polynomials of n_limbs limbs each stored back to back; limb z of every
+ * polynomial uses prime index first_prime + z.  Forward: natural order in,
+ * bit-reversed out.  Inverse: bit-reversed in, natural out, includes N^-1.
+ * first_prime + n_limbs <= L + K.
+ */
+int fides_ntt(fides_ctx *ctx, uint64_t *dev, int first_prime, int n_limbs, int batch, void *stream);
+int fides_intt(fides_ctx *ctx, uint64_t *dev, int first_prime, int n_limbs, int batch, void *stream);
+
+/*
+ * ModUp (Sec. III-E3; Sec. II hybrid key switching): dev_d is an n_limbs-limb
+ * polynomial in evaluation form.  For each digit D_j, the limbs of D_j are
+ * copied and every other prime of q_0..q_{n_limbs-1} and every special prime
+ * is filled by fast base conversion (Eq. 1) of D_j in coefficient form
+ * followed by an NTT.  dev_ext receives [beta][n_limbs + K][N].
+ */
+int fides_modup(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, uint64_t *dev_ext, void *stream);
+
+/*
+ * ModDown (Sec. III-E3, Sec. III-E5 "ModDown fusion"): dev_x is an extended
+ * polynomial [n_limbs + K][N] in evaluation form; dev_out [n_limbs][N]
+ * receives P^-1 (x_i - NTT(Conv_{P->Q}(INTT(x_P))))_i mod q_i (floor, no
+ * rounding offset).
+ */
+int fides_moddown(fides_ctx *ctx, const uint64_t *dev_x, int n_limbs, uint64_t *dev_out, void *stream);
+
+/*
+ * Hybrid key switching of one polynomial d (n_limbs limbs, evaluation form)
+ * with key dev_evk ([dnum][2][L+K][N]): ModUp, key inner product
+ * acc_t = sum_j d~_j evk_{j,t} (Sec. III-E5 "Dot product fusion"), ModDown of
+ * both accumulators.  Output (dev_out0, dev_out1), each [n_limbs][N], with
+ * out0 + out1 s ~= d s'.
+ */
+int fides_keyswitch(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, const uint64_t *dev_evk,
+                    uint64_t *dev_out0, uint64_t *dev_out1, void *stream);
+
+/*
+ * HMult with relinearisation (Table I): d0 = a0 b0, d1 = a0 b1 + a1 b0,
+ * d2 = a1 b1, out = (d0, d1) + KeySwitch(d2, rlk).  a, b and out have the
+ * same n_limbs; out->scale = a->scale * b->scale.  out may not alias a or b.
+ */
+int fides_hmult(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint64_t *dev_rlk,
+                fides_ct *out, void *stream);
+
+/*
+ * HRotate (Table I): rotation of the slots left by `steps` (g = 5^steps mod
+ * 2N); out = (sigma_g(c0) + ks0, ks1) with (ks0, ks1) = KeySwitch(sigma_g(c1),
+ * rk) and rk the switching key of s(X^g).  out may not alias a.
+ */
+int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_t *dev_rk,
+                 fides_ct *out, void *stream);
+
+/*
+ * Rescale (Table I, Sec. III-E5 "Rescale fusion"): drops the last limb q_l,
+ * l = a->n_limbs - 1 >= 1: out_i = q_l^-1 (x_i - NTT_{q_i}([INTT(x_l)]_{q_i}))
+ * mod q_i, which is floor(x / q_l) limb-wise.  out->n_limbs must equal
+ * a->n_limbs - 1; out->scale = a->scale / q_l.  out may not alias a.
+ */
+int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIDES_H */

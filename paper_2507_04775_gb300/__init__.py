@@ -1,0 +1,8 @@
+"""GB300-native CKKS hybrid key-switching engine (FIDESlib, arXiv 2507.04775).
+
+The compute path is the CUDA library ``_build/libfides.so`` (hand-written
+sm_103a kernels behind the C ABI of ``include/fides.h``); ``fides`` is its
+ctypes binding.  Build with ``paper_2507_04775_gb300.build.build()``.
+"""
+from .fides import (Context, FidesError, find_primes, lib, to_device, to_host, version, EXPORTS,  # noqa: F401
+                    LIB_PATH)

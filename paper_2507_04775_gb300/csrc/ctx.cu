@@ -1,0 +1,324 @@
+// Context creation: validates the primes, finds psi for each of them and
+// precomputes every per-prime table the kernels read (Sec. III-D
+// "Precomputation": constants are computed once, when the context is built).
+// Unlike the paper's singleton, every context owns its device tables, so
+// several parameter sets can live in one process.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fides_internal.cuh"
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// Error state (thread-local message of the last failure)
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+int fides_set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int fides_check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return FIDES_OK;
+    return fides_set_error(e == cudaErrorMemoryAllocation ? FIDES_ERR_NOMEM : FIDES_ERR_CUDA,
+                           "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *fides_last_error(void) { return g_err; }
+extern "C" const char *fides_version(void) { return "fides-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Host number theory (u128 products)
+// ---------------------------------------------------------------------------
+namespace {
+
+u64 hmul(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+
+u64 hpow(u64 a, u64 e, u64 q)
+{
+    u64 r = 1 % q;
+    a %= q;
+    for (; e; e >>= 1) {
+        if (e & 1) r = hmul(r, a, q);
+        a = hmul(a, a, q);
+    }
+    return r;
+}
+
+u64 hinv(u64 a, u64 q) { return hpow(a, q - 2, q); }
+
+// Shoup companion floor(w * 2^64 / q) for w < q
+u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+TwPair pair_of(u64 w, u64 q) { return TwPair{w % q, shoup_of(w % q, q)}; }
+
+// Miller-Rabin with the first twelve prime bases: exact below 3.3e24.
+bool is_prime(u64 n)
+{
+    static const u64 B[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 b : B)
+        if (n % b == 0) return n == b;
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) { d >>= 1; ++s; }
+    for (u64 b : B) {
+        u64 x = hpow(b, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int r = 1; r < s && composite; ++r) {
+            x = hmul(x, x, n);
+            if (x == n - 1) composite = false;
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+// smallest generator of Z_q^* (q prime): test g^((q-1)/f) != 1 for every
+// prime factor f of q - 1
+u64 smallest_generator(u64 q)
+{
+    std::vector<u64> f;
+    u64 n = q - 1;
+    for (u64 p = 2; p * p <= n; p = (p == 2 ? 3 : p + 2)) {
+        if (n % p == 0) {
+            f.push_back(p);
+            while (n % p == 0) n /= p;
+        }
+    }
+    if (n > 1) f.push_back(n);
+    for (u64 g = 2; g < q; ++g) {
+        bool ok = true;
+        for (u64 p : f)
+            if (hpow(g, (q - 1) / p, q) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
+    return 0;
+}
+
+u64 bitrev(u64 x, int bits)
+{
+    u64 r = 0;
+    for (int i = 0; i < bits; ++i) { r = (r << 1) | (x & 1); x >>= 1; }
+    return r;
+}
+
+template <class T>
+int upload(T **dptr, const std::vector<T> &h, const char *what)
+{
+    size_t bytes = sizeof(T) * (h.empty() ? 1 : h.size());
+    int rc = fides_check_cuda(cudaMalloc((void **)dptr, bytes), what);
+    if (rc) return rc;
+    if (!h.empty()) rc = fides_check_cuda(cudaMemcpy(*dptr, h.data(), bytes, cudaMemcpyHostToDevice), what);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, int n_exclude,
+                                 uint64_t *out)
+{
+    if (logN < 1 || logN > 20 || bits < logN + 2 || bits > 61 || count < 0 || (count && !out) ||
+        n_exclude < 0 || (n_exclude && !exclude))
+        return fides_set_error(FIDES_ERR_ARG, "fides_find_primes: bad arguments");
+    u64 step = (u64)2 << logN;
+    u64 q = ((u64)1 << bits) - step + 1;
+    int found = 0;
+    while (found < count && q > step) {
+        bool skip = false;
+        for (int i = 0; i < n_exclude; ++i) skip |= (exclude[i] == q);
+        if (!skip && is_prime(q)) out[found++] = q;
+        q -= step;
+    }
+    if (found < count) return fides_set_error(FIDES_ERR_PRIME, "fides_find_primes: only %d primes", found);
+    return FIDES_OK;
+}
+
+extern "C" void fides_ctx_destroy(fides_ctx *c)
+{
+    if (!c) return;
+    cudaFree(c->d_prime);
+    cudaFree(c->d_tw);
+    cudaFree(c->d_itw);
+    cudaFree(c->d_mu_scale);
+    cudaFree(c->d_mu_mat);
+    cudaFree(c->d_md_scale);
+    cudaFree(c->d_md_mat);
+    cudaFree(c->d_md_pinv);
+    cudaFree(c->d_rs_qlinv);
+    cudaFree(c->scratch);
+    free(c);
+}
+
+extern "C" int fides_ctx_beta(const fides_ctx *c, int n_limbs)
+{
+    if (!c || n_limbs < 1) return 0;
+    return (n_limbs + c->alpha - 1) / c->alpha;
+}
+
+extern "C" uint64_t fides_ctx_psi(const fides_ctx *c, int i)
+{
+    if (!c || i < 0 || i >= c->L + c->K) return 0;
+    return c->psi[i];
+}
+
+extern "C" uint64_t fides_galois_elt(const fides_ctx *c, int64_t steps)
+{
+    if (!c) return 0;
+    int64_t half = c->N / 2;
+    int64_t k = ((steps % half) + half) % half;
+    return hpow(5, (u64)k, 2 * (u64)c->N);
+}
+
+// Scratch words one top-level operation needs (see the layout in kernels.cu).
+static size_t scratch_words_for(int L, int K, int dnum, int alpha, int N)
+{
+    int beta = (L + alpha - 1) / alpha;
+    (void)dnum;
+    size_t ne = (size_t)(L + K);
+    // d2 / rotated c1 (L) + coeff copy (L) + ext (beta*ne) + acc (2*ne)
+    // + P-limb INTT (2K) + conversion outputs (2L) + two spare limbs
+    return (size_t)N * (2 * (size_t)L + beta * ne + 2 * ne + 2 * (size_t)K + 2 * (size_t)L + 2);
+}
+
+extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out)
+{
+    if (!out) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_create: out is NULL");
+    *out = nullptr;
+    if (!primes || L < 1 || K < 1 || L + K > FIDES_MAX_PRIMES || dnum < 1 || dnum > L)
+        return fides_set_error(FIDES_ERR_ARG, "fides_ctx_create: bad sizes (L=%d K=%d dnum=%d)", L, K, dnum);
+    if (logN != 12 && logN != 16)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: logN=%d (supported: 12, 16)", logN);
+    int alpha = (L + dnum - 1) / dnum;
+    if (alpha > FIDES_MAX_SRC || K > FIDES_MAX_SRC)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: digit size %d or K=%d above %d",
+                               alpha, K, FIDES_MAX_SRC);
+    if ((L + alpha - 1) / alpha > FIDES_MAX_DIGITS)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: more than %d digits", FIDES_MAX_DIGITS);
+    const int N = 1 << logN, np = L + K;
+    for (int i = 0; i < np; ++i) {
+        u64 q = primes[i];
+        if (q >= ((u64)1 << 61) || !is_prime(q) || (q - 1) % (2 * (u64)N) != 0)
+            return fides_set_error(FIDES_ERR_PRIME, "fides_ctx_create: primes[%d]=%llu is not an NTT prime < 2^61",
+                                   i, (unsigned long long)q);
+        for (int k = 0; k < i; ++k)
+            if (primes[k] == q) return fides_set_error(FIDES_ERR_PRIME, "fides_ctx_create: repeated prime");
+    }
+
+    fides_ctx *c = (fides_ctx *)calloc(1, sizeof(fides_ctx));
+    if (!c) return fides_set_error(FIDES_ERR_NOMEM, "fides_ctx_create: host allocation");
+    cudaGetDevice(&c->device);
+    c->logN = logN; c->N = N; c->L = L; c->K = K; c->dnum = dnum; c->alpha = alpha;
+    memcpy(c->primes, primes, sizeof(u64) * np);
+
+    // per-prime constants and twiddles
+    std::vector<PrimeInfo> pinfo(np);
+    std::vector<TwPair> tw((size_t)np * N), itw((size_t)np * N);
+    for (int i = 0; i < np; ++i) {
+        u64 q = primes[i];
+        u64 g = smallest_generator(q);
+        u64 psi = hpow(g, (q - 1) / (2 * (u64)N), q);
+        c->psi[i] = psi;
+        u64 ipsi = hinv(psi, q);
+        PrimeInfo &P = pinfo[i];
+        P.q = q; P.q2 = 2 * q;
+        P.mu = (u64)(((u128)1 << 64) / q);
+        P.r64 = (u64)(((u128)1 << 64) % q);
+        P.r64p = shoup_of(P.r64, q);
+        P.ninv = hinv((u64)N % q, q);
+        P.ninvp = shoup_of(P.ninv, q);
+        P.pad = 0;
+        // powers in natural order, then scattered to bit-reversed positions
+        u64 x = 1, y = 1;
+        for (int k = 0; k < N; ++k) {
+            size_t at = (size_t)i * N + bitrev(k, logN);
+            tw[at] = pair_of(x, q);
+            itw[at] = pair_of(y, q);
+            x = hmul(x, psi, q);
+            y = hmul(y, ipsi, q);
+        }
+    }
+
+    // ModUp tables per (nl, j)
+    std::vector<TwPair> mu_scale((size_t)L * dnum * alpha);
+    std::vector<u64> mu_mat((size_t)L * dnum * alpha * np);
+    for (int nl = 1; nl <= L; ++nl) {
+        int beta = (nl + alpha - 1) / alpha;
+        for (int j = 0; j < beta; ++j) {
+            int lo = j * alpha, hi = std::min(lo + alpha, nl);
+            size_t off = ((size_t)(nl - 1) * dnum + j) * alpha;
+            for (int i = lo; i < hi; ++i) {
+                u64 qi = primes[i];
+                u64 prod = 1;
+                for (int k = lo; k < hi; ++k)
+                    if (k != i) prod = hmul(prod, primes[k] % qi, qi);
+                mu_scale[off + (i - lo)] = pair_of(hinv(prod, qi), qi);
+                for (int z = 0; z < np; ++z) {
+                    u64 p = primes[z], h = 1;
+                    for (int k = lo; k < hi; ++k)
+                        if (k != i) h = hmul(h, primes[k] % p, p);
+                    mu_mat[(off + (i - lo)) * np + z] = h;
+                }
+            }
+        }
+    }
+
+    // ModDown tables
+    std::vector<TwPair> md_scale(K), md_pinv(L);
+    std::vector<u64> md_mat((size_t)K * np);
+    for (int k = 0; k < K; ++k) {
+        u64 pk = primes[L + k], prod = 1;
+        for (int m = 0; m < K; ++m)
+            if (m != k) prod = hmul(prod, primes[L + m] % pk, pk);
+        md_scale[k] = pair_of(hinv(prod, pk), pk);
+        for (int z = 0; z < np; ++z) {
+            u64 p = primes[z], h = 1;
+            for (int m = 0; m < K; ++m)
+                if (m != k) h = hmul(h, primes[L + m] % p, p);
+            md_mat[(size_t)k * np + z] = h;
+        }
+    }
+    for (int i = 0; i < L; ++i) {
+        u64 qi = primes[i], P = 1;
+        for (int k = 0; k < K; ++k) P = hmul(P, primes[L + k] % qi, qi);
+        md_pinv[i] = pair_of(hinv(P, qi), qi);
+    }
+
+    // Rescale tables
+    std::vector<TwPair> rs((size_t)L * L);
+    for (int l = 1; l < L; ++l)
+        for (int i = 0; i < l; ++i) rs[(size_t)l * L + i] = pair_of(hinv(primes[l] % primes[i], primes[i]), primes[i]);
+
+    int rc = FIDES_OK;
+    if (!rc) rc = upload(&c->d_prime, pinfo, "tables");
+    if (!rc) rc = upload(&c->d_tw, tw, "twiddles");
+    if (!rc) rc = upload(&c->d_itw, itw, "twiddles");
+    if (!rc) rc = upload(&c->d_mu_scale, mu_scale, "modup tables");
+    if (!rc) rc = upload(&c->d_mu_mat, mu_mat, "modup tables");
+    if (!rc) rc = upload(&c->d_md_scale, md_scale, "moddown tables");
+    if (!rc) rc = upload(&c->d_md_mat, md_mat, "moddown tables");
+    if (!rc) rc = upload(&c->d_md_pinv, md_pinv, "moddown tables");
+    if (!rc) rc = upload(&c->d_rs_qlinv, rs, "rescale tables");
+    if (!rc) {
+        c->scratch_words = scratch_words_for(L, K, dnum, alpha, N);
+        rc = fides_check_cuda(cudaMalloc((void **)&c->scratch, c->scratch_words * sizeof(u64)), "scratch pool");
+    }
+    if (rc) {
+        fides_ctx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return FIDES_OK;
+}

@@ -1,0 +1,188 @@
+// Internal definitions of the GB300 CKKS key-switching engine: context layout,
+// per-prime constants, job descriptors and 64-bit modular arithmetic.
+//
+// Modular arithmetic (Sec. III-E2 and its Table "mod_red"):
+//   - Shoup multiplication by a fixed operand w with companion
+//     w' = floor(w * 2^64 / q): one high and two low 64-bit products, result in
+//     [0, 2q) for any 64-bit input (used for twiddles and per-prime constants).
+//   - Reduction of a full 128-bit value (hi, lo): hi * 2^64 is folded with a
+//     Shoup product by 2^64 mod q and lo with a one-word Barrett step
+//     (mu = floor(2^64 / q)); two high and three low products in total.
+//   - Additions keep values in [0, 2q) (lazy) or [0, q) (canonical) with one
+//     conditional subtraction.
+// All primes are below 2^61, so 4q < 2^63 and sums of up to 32 products of
+// canonical residues fit in 128 bits.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fides.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+#define FIDES_MAX_PRIMES 64
+#define FIDES_MAX_SEG 24
+#define FIDES_MAX_DIGITS 8
+#define FIDES_MAX_SRC 32
+
+// A twiddle or constant with its Shoup companion.
+struct __align__(16) TwPair {
+    u64 w, wp;
+};
+
+// Per-prime constants.
+struct __align__(16) PrimeInfo {
+    u64 q;      // the prime
+    u64 q2;     // 2q
+    u64 mu;     // floor(2^64 / q)
+    u64 r64;    // 2^64 mod q
+    u64 r64p;   // Shoup companion of r64
+    u64 ninv;   // N^-1 mod q
+    u64 ninvp;  // Shoup companion of ninv
+    u64 pad;
+};
+
+// One contiguous run of limbs processed by a kernel: limb k of the run reads
+// src + k*src_step*N, writes dst + k*N, optionally reads aux + k*N and writes
+// out + k*N, and uses prime index prime0 + k.  `mode` selects an epilogue
+// variant (see the functors in kernels.cu).
+struct Seg {
+    const u64 *src;
+    u64 *dst;
+    const u64 *aux;
+    u64 *out;
+    int count;
+    int prime0;
+    int src_step;   // 1: src advances one limb per limb; 0: every limb reads the same src limb
+    int mode;
+};
+
+struct LimbSet {
+    int nseg;
+    int total;
+    Seg seg[FIDES_MAX_SEG];
+};
+
+// A job resolved for limb z of a LimbSet.
+struct Job {
+    const u64 *src;
+    u64 *dst;
+    const u64 *aux;
+    u64 *out;
+    int prime;
+    int mode;
+};
+
+struct fides_ctx {
+    int device;
+    int logN;
+    int N;
+    int L, K, dnum, alpha;
+    u64 primes[FIDES_MAX_PRIMES];
+    u64 psi[FIDES_MAX_PRIMES];
+
+    PrimeInfo *d_prime;   // [L+K]
+    TwPair *d_tw;         // [L+K][N]   psi^brv(k)
+    TwPair *d_itw;        // [L+K][N]   psi^-brv(k)
+
+    // ModUp base conversion, per (nl, digit j) at index (nl-1)*dnum + j:
+    //   d_mu_scale[off .. off+alpha)        qhat_i^-1 mod q_i (Shoup pairs)
+    //   d_mu_mat[off*(L+K) ..]              [alpha][L+K]: [qhat_i]_{prime z}
+    TwPair *d_mu_scale;
+    u64 *d_mu_mat;
+
+    // ModDown base conversion P -> Q (independent of the level)
+    TwPair *d_md_scale;   // [K]      Phat_k^-1 mod p_k
+    u64 *d_md_mat;        // [K][L+K] [Phat_k]_{prime z}
+    TwPair *d_md_pinv;    // [L]      P^-1 mod q_i
+
+    // Rescale: [L][L], entry (l, i) = q_l^-1 mod q_i
+    TwPair *d_rs_qlinv;
+
+    // Scratch pool for one operation at the top level.
+    u64 *scratch;
+    size_t scratch_words;
+};
+
+// ---------------------------------------------------------------------------
+// Device modular arithmetic
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
+
+// a >= m ? a - m : a
+__device__ __forceinline__ u64 csub(u64 a, u64 m) { return a >= m ? a - m : a; }
+
+// a * w mod q in [0, 2q) for any 64-bit a (Shoup).
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wp, u64 q)
+{
+    return a * w - mulhi64(a, wp) * q;
+}
+
+__device__ __forceinline__ u64 mul_shoup(u64 a, const TwPair &t, u64 q)
+{
+    return mul_shoup(a, t.w, t.wp, q);
+}
+
+// x mod q in [0, 2q) for a 64-bit x (one-word Barrett).
+__device__ __forceinline__ u64 reduce64_lazy(u64 x, const PrimeInfo &p)
+{
+    return x - mulhi64(x, p.mu) * p.q;
+}
+
+// (hi * 2^64 + lo) mod q, canonical.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const PrimeInfo &p)
+{
+    u64 a = mul_shoup(hi, p.r64, p.r64p, p.q);   // [0, 2q)
+    u64 b = reduce64_lazy(lo, p);                  // [0, 2q)
+    u64 s = csub(a + b, p.q2);                     // [0, 2q)
+    return csub(s, p.q);
+}
+
+// a * b mod q, canonical, for any 64-bit a, b.
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeInfo &p)
+{
+    return reduce128(mulhi64(a, b), a * b, p);
+}
+
+// 128-bit accumulator
+struct U128 {
+    u64 lo, hi;
+};
+
+__device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b)
+{
+    u64 lo = a * b;
+    u64 hi = mulhi64(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+}
+
+__device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
+{
+    Job j;
+    #pragma unroll 1
+    for (int s = 0; s < S.nseg; ++s) {
+        const Seg &g = S.seg[s];
+        if (z < g.count) {
+            j.src = g.src + (size_t)z * g.src_step * N;
+            j.dst = g.dst ? g.dst + (size_t)z * N : nullptr;
+            j.aux = g.aux ? g.aux + (size_t)z * N : nullptr;
+            j.out = g.out ? g.out + (size_t)z * N : nullptr;
+            j.prime = g.prime0 + z;
+            j.mode = g.mode;
+            return j;
+        }
+        z -= g.count;
+    }
+    j.src = nullptr; j.dst = nullptr; j.aux = nullptr; j.out = nullptr; j.prime = 0; j.mode = 0;
+    return j;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers shared by the translation units
+// ---------------------------------------------------------------------------
+int fides_set_error(int code, const char *fmt, ...);
+int fides_check_cuda(cudaError_t e, const char *what);

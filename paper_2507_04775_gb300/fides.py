@@ -1,0 +1,201 @@
+"""Python binding of the C ABI in ``include/fides.h`` (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``_build/libfides.so``;
+this module converts torch tensors to device pointers, passes the current torch
+stream, and turns negative return codes into exceptions.  There is no CPU
+fallback: if the library is missing, every call raises.
+
+Buffers are torch tensors on the context's device, contiguous, of dtype
+``torch.int64`` or ``torch.uint64`` (the bits are the u64 residues).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfides.so")
+
+FIDES_OK = 0
+ERRORS = {-1: "FIDES_ERR_ARG", -2: "FIDES_ERR_UNSUPPORTED", -3: "FIDES_ERR_NOMEM", -4: "FIDES_ERR_CUDA",
+          -5: "FIDES_ERR_TIMEOUT", -6: "FIDES_ERR_PRIME"}
+
+EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_create", "fides_ctx_destroy",
+           "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
+           "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale"]
+
+
+class FidesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "FIDES_ERR"), code, msg))
+        self.code = code
+
+
+class fides_ct(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n_limbs", ctypes.c_int), ("scale", ctypes.c_double)]
+
+
+_lib = None
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfides.so is missing (%s); build it with __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.fides_last_error.restype = ctypes.c_char_p
+        L.fides_version.restype = ctypes.c_char_p
+        L.fides_find_primes.argtypes = [_i, _i, _i, _u64p, _i, _u64p]
+        L.fides_ctx_create.argtypes = [_i, _i, _i, _i, _u64p, ctypes.POINTER(_vp)]
+        L.fides_ctx_destroy.argtypes = [_vp]
+        L.fides_ctx_destroy.restype = None
+        L.fides_ctx_beta.argtypes = [_vp, _i]
+        L.fides_ctx_psi.argtypes = [_vp, _i]
+        L.fides_ctx_psi.restype = ctypes.c_uint64
+        L.fides_galois_elt.argtypes = [_vp, ctypes.c_int64]
+        L.fides_galois_elt.restype = ctypes.c_uint64
+        for name in ("fides_ntt", "fides_intt"):
+            getattr(L, name).argtypes = [_vp, _vp, _i, _i, _i, _vp]
+        L.fides_modup.argtypes = [_vp, _vp, _i, _vp, _vp]
+        L.fides_moddown.argtypes = [_vp, _vp, _i, _vp, _vp]
+        L.fides_keyswitch.argtypes = [_vp, _vp, _i, _vp, _vp, _vp, _vp]
+        ctp = ctypes.POINTER(fides_ct)
+        L.fides_hmult.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
+        L.fides_rotate.argtypes = [_vp, ctp, ctypes.c_int64, _vp, ctp, _vp]
+        L.fides_rescale.argtypes = [_vp, ctp, ctp, _vp]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FIDES_OK:
+        raise FidesError(rc, lib().fides_last_error().decode())
+
+
+def version() -> str:
+    return lib().fides_version().decode()
+
+
+def find_primes(logN: int, bits: int, count: int, exclude=()) -> list[int]:
+    ex = np.ascontiguousarray(list(exclude) or [0], dtype=np.uint64)
+    out = np.zeros(max(count, 1), dtype=np.uint64)
+    _check(lib().fides_find_primes(logN, bits, count, ex.ctypes.data_as(_u64p), len(exclude),
+                                   out.ctypes.data_as(_u64p)))
+    return [int(x) for x in out[:count]]
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, words: int | None = None, name: str = "buffer"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("%s must be int64/uint64" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if words is not None and t.numel() < words:
+        raise ValueError("%s holds %d words, needs %d" % (name, t.numel(), words))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def to_device(a: np.ndarray, device="cuda"):
+    """uint64 numpy array -> int64 CUDA tensor with the same bits."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def to_host(t) -> np.ndarray:
+    """CUDA tensor -> uint64 numpy array with the same bits."""
+    return t.detach().cpu().contiguous().numpy().view(np.uint64)
+
+
+class Context:
+    """A library context (``fides_ctx``) on the current CUDA device."""
+
+    def __init__(self, logN: int, q_primes, p_primes, dnum: int):
+        self.logN, self.N = logN, 1 << logN
+        self.q = [int(x) for x in q_primes]
+        self.p = [int(x) for x in p_primes]
+        self.L, self.K, self.dnum = len(self.q), len(self.p), dnum
+        self.alpha = -(-self.L // dnum)
+        arr = np.ascontiguousarray(self.q + self.p, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        _check(lib().fides_ctx_create(logN, self.L, self.K, dnum, arr.ctypes.data_as(_u64p), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fides_ctx_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    # -- structure ---------------------------------------------------------
+    def beta(self, n_limbs: int) -> int:
+        return lib().fides_ctx_beta(self._h, n_limbs)
+
+    def psi(self, i: int) -> int:
+        return int(lib().fides_ctx_psi(self._h, i))
+
+    def galois_elt(self, steps: int) -> int:
+        return int(lib().fides_galois_elt(self._h, steps))
+
+    # -- primitives --------------------------------------------------------
+    def ntt(self, t, first_prime: int, n_limbs: int, batch: int = 1, stream=None):
+        _check(lib().fides_ntt(self._h, _ptr(t, batch * n_limbs * self.N), first_prime, n_limbs, batch,
+                               _stream(stream)))
+
+    def intt(self, t, first_prime: int, n_limbs: int, batch: int = 1, stream=None):
+        _check(lib().fides_intt(self._h, _ptr(t, batch * n_limbs * self.N), first_prime, n_limbs, batch,
+                                _stream(stream)))
+
+    def modup(self, d, n_limbs: int, ext, stream=None):
+        ne = n_limbs + self.K
+        _check(lib().fides_modup(self._h, _ptr(d, n_limbs * self.N, "d"), n_limbs,
+                                 _ptr(ext, self.beta(n_limbs) * ne * self.N, "ext"), _stream(stream)))
+
+    def moddown(self, x, n_limbs: int, out, stream=None):
+        _check(lib().fides_moddown(self._h, _ptr(x, (n_limbs + self.K) * self.N, "x"), n_limbs,
+                                   _ptr(out, n_limbs * self.N, "out"), _stream(stream)))
+
+    def keyswitch(self, d, n_limbs: int, evk, out0, out1, stream=None):
+        w = n_limbs * self.N
+        _check(lib().fides_keyswitch(self._h, _ptr(d, w, "d"), n_limbs, _ptr(evk, self.key_words(), "evk"),
+                                     _ptr(out0, w, "out0"), _ptr(out1, w, "out1"), _stream(stream)))
+
+    def key_words(self) -> int:
+        return self.dnum * 2 * (self.L + self.K) * self.N
+
+    # -- ciphertext operations ---------------------------------------------
+    def _ct(self, t, n_limbs: int, scale: float, name: str):
+        return fides_ct(_ptr(t, 2 * n_limbs * self.N, name).value, n_limbs, scale)
+
+    def hmult(self, a, b, n_limbs: int, rlk, out, scale_a: float = 1.0, scale_b: float = 1.0, stream=None) -> float:
+        ca, cb = self._ct(a, n_limbs, scale_a, "a"), self._ct(b, n_limbs, scale_b, "b")
+        co = self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_hmult(self._h, ctypes.byref(ca), ctypes.byref(cb), _ptr(rlk, self.key_words(), "rlk"),
+                                 ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def rotate(self, a, n_limbs: int, steps: int, rk, out, scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_rotate(self._h, ctypes.byref(ca), steps, _ptr(rk, self.key_words(), "rk"),
+                                  ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
+        _check(lib().fides_rescale(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
+        return co.scale

@@ -1,0 +1,209 @@
+"""GPU parity: every entry point of the C ABI against the CPU oracle, residue
+for residue (bit-exact), on seeded inputs.
+
+Sizes: the logN=12 workload (3 limbs, K=1, dnum=3) and a logN=12 set with 12
+limbs (K=4, alpha=4: several digits, a ragged last digit) run in full; the
+logN=16 workload (30 limbs, K=10, dnum=3) runs in full at the top level and
+at ragged levels.  Keys are uniform residues (parity does not depend on key
+structure); decryption through real keys is checked separately.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from oracle.client import Client
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2507_04775_gb300 import Context, FidesError, find_primes, to_device, to_host  # noqa: E402
+
+
+def make_pair(P):
+    q = find_primes(P.logN, P.q_bits, P.nq)
+    p = find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    return Context(P.logN, q, p, P.dnum), oracle.Context(P.logN, q, p, P.dnum)
+
+
+@pytest.fixture(scope="module", params=["SMALL", "MID", "FULL"])
+def pair(request):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = getattr(si, request.param)
+    g, o = make_pair(P)
+    yield P, g, o
+    g.close()
+
+
+def rand_poly(st, primes, N, npoly=None):
+    if npoly is None:
+        return si.uniform_poly(st, primes, N)
+    return np.stack([si.uniform_poly(st, primes, N) for _ in range(npoly)])
+
+
+def rand_key(st, o):
+    return np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
+
+
+def levels(P):
+    # top level, a ragged level inside a digit, and the bottom
+    return sorted({P.nq, max(1, P.nq - 3), max(1, (P.nq + 1) // 2), 1})
+
+
+def test_ntt_intt_all_primes(pair):
+    P, g, o = pair
+    st = si.Stream(1000 + P.logN, 1)
+    n = len(o.primes)
+    a = rand_poly(st, o.primes, o.N)
+    d = to_device(a)
+    g.ntt(d, 0, n)
+    A = o.ntt_limbs(a, list(range(n)))
+    assert np.array_equal(to_host(d).reshape(a.shape), A)
+    g.intt(d, 0, n)
+    assert np.array_equal(to_host(d).reshape(a.shape), a)
+
+
+def test_ntt_batch_and_offset(pair):
+    P, g, o = pair
+    st = si.Stream(1001, 2)
+    first, nl, batch = 1, min(3, len(o.primes) - 1), 3
+    prim = o.primes[first:first + nl]
+    a = np.stack([rand_poly(st, prim, o.N) for _ in range(batch)])
+    d = to_device(a)
+    g.ntt(d, first, nl, batch)
+    got = to_host(d).reshape(a.shape)
+    for b in range(batch):
+        assert np.array_equal(got[b], o.ntt_limbs(a[b], list(range(first, first + nl))))
+    g.intt(d, first, nl, batch)
+    assert np.array_equal(to_host(d).reshape(a.shape), a)
+
+
+def test_modup(pair):
+    P, g, o = pair
+    st = si.Stream(1002, 3)
+    for nl in levels(P):
+        d = rand_poly(st, o.q[:nl], o.N)
+        beta = g.beta(nl)
+        ext = torch.zeros(beta * (nl + o.nk) * o.N, dtype=torch.int64, device="cuda")
+        g.modup(to_device(d), nl, ext)
+        got = to_host(ext).reshape(beta, nl + o.nk, o.N)
+        assert np.array_equal(got, o.modup(d)), "modup differs at nl=%d" % nl
+
+
+def test_moddown(pair):
+    P, g, o = pair
+    st = si.Stream(1003, 4)
+    for nl in levels(P):
+        x = rand_poly(st, o.q[:nl] + o.p, o.N)
+        out = torch.zeros(nl * o.N, dtype=torch.int64, device="cuda")
+        g.moddown(to_device(x), nl, out)
+        assert np.array_equal(to_host(out).reshape(nl, o.N), o.moddown(x)), "moddown differs at nl=%d" % nl
+
+
+def test_keyswitch(pair):
+    P, g, o = pair
+    st = si.Stream(1004, 5)
+    key = rand_key(st, o)
+    dk = to_device(key)
+    for nl in levels(P):
+        d = rand_poly(st, o.q[:nl], o.N)
+        o0 = torch.zeros(nl * o.N, dtype=torch.int64, device="cuda")
+        o1 = torch.zeros_like(o0)
+        g.keyswitch(to_device(d), nl, dk, o0, o1)
+        w0, w1 = o.keyswitch(d, key)
+        assert np.array_equal(to_host(o0).reshape(nl, o.N), w0), "ks0 differs at nl=%d" % nl
+        assert np.array_equal(to_host(o1).reshape(nl, o.N), w1), "ks1 differs at nl=%d" % nl
+
+
+def test_hmult(pair):
+    P, g, o = pair
+    st = si.Stream(1005, 6)
+    key = rand_key(st, o)
+    dk = to_device(key)
+    for nl in levels(P):
+        a, b = rand_poly(st, o.q[:nl], o.N, 2), rand_poly(st, o.q[:nl], o.N, 2)
+        out = torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
+        scale = g.hmult(to_device(a), to_device(b), nl, dk, out, 2.0**40, 2.0**40)
+        assert scale == 2.0**80
+        assert np.array_equal(to_host(out).reshape(2, nl, o.N), o.hmult(a, b, key)), "hmult differs at nl=%d" % nl
+
+
+def test_rotate(pair):
+    P, g, o = pair
+    st = si.Stream(1006, 7)
+    key = rand_key(st, o)
+    dk = to_device(key)
+    nl = P.nq
+    a = rand_poly(st, o.q[:nl], o.N, 2)
+    da = to_device(a)
+    steps_list = [1, 2, 1 << (P.logN - 3), -1, o.N // 2, 3 * o.N]
+    for steps in steps_list:
+        out = torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
+        g.rotate(da, nl, steps, dk, out)
+        assert np.array_equal(to_host(out).reshape(2, nl, o.N), o.rotate(a, steps, key)), "rotate %d" % steps
+    nl2 = max(1, nl - 3)
+    a2 = rand_poly(st, o.q[:nl2], o.N, 2)
+    out = torch.zeros(2 * nl2 * o.N, dtype=torch.int64, device="cuda")
+    g.rotate(to_device(a2), nl2, 5, dk, out)
+    assert np.array_equal(to_host(out).reshape(2, nl2, o.N), o.rotate(a2, 5, key))
+
+
+def test_rescale(pair):
+    P, g, o = pair
+    st = si.Stream(1007, 8)
+    for nl in sorted({P.nq, 2, max(2, P.nq // 2)}):
+        a = rand_poly(st, o.q[:nl], o.N, 2)
+        out = torch.zeros(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+        scale = g.rescale(to_device(a), nl, out, 2.0**80)
+        assert scale == 2.0**80 / o.q[nl - 1]
+        assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), o.rescale(a)), "rescale differs at nl=%d" % nl
+
+
+def test_galois_and_psi(pair):
+    P, g, o = pair
+    for i in range(len(o.primes)):
+        assert g.psi(i) == o.psi(i)
+    for s in [0, 1, 7, -1, -5, o.N, 12345]:
+        assert g.galois_elt(s) == o.galois_elt(s)
+
+
+def test_argument_errors(pair):
+    P, g, o = pair
+    d = torch.zeros(2 * o.N, dtype=torch.int64, device="cuda")
+    with pytest.raises(FidesError) as e:
+        g.rescale(d, 1, d)
+    assert e.value.code == -1
+    with pytest.raises(FidesError):
+        g.ntt(d, len(o.primes), 1)
+    with pytest.raises(ValueError):
+        g.ntt(d, 0, 3)
+
+
+def test_decrypts_through_gpu_with_real_keys():
+    """HMult+relin, Rescale and HRotate on the GPU with keys made by the
+    oracle's client: slot error against the FP64 product/rotation <= 2^-20."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.SMALL
+    g, o = make_pair(P)
+    cl = Client(o, seed=si.workload_seed(0))
+    z1, z2 = cl.random_slots(), cl.random_slots()
+    nl = P.nq
+    a, b = cl.encrypt(z1, nl, 2.0**40), cl.encrypt(z2, nl, 2.0**40)
+    rlk, rk = cl.relin_key(), cl.rotation_key(3)
+    out = torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
+    s = g.hmult(to_device(a), to_device(b), nl, to_device(rlk), out, 2.0**40, 2.0**40)
+    prod = to_host(out).reshape(2, nl, o.N)
+    ref = z1 * z2
+    err = np.max(np.abs(cl.decrypt(prod, s) - ref)) / max(1.0, np.max(np.abs(ref)))
+    assert err < 2.0**-20, err
+    rs = torch.zeros(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+    s2 = g.rescale(out, nl, rs, s)
+    err2 = np.max(np.abs(cl.decrypt(to_host(rs).reshape(2, nl - 1, o.N), s2) - ref)) / max(1.0, np.max(np.abs(ref)))
+    assert err2 < 2.0**-20, err2
+    rot = torch.zeros_like(out)
+    g.rotate(to_device(a), nl, 3, to_device(rk), rot)
+    err3 = np.max(np.abs(cl.decrypt(to_host(rot).reshape(2, nl, o.N), 2.0**40) - np.roll(z1, -3)))
+    assert err3 < 2.0**-20, err3
+    g.close()
