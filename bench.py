@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Benchmark of the CKKS hybrid key-switching path on one GB300 (or N replicas).
+
+Workload (single-op path): logN=16 (N=65536), 30 ciphertext limbs of 54-bit
+primes, K=10 special 60-bit primes, dnum=3 (10 limbs per digit).  One step is
+  HMult+relin of a ciphertext pair  ->  Rescale of the product (30 -> 29 limbs)
+  HRotate of a ciphertext by 2^(k mod 15) slots (15 rotation keys)
+with every input resident in HBM.  The metric counts HMult+relin and HRotate
+operations (two per step); the Rescale time is inside the timed region.
+
+Inputs are seeded synthetic residues (uniform mod each prime, from the shared
+generator in seeded_inputs.py); keys are uniform residues of the key shape
+(computationally indistinguishable from real RLWE keys, and the kernels'
+work does not depend on their values).  A pool of 8 ciphertext pairs and the
+16 keys (1.9 GiB) are cycled, so each step touches >400 MB: more than the
+129 MB L2 between repeats.
+
+Modes
+  python bench.py [--gpus N --steps K --warmup W]      the CUDA library
+  python bench.py --impl reference ...                 the CPU oracle (reference arm)
+Multi-GPU runs are replicas (one independent workload per rank, no collective
+on the data path; torch.distributed only for the barrier and the max-time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+METRIC = "HMult+relin & HRotate ops/s (logN=16,L=30,dnum=3)"
+POOL = 8
+N_ROT = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fides", choices=["fides", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="one ciphertext pair and two keys (for profiler captures; not a bench line)")
+    args = ap.parse_args()
+    if args.small:
+        global POOL, N_ROT
+        POOL, N_ROT = 1, 1
+    return args
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "fides" else "gloo"
+        if args.impl == "fides":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload_inputs(P, q, p, seed):
+    """Host arrays of the workload: POOL ciphertext pairs and 16 keys."""
+    st = si.Stream(seed, 10)
+    N = 1 << P.logN
+    A = [np.stack([si.uniform_poly(st, q, N) for _ in range(2)]) for _ in range(POOL)]
+    B = [np.stack([si.uniform_poly(st, q, N) for _ in range(2)]) for _ in range(POOL)]
+    keys = [np.stack([np.stack([si.uniform_poly(st, q + p, N) for _ in range(2)]) for _ in range(P.dnum)])
+            for _ in range(1 + N_ROT)]
+    return A, B, keys
+
+
+def launch_model(nl, K, alpha, N):
+    """Per-step launches of the library's kernels with their algorithmic work.
+
+    Unit of an NTT pass: one limb (N u64 read + N written = 16 N bytes,
+    (N/2)*log2(N)/2 butterflies = one Shoup product each).  Element-wise
+    kernels count the limbs they must read and write once.  Returns a list of
+    (kernel, bytes, modmuls)."""
+    W = 8 * N
+    half_bfly = (N // 2) * 8          # butterflies of one pass (8 of the 16 stages) per limb
+    beta = -(-nl // alpha)
+    ne = nl + K
+    L = []
+
+    def ntt(direction, limbs, extra_bytes=0, extra_mm=0, ninv=False):
+        # two passes; the second carries any fused epilogue
+        L.append(("k_ntt_%s_%s" % (direction, "rows" if direction == "inv" else "cols"), 2 * W * limbs, half_bfly * limbs))
+        L.append(("k_ntt_%s_%s" % (direction, "cols" if direction == "inv" else "rows"),
+                  2 * W * limbs + extra_bytes, half_bfly * limbs + extra_mm + (N * limbs if ninv else 0)))
+
+    def keyswitch(mode0, mode1):
+        ntt("inv", nl, ninv=True)                                    # ModUp: coefficient form of d
+        ntgt = beta * ne - nl
+        L.append(("k_bconv", W * (nl + ntgt), N * (nl + sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta)))))
+        ntt("fwd", ntgt)
+        L.append(("k_inner", W * (beta * ne + 2 * beta * ne + 2 * ne), N * 2 * beta * ne))
+        ntt("inv", 2 * K, ninv=True)                                 # ModDown: P-limbs to coefficients
+        L.append(("k_bconv", W * (2 * K + 2 * nl), N * 2 * (K + K * nl)))
+        extra = W * nl * (2 + mode0 + mode1)                         # aux reads (+ out reads when accumulating)
+        ntt("fwd", 2 * nl, extra_bytes=extra, extra_mm=2 * N * nl)
+
+    # HMult+relin
+    L.append(("k_tensor", W * (4 * nl + 3 * nl), 4 * N * nl))
+    keyswitch(1, 1)
+    # Rescale of the product
+    ntt("inv", 2, ninv=True)
+    ntt("fwd", 2 * (nl - 1), extra_bytes=W * 2 * (nl - 1), extra_mm=N * 4 * (nl - 1))
+    # HRotate
+    L.append(("k_permute", W * 2 * nl, 0))
+    L.append(("k_permute", W * 2 * nl, 0))
+    keyswitch(1, 0)
+    return L
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        mp = json.load(open(path))
+        return float(mp["hbm_gbs"]), "measured", float(mp.get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback", 2070.0
+
+
+# ALU roofline of a 64-bit Shoup product: 10 IMAD-class instructions (4 for the
+# high half of a 64x64 product, 3 for each low half), 64 IMAD per clock per
+# SM, 152 SMs.
+IMAD_PER_MODMUL = 10
+IMAD_PER_CLK_SM = 64
+SMS = 152
+
+
+def run_fides(args, world, rank, local):
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+
+    torch.cuda.set_device(local)
+    P = si.FULL
+    q = fides.find_primes(P.logN, P.q_bits, P.nq)
+    p = fides.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    ctx = fides.Context(P.logN, q, p, P.dnum)
+    N, nl = ctx.N, P.nq
+    A, B, keys = workload_inputs(P, q, p, si.workload_seed(1) + 1000 * rank)
+    dA = [fides.to_device(x) for x in A]
+    dB = [fides.to_device(x) for x in B]
+    dK = [fides.to_device(x) for x in keys]
+    rlk, rks = dK[0], dK[1:]
+    out_m = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    out_r = torch.empty_like(out_m)
+    out_s = torch.empty(2 * (nl - 1) * N, dtype=torch.int64, device="cuda")
+    scale = 2.0 ** P.log_scale
+
+    def step(k, a=None, b=None):
+        i = k % POOL
+        a = dA[i] if a is None else a
+        b = dB[i] if b is None else b
+        s = ctx.hmult(a, b, nl, rlk, out_m, scale, scale)
+        ctx.rescale(out_m, nl, out_s, s)
+        ctx.rotate(a, nl, 1 << (k % N_ROT), rks[k % N_ROT], out_r, scale)
+
+    clocks = Clocks(local)
+    clocks.start()             # sampling runs through the warm-up and the timed region
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (inputs resident in HBM) ----------------
+    fides.trace_reset()
+    fides.trace_enable(True)
+    launches0 = fides.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    launches = fides.kernel_launches() - launches0
+    fides.trace_enable(False)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    trace = fides.trace_read()
+    fides.trace_reset()
+    ops = 2 * args.steps * world
+    value = ops / (ms_max / 1e3)
+
+    # ---------------- roofline of the dominant kernel ----------------
+    kern = {k: v for k, v in trace.items() if k.startswith("k_")}
+    top = max(kern, key=lambda k: kern[k][1])
+    model = launch_model(nl, P.nk, ctx.alpha, N)
+    per_kernel = {}
+    for name, by, mm in model:
+        d = per_kernel.setdefault(name, [0, 0, 0])
+        d[0] += 1
+        d[1] += by
+        d[2] += mm
+    mismatch = {k: (per_kernel.get(k, [0])[0] * args.steps, kern[k][0]) for k in kern
+                if per_kernel.get(k, [0])[0] * args.steps != kern[k][0]}
+    n_launch, by_step, mm_step = per_kernel[top]
+    avg_ms = kern[top][1] / kern[top][0]
+    bytes_per_launch = by_step / n_launch
+    mm_per_launch = mm_step / n_launch
+    hbm_peak, hbm_src, sm_max = peaks()
+    hbm_ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    clk = (ck or {}).get("sm_mhz") or sm_max
+    alu_peak = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / IMAD_PER_MODMUL / 1e9     # Gmodmul/s at max clock
+    alu_ach = mm_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = load_traffic(top, bytes_per_launch)
+    hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(hbm_ach / hbm_peak, 4), "traffic": traffic, "peak_source": hbm_src}
+    alu = {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
+           "frac": round(alu_ach / alu_peak, 4),
+           "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max}
+    roof = dict(hbm if hbm["frac"] >= alu["frac"] else alu)
+    roof["kernel"] = top
+    roof["avg_launch_us"] = round(avg_ms * 1e3, 2)
+    roof["other_bound"] = alu if roof["bound"] == "hbm" else hbm
+    roof["clock_mhz_median"] = clk
+
+    # ---------------- end to end through host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale)
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "ops/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "single-op path logN=16 L=30 K=10 dnum=3: HMult+relin, Rescale, HRotate(2^(k mod 15))",
+                   "logN": P.logN, "limbs": nl, "special_primes": P.nk, "dnum": P.dnum, "q_bits": P.q_bits,
+                   "p_bits": P.p_bits, "ops_per_step": 2,
+                   "l2": "inputs larger than L2: 8 ciphertext pairs + 16 keys (1.9 GiB) cycled, >400 MB per step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "per_op_us": {k[3:]: round(v[1] / v[0] * 1e3, 1) for k, v in trace.items() if k.startswith("op_")},
+        "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items(), key=lambda x: -x[1][1])},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "e2e": e2e,
+    }
+    if mismatch:
+        result["launch_model_mismatch"] = mismatch
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(P, q, p, A, B, keys, args.cpu_seconds)
+    elif rank == 0:
+        result["cpu_baseline"] = None
+    return result
+
+
+def load_traffic(kernel, bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = t.get(kernel)
+    if not ent or ent.get("sources_sha") != sources_sha():
+        return None
+    # the capture ran a smaller case: scale by the units one bench launch processes
+    return int(ent["dram_bytes_per_unit"] * bytes_per_launch / ent["algorithmic_bytes_per_unit"])
+
+
+def sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2507_04775_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
+    """Same steps through the public API with host buffers: every step copies
+    its input pair from pinned host memory and reads its three results back."""
+    import torch
+    steps = max(5, min(args.steps, 50))
+    hA = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in A]
+    hB = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in B]
+    da, db = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda"), torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    om, orr = torch.empty_like(da), torch.empty_like(da)
+    os_ = torch.empty(2 * (nl - 1) * N, dtype=torch.int64, device="cuda")
+    hm = torch.empty(om.shape, dtype=torch.int64).pin_memory()
+    hr = torch.empty(orr.shape, dtype=torch.int64).pin_memory()
+    hs = torch.empty(os_.shape, dtype=torch.int64).pin_memory()
+
+    def step(k):
+        i = k % POOL
+        da.copy_(hA[i], non_blocking=True)
+        db.copy_(hB[i], non_blocking=True)
+        s = ctx.hmult(da, db, nl, rlk, om, scale, scale)
+        ctx.rescale(om, nl, os_, s)
+        ctx.rotate(da, nl, 1 << (k % N_ROT), rks[k % N_ROT], orr, scale)
+        hm.copy_(om, non_blocking=True)
+        hs.copy_(os_, non_blocking=True)
+        hr.copy_(orr, non_blocking=True)
+
+    for k in range(3):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(steps):
+        step(k)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    return {"value": round(2 * steps * world / (ms / 1e3), 2), "unit": "ops/s", "steps": steps,
+            "h2d_bytes_per_step": 2 * hA[0].numel() * 8,
+            "d2h_bytes_per_step": (hm.numel() + hr.numel() + hs.numel()) * 8}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_steps(P, q, p, A, B, keys, budget_s, max_steps):
+    import oracle
+    ctx = oracle.Context(P.logN, q, p, P.dnum)
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        i = done % POOL
+        out = ctx.hmult(A[i], B[i], keys[0])
+        ctx.rescale(out)
+        ctx.rotate(A[i], 1 << (done % N_ROT), keys[1 + done % N_ROT])
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(P, q, p, A, B, keys, budget_s):
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    done, el = oracle_steps(P, q, p, A, B, keys, budget_s, 1000)
+    return {"value": round(2 * done / el, 4), "unit": "ops/s", "cores": cores, "kind": "oracle",
+            "sample": "%d step(s) of the same workload (HMult+relin, Rescale, HRotate at 30 limbs), %.1f s" % (done, el)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    P = si.FULL
+    import oracle
+    q = oracle.find_primes(P.logN, P.q_bits, P.nq)
+    p = oracle.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    A, B, keys = workload_inputs(P, q, p, si.workload_seed(1))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle_steps(P, q, p, A, B, keys, 0.0, min(args.warmup, 1))
+    # each step is the full workload step; the number timed is capped so the
+    # run stays within a few minutes
+    cap = max(1, min(args.steps, 40))
+    done, el = oracle_steps(P, q, p, A, B, keys, 120.0, cap)
+    value = 2 * done / el
+    return {"metric": METRIC, "value": round(value, 4), "unit": "ops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / done * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "single-op path logN=16 L=30 K=10 dnum=3: HMult+relin, Rescale, HRotate(2^(k mod 15))",
+                       "logN": P.logN, "limbs": P.nq, "special_primes": P.nk, "dnum": P.dnum},
+            "cpu_baseline": {"value": round(value, 4), "unit": "ops/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d of %d steps timed (capped at 40 steps / 120 s)" % (done, args.steps)},
+            "e2e": {"value": round(value, 4), "unit": "ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_fides(args, world, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

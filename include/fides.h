@@ -162,6 +162,27 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
  */
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
+/*
+ * Tracing (a profiling aid, not part of the method).  While enabled, every
+ * kernel launch and every public operation is bracketed by CUDA events on its
+ * stream.  fides_trace_read() waits for the recorded events and writes one
+ * entry per name (kernel names start with "k_", operations with "op_") in
+ * first-seen order to out[0..max); *n_out receives the number of names.
+ * `name` points to static storage.  fides_trace_reset() drops the records.
+ * fides_kernel_launches() counts every kernel launched by the library since
+ * it was loaded, traced or not.
+ */
+typedef struct {
+    const char *name;
+    uint64_t launches;
+    double total_ms;
+} fides_trace_stat;
+
+int fides_trace_enable(int on);
+void fides_trace_reset(void);
+int fides_trace_read(fides_trace_stat *out, int max, int *n_out);
+uint64_t fides_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -186,3 +186,25 @@ __device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
 // ---------------------------------------------------------------------------
 int fides_set_error(int code, const char *fmt, ...);
 int fides_check_cuda(cudaError_t e, const char *what);
+
+// tracing (trace.cu)
+int fides_trace_begin(const char *name, cudaStream_t st);
+void fides_trace_end(int id, cudaStream_t st);
+void fides_count_launch();
+
+// Launch a kernel: count it and, when tracing is on, bracket it with events.
+#define FIDES_LAUNCH(name, st, ...)                   \
+    do {                                              \
+        int fides_trace_id_ = fides_trace_begin(name, st); \
+        __VA_ARGS__;                                  \
+        fides_trace_end(fides_trace_id_, st);         \
+        fides_count_launch();                         \
+    } while (0)
+
+// Bracket a whole public operation with events when tracing is on.
+struct OpTrace {
+    int id;
+    cudaStream_t st;
+    OpTrace(const char *name, cudaStream_t s) : id(fides_trace_begin(name, s)), st(s) {}
+    ~OpTrace() { fides_trace_end(id, st); }
+};

@@ -104,9 +104,9 @@ int launch_bconv(const fides_ctx *c, const BConvArgs &A, int max_src, cudaStream
 {
     if (A.njob == 0) return FIDES_OK;
     dim3 grid(c->N / 256, A.njob), block(256);
-    if (max_src <= 8) k_bconv<8><<<grid, block, 0, st>>>(A, c->d_prime, c->logN);
-    else if (max_src <= 16) k_bconv<16><<<grid, block, 0, st>>>(A, c->d_prime, c->logN);
-    else k_bconv<32><<<grid, block, 0, st>>>(A, c->d_prime, c->logN);
+    if (max_src <= 8) FIDES_LAUNCH("k_bconv", st, k_bconv<8><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
+    else if (max_src <= 16) FIDES_LAUNCH("k_bconv", st, k_bconv<16><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
+    else FIDES_LAUNCH("k_bconv", st, k_bconv<32><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
     return fides_check_cuda(cudaGetLastError(), "bconv launch");
 }
 
@@ -309,7 +309,7 @@ int do_keyswitch(const fides_ctx *c, const u64 *d, int nl, const u64 *evk, u64 *
     int rc;
     if ((rc = do_modup(c, d, nl, s.ext, s, st))) return rc;
     dim3 grid(N / 256, ne);
-    k_inner<<<grid, 256, 0, st>>>(s.ext, beta, nl, ne, evk, c->L, c->L + K, s.acc, c->d_prime, c->logN);
+    FIDES_LAUNCH("k_inner", st, k_inner<<<grid, 256, 0, st>>>(s.ext, beta, nl, ne, evk, c->L, c->L + K, s.acc, c->d_prime, c->logN));
     if ((rc = fides_check_cuda(cudaGetLastError(), "inner product launch"))) return rc;
     const u64 *xs[2] = {s.acc, s.acc + (size_t)ne * N};
     u64 *outs[2] = {out0, out1};
@@ -391,6 +391,7 @@ extern "C" int fides_keyswitch(fides_ctx *c, const uint64_t *d, int nl, const ui
     if (int rc = check_ctx(c, "fides_keyswitch")) return rc;
     if (int rc = check_level(c, nl, "fides_keyswitch")) return rc;
     if (!d || !evk || !out0 || !out1) return fides_set_error(FIDES_ERR_ARG, "fides_keyswitch: NULL buffer");
+    OpTrace op("op_keyswitch", as_stream(stream));
     return do_keyswitch(c, d, nl, evk, out0, out1, 0, 0, carve(c), as_stream(stream));
 }
 
@@ -407,9 +408,10 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
                                out->n_limbs);
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
+    OpTrace op("op_hmult", st);
     Scratch s = carve(c);
-    k_tensor<<<dim3(c->N / 256, nl), 256, 0, st>>>(a->data, b->data, nl, out->data, out->data + S, s.dsrc,
-                                                    c->d_prime, c->logN);
+    FIDES_LAUNCH("k_tensor", st, k_tensor<<<dim3(c->N / 256, nl), 256, 0, st>>>(a->data, b->data, nl, out->data, out->data + S, s.dsrc,
+                                                    c->d_prime, c->logN));
     if (int rc = fides_check_cuda(cudaGetLastError(), "tensor launch")) return rc;
     int rc = do_keyswitch(c, s.dsrc, nl, rlk, out->data, out->data + S, 1, 1, s, st);
     if (!rc) out->scale = a->scale * b->scale;
@@ -426,10 +428,11 @@ extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, cons
     if (out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "fides_rotate: level mismatch");
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
+    OpTrace op("op_rotate", st);
     Scratch s = carve(c);
     const u64 g = fides_galois_elt(c, steps);
-    k_permute<<<c->N / 256, 256, 0, st>>>(a->data, out->data, nl, g, c->logN);
-    k_permute<<<c->N / 256, 256, 0, st>>>(a->data + S, s.dsrc, nl, g, c->logN);
+    FIDES_LAUNCH("k_permute", st, k_permute<<<c->N / 256, 256, 0, st>>>(a->data, out->data, nl, g, c->logN));
+    FIDES_LAUNCH("k_permute", st, k_permute<<<c->N / 256, 256, 0, st>>>(a->data + S, s.dsrc, nl, g, c->logN));
     if (int rc = fides_check_cuda(cudaGetLastError(), "permute launch")) return rc;
     int rc = do_keyswitch(c, s.dsrc, nl, rk, out->data, out->data + S, 1, 0, s, st);
     if (!rc) out->scale = a->scale;
@@ -447,6 +450,7 @@ extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, voi
     const int l = nl - 1;
     const size_t N = c->N, Sin = (size_t)nl * N, Sout = (size_t)l * N;
     cudaStream_t st = as_stream(stream);
+    OpTrace op("op_rescale", st);
     Scratch s = carve(c);
     int rc;
     LimbSet last = empty_set();

@@ -207,11 +207,11 @@ int ntt_forward(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaSt
     dim3 block(256);
     if (c->logN == 16) {
         dim3 grid(16, set.total);
-        k_ntt<16, 8, 0, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, EpiLazy{});
-        k_ntt<16, 8, 1, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, ProDst{}, epi);
+        FIDES_LAUNCH("k_ntt_fwd_cols", st, k_ntt<16, 8, 0, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, EpiLazy{}));
+        FIDES_LAUNCH("k_ntt_fwd_rows", st, k_ntt<16, 8, 1, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, ProDst{}, epi));
     } else {
         dim3 grid(1, set.total);
-        k_ntt<12, 12, 2, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, epi);
+        FIDES_LAUNCH("k_ntt_fwd_limb", st, k_ntt<12, 12, 2, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, epi));
     }
     return fides_check_cuda(cudaGetLastError(), "ntt forward launch");
 }
@@ -223,11 +223,11 @@ int ntt_inverse(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaSt
     dim3 block(256);
     if (c->logN == 16) {
         dim3 grid(16, set.total);
-        k_ntt<16, 8, 1, true, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, EpiLazy{});
-        k_ntt<16, 8, 0, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, ProDst{}, epi);
+        FIDES_LAUNCH("k_ntt_inv_rows", st, k_ntt<16, 8, 1, true, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, EpiLazy{}));
+        FIDES_LAUNCH("k_ntt_inv_cols", st, k_ntt<16, 8, 0, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, ProDst{}, epi));
     } else {
         dim3 grid(1, set.total);
-        k_ntt<12, 12, 2, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, epi);
+        FIDES_LAUNCH("k_ntt_inv_limb", st, k_ntt<12, 12, 2, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, epi));
     }
     return fides_check_cuda(cudaGetLastError(), "ntt inverse launch");
 }

@@ -24,13 +24,18 @@ ERRORS = {-1: "FIDES_ERR_ARG", -2: "FIDES_ERR_UNSUPPORTED", -3: "FIDES_ERR_NOMEM
 
 EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_create", "fides_ctx_destroy",
            "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
-           "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale"]
+           "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale",
+           "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches"]
 
 
 class FidesError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("%s (%d): %s" % (ERRORS.get(code, "FIDES_ERR"), code, msg))
         self.code = code
+
+
+class fides_trace_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
 
 class fides_ct(ctypes.Structure):
@@ -70,6 +75,10 @@ def lib():
         L.fides_hmult.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
         L.fides_rotate.argtypes = [_vp, ctp, ctypes.c_int64, _vp, ctp, _vp]
         L.fides_rescale.argtypes = [_vp, ctp, ctp, _vp]
+        L.fides_trace_enable.argtypes = [_i]
+        L.fides_trace_reset.restype = None
+        L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
+        L.fides_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -81,6 +90,29 @@ def _check(rc: int):
 
 def version() -> str:
     return lib().fides_version().decode()
+
+
+def trace_enable(on: bool = True):
+    """Bracket every kernel launch and public operation with CUDA events."""
+    _check(lib().fides_trace_enable(1 if on else 0))
+
+
+def trace_reset():
+    lib().fides_trace_reset()
+
+
+def trace_read() -> dict:
+    """{name: (launches, total_ms)} for everything traced since the last reset."""
+    n = ctypes.c_int(0)
+    _check(lib().fides_trace_read(None, 0, ctypes.byref(n)))
+    buf = (fides_trace_stat * max(1, n.value))()
+    _check(lib().fides_trace_read(buf, n.value, ctypes.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().fides_kernel_launches())
 
 
 def find_primes(logN: int, bits: int, count: int, exclude=()) -> list[int]:
