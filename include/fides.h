@@ -4,9 +4,9 @@
  * The engine implements the server-side hot path of CKKS described in
  * "FIDESlib: A Fully-Fledged Open-Source FHE Library for Efficient CKKS on
  * GPUs" (arXiv 2507.04775): the 64-bit negacyclic (i)NTT over RNS limbs
- * (Sec. III-E4), fast base conversion (Sec. III-E3, Eq. 1), ModUp / ModDown,
+ * (Sec. III-F4), fast base conversion (Sec. III-F3, Eq. 1), ModUp / ModDown,
  * the key inner product and hybrid key switching (Sec. II), HMult with
- * relinearisation, HRotate and Rescale (Table I; fusions of Sec. III-E5).
+ * relinearisation, HRotate and Rescale (Table I; fusions of Sec. III-F5).
  *
  * Conventions (all entry points)
  * ------------------------------
@@ -18,7 +18,7 @@
  *    q_{nl-1} followed by the K special primes p_0 .. p_{K-1}.
  *  - Evaluation ("NTT") form: word j of a limb holds a(psi^(2 brv(j) + 1)) mod
  *    q, psi = g^((q-1)/2N) with g the smallest generator of Z_q^*; i.e. the
- *    forward transform maps natural order to bit-reversed order (Sec. III-E4).
+ *    forward transform maps natural order to bit-reversed order (Sec. III-F4).
  *  - A ciphertext is two polynomials (c0, c1) stored back to back:
  *    [2][nl][N], evaluation form, decrypting to c0 + c1 s.
  *  - A switching key is [dnum][2][L + K][N] (component 0 = b, 1 = a),
@@ -80,7 +80,7 @@ int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, in
                       uint64_t *out);
 
 /*
- * Creates a context on the current CUDA device (Sec. III-D "Precomputation":
+ * Creates a context on the current CUDA device (Sec. III-E "Precomputation":
  * per-prime constants are computed once at context creation).
  *   logN   : ring degree N = 2^logN; this build supports logN in {12, 16}.
  *   L      : number of q-primes (maximum ciphertext limbs), 1 <= L.
@@ -102,7 +102,7 @@ uint64_t fides_ctx_psi(const fides_ctx *ctx, int prime_index);
 uint64_t fides_galois_elt(const fides_ctx *ctx, int64_t steps);
 
 /*
- * Forward / inverse negacyclic NTT (Sec. III-E4), in place, on `batch`
+ * Forward / inverse negacyclic NTT (Sec. III-F4), in place, on `batch`
  * polynomials of n_limbs limbs each stored back to back; limb z of every
  * polynomial uses prime index first_prime + z.  Forward: natural order in,
  * bit-reversed out.  Inverse: bit-reversed in, natural out, includes N^-1.
@@ -112,7 +112,7 @@ int fides_ntt(fides_ctx *ctx, uint64_t *dev, int first_prime, int n_limbs, int b
 int fides_intt(fides_ctx *ctx, uint64_t *dev, int first_prime, int n_limbs, int batch, void *stream);
 
 /*
- * ModUp (Sec. III-E3; Sec. II hybrid key switching): dev_d is an n_limbs-limb
+ * ModUp (Sec. III-F3; Sec. II hybrid key switching): dev_d is an n_limbs-limb
  * polynomial in evaluation form.  For each digit D_j, the limbs of D_j are
  * copied and every other prime of q_0..q_{n_limbs-1} and every special prime
  * is filled by fast base conversion (Eq. 1) of D_j in coefficient form
@@ -121,7 +121,7 @@ int fides_intt(fides_ctx *ctx, uint64_t *dev, int first_prime, int n_limbs, int 
 int fides_modup(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, uint64_t *dev_ext, void *stream);
 
 /*
- * ModDown (Sec. III-E3, Sec. III-E5 "ModDown fusion"): dev_x is an extended
+ * ModDown (Sec. III-F3, Sec. III-F5 "ModDown fusion"): dev_x is an extended
  * polynomial [n_limbs + K][N] in evaluation form; dev_out [n_limbs][N]
  * receives P^-1 (x_i - NTT(Conv_{P->Q}(INTT(x_P))))_i mod q_i (floor, no
  * rounding offset).
@@ -131,7 +131,7 @@ int fides_moddown(fides_ctx *ctx, const uint64_t *dev_x, int n_limbs, uint64_t *
 /*
  * Hybrid key switching of one polynomial d (n_limbs limbs, evaluation form)
  * with key dev_evk ([dnum][2][L+K][N]): ModUp, key inner product
- * acc_t = sum_j d~_j evk_{j,t} (Sec. III-E5 "Dot product fusion"), ModDown of
+ * acc_t = sum_j d~_j evk_{j,t} (Sec. III-F5 "Dot product fusion"), ModDown of
  * both accumulators.  Output (dev_out0, dev_out1), each [n_limbs][N], with
  * out0 + out1 s ~= d s'.
  */
@@ -155,7 +155,7 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
                  fides_ct *out, void *stream);
 
 /*
- * Rescale (Table I, Sec. III-E5 "Rescale fusion"): drops the last limb q_l,
+ * Rescale (Table I, Sec. III-F5 "Rescale fusion"): drops the last limb q_l,
  * l = a->n_limbs - 1 >= 1: out_i = q_l^-1 (x_i - NTT_{q_i}([INTT(x_l)]_{q_i}))
  * mod q_i, which is floor(x / q_l) limb-wise.  out->n_limbs must equal
  * a->n_limbs - 1; out->scale = a->scale / q_l.  out may not alias a.

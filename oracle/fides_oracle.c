@@ -31,7 +31,7 @@ typedef int64_t i64;
 typedef unsigned __int128 u128;
 
 /* ------------------------------------------------------------------------
- * Modular arithmetic by definition (Sec. III-E2 "Modular arithmetic": the
+ * Modular arithmetic by definition (Sec. III-F2 "Modular arithmetic": the
  * result of a product must be brought back to [0, p); here with a plain %).
  * ---------------------------------------------------------------------- */
 static u64 mul_mod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
@@ -150,7 +150,7 @@ static u64 brv(u64 x, int bits)
 
 /* ------------------------------------------------------------------------
  * Context: the primes and the per-prime constants the definitions need
- * (Sec. III-D "Precomputation" lists the same kind of values).
+ * (Sec. III-E "Precomputation" lists the same kind of values).
  * ---------------------------------------------------------------------- */
 typedef struct {
     int logN;
@@ -214,7 +214,7 @@ int or_ctx_alpha(const or_ctx *c) { return c->alpha; }
 static int ext_prime(const or_ctx *c, int nl, int z) { return z < nl ? z : c->nq + (z - nl); }
 
 /* ------------------------------------------------------------------------
- * NTT (Sec. III-E4).  Evaluation slot j of a limb holds a(psi^(2 brv(j) + 1))
+ * NTT (Sec. III-F4).  Evaluation slot j of a limb holds a(psi^(2 brv(j) + 1))
  * (forward output in bit-reversed order, inverse input in bit-reversed order).
  * ---------------------------------------------------------------------- */
 
@@ -252,7 +252,7 @@ void or_intt_naive(const or_ctx *c, int pi, const u64 *A, u64 *out)
 
 /*
  * Textbook radix-2 negacyclic NTT, in place: Cooley-Tukey butterflies,
- * natural-order input, bit-reversed output (Sec. III-E4).  Stage m has m
+ * natural-order input, bit-reversed output (Sec. III-F4).  Stage m has m
  * blocks of 2t elements; block i uses twiddle psi^brv(m + i).
  */
 void or_ntt(const or_ctx *c, int pi, u64 *a)
@@ -275,7 +275,7 @@ void or_ntt(const or_ctx *c, int pi, u64 *a)
 
 /*
  * Textbook radix-2 inverse: Gentleman-Sande butterflies, bit-reversed input,
- * natural-order output, then the N^-1 scaling (Sec. III-E4).  Each stage undoes
+ * natural-order output, then the N^-1 scaling (Sec. III-F4).  Each stage undoes
  * the forward stage with the same (m, i): (U, V) <- (U + V, (U - V) psi^-brv(m+i)).
  */
 void or_intt(const or_ctx *c, int pi, u64 *a)
@@ -311,7 +311,7 @@ void or_intt_limbs(const or_ctx *c, u64 *a, const int *pidx, int n)
 }
 
 /* ------------------------------------------------------------------------
- * Fast base conversion, Eq. (1) (Sec. III-E3): for every target prime p,
+ * Fast base conversion, Eq. (1) (Sec. III-F3): for every target prime p,
  *   y_p = ( sum_i [x_i * qhat_i^-1]_{q_i} * [qhat_i]_p ) mod p,
  * qhat_i = prod_{k != i} q_k over the source base.  Coefficient domain.
  * ---------------------------------------------------------------------- */
@@ -354,7 +354,7 @@ void or_bconv(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
 int or_beta(const or_ctx *c, int nl) { return (nl + c->alpha - 1) / c->alpha; }
 
 /*
- * ModUp (Sec. III-E3, Sec. II hybrid key switching): bring d (nl limbs,
+ * ModUp (Sec. III-F3, Sec. II hybrid key switching): bring d (nl limbs,
  * evaluation form) to coefficient form; for each digit D_j (contiguous blocks
  * of alpha limbs from limb 0, the last one partial) convert D_j to every other
  * prime of Q_l and to every special prime, then NTT the new limbs.  The limbs
@@ -395,7 +395,7 @@ void or_modup(const or_ctx *c, const u64 *d, int nl, u64 *ext)
 }
 
 /*
- * ModDown (Sec. III-E3 and the "ModDown fusion" item of Sec. III-E5):
+ * ModDown (Sec. III-F3 and the "ModDown fusion" item of Sec. III-F5):
  * x has nl q-limbs then K p-limbs, evaluation form.  INTT the p-limbs,
  * base-convert P -> Q_l, NTT, and return P^-1 (x_i - conv_i) mod q_i.
  * (Floor semantics: no rounding offset is added.)
@@ -427,7 +427,7 @@ void or_moddown(const or_ctx *c, const u64 *x, int nl, u64 *out)
 }
 
 /*
- * Hybrid key switching (Sec. II, Sec. III-E3): ModUp, key inner product
+ * Hybrid key switching (Sec. II, Sec. III-F3): ModUp, key inner product
  * acc_t = sum_j d~_j * evk_{j,t} over Q_l and P, then ModDown of each
  * accumulator.  evk: [dnum][2][nq + K][N] (component 0 = b, 1 = a), stored
  * at the full level; at nl limbs the q-limbs 0..nl-1 and the K p-limbs are used.
@@ -460,7 +460,7 @@ void or_keyswitch(const or_ctx *c, const u64 *d, int nl, const u64 *evk, u64 *ou
 }
 
 /*
- * HMult with relinearisation (Table I; Sec. III-E5 "HMult fusion" names the
+ * HMult with relinearisation (Table I; Sec. III-F5 "HMult fusion" names the
  * same three tensor products): d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1,
  * then (d0, d1) + KeySwitch(d2) with the relinearisation key.
  * a, b, out: [2][nl][N] evaluation form.
@@ -494,7 +494,7 @@ void or_hmult(const or_ctx *c, const u64 *a, const u64 *b, int nl, const u64 *rl
 }
 
 /* ------------------------------------------------------------------------
- * Automorphism X -> X^g (Sec. III-E1: a dependency within one limb; Table I
+ * Automorphism X -> X^g (Sec. III-F1: a dependency within one limb; Table I
  * HRotate/Conjugate).  Rotation by k slots uses g = 5^k mod 2N (negative k
  * taken modulo N/2, the order of 5); conjugation uses g = 2N - 1.
  * ---------------------------------------------------------------------- */
@@ -551,7 +551,7 @@ void or_rotate(const or_ctx *c, const u64 *a, int nl, i64 steps, const u64 *rk, 
 }
 
 /*
- * Rescale (Table I; Sec. III-E5 "Rescale fusion"): with l = nl - 1, INTT limb
+ * Rescale (Table I; Sec. III-F5 "Rescale fusion"): with l = nl - 1, INTT limb
  * l, take its canonical [0, q_l) representative modulo each q_i (SwitchModulo),
  * NTT under q_i, and return q_l^-1 (x_i - that) mod q_i for i < l.
  * a: [2][nl][N] -> out: [2][nl-1][N].

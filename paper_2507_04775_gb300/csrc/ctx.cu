@@ -1,5 +1,5 @@
 // Context creation: validates the primes, finds psi for each of them and
-// precomputes every per-prime table the kernels read (Sec. III-D
+// precomputes every per-prime table the kernels read (Sec. III-E
 // "Precomputation": constants are computed once, when the context is built).
 // Unlike the paper's singleton, every context owns its device tables, so
 // several parameter sets can live in one process.

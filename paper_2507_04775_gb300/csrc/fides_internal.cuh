@@ -1,7 +1,7 @@
 // Internal definitions of the GB300 CKKS key-switching engine: context layout,
 // per-prime constants, job descriptors and 64-bit modular arithmetic.
 //
-// Modular arithmetic (Sec. III-E2 and its Table "mod_red"):
+// Modular arithmetic (Sec. III-F2 and its Table "mod_red"):
 //   - Shoup multiplication by a fixed operand w with companion
 //     w' = floor(w * 2^64 / q): one high and two low 64-bit products, result in
 //     [0, 2q) for any 64-bit input (used for twiddles and per-prime constants).

@@ -1,6 +1,6 @@
 // Hybrid key switching and the CKKS operations built on it, for sm_103a:
-// fast base conversion (Sec. III-E3, Eq. 1), ModUp, the key inner product
-// (Sec. III-E5 "Dot product fusion"), ModDown, HMult + relinearisation,
+// fast base conversion (Sec. III-F3, Eq. 1), ModUp, the key inner product
+// (Sec. III-F5 "Dot product fusion"), ModDown, HMult + relinearisation,
 // HRotate and Rescale (Table I), and the C ABI entry points for them.
 #include <algorithm>
 #include <cstring>
@@ -15,7 +15,7 @@ namespace {
 //   y_p[n] = ( sum_i [x_i[n] * qhat_i^-1]_{q_i} * [qhat_i]_p ) mod p.
 // One thread per coefficient: the scaled source values stay in registers and
 // are reused for every target; the partial dot products accumulate in 128
-// bits and are reduced once per output (Sec. III-E3: lazy 128-bit
+// bits and are reduced once per output (Sec. III-F3: lazy 128-bit
 // accumulation, one reduction before the write-back).  The conversion matrix
 // of the targets is staged in shared memory (every thread reads the same entry).
 // ---------------------------------------------------------------------------
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_tensor(const u64 *__restrict__ a, const
     d2[o] = mul_mod(a1, b1, pr);
 }
 
-// Automorphism sigma_g in evaluation form (Sec. III-E1: a dependency within
+// Automorphism sigma_g in evaluation form (Sec. III-F1: a dependency within
 // one limb): out[j] = in[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)].
 __global__ void __launch_bounds__(256) k_permute(const u64 *__restrict__ in, u64 *__restrict__ out,
                                                  int n_limbs, u64 g, int logN)

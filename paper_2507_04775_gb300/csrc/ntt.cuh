@@ -1,4 +1,4 @@
-// Negacyclic NTT engine for sm_103a (Sec. III-E4).
+// Negacyclic NTT engine for sm_103a (Sec. III-F4).
 //
 // Convention: slot j of a limb holds a(psi^(2 brv(j) + 1)); the forward
 // transform uses Cooley-Tukey butterflies (natural in, bit-reversed out) and
@@ -24,7 +24,7 @@
 // Arithmetic is lazy: values stay in [0, 2q) between butterflies (primes are
 // below 2^61, so 4q fits in 64 bits); each butterfly costs one Shoup product.
 // Prologue and epilogue functors let callers fuse element-wise work into the
-// first load and the last store (Sec. III-E5 "Operation Fusions").
+// first load and the last store (Sec. III-F5 "Operation Fusions").
 #pragma once
 
 #include "fides_internal.cuh"
@@ -76,7 +76,7 @@ struct EpiCanon {
     }
 };
 // out = c_i (aux - v) mod q_i, or out += that when the segment's mode is 1
-// (ModDown with c = P^-1, Rescale with c = q_l^-1; Sec. III-E5).
+// (ModDown with c = P^-1, Rescale with c = q_l^-1; Sec. III-F5).
 struct EpiSubMul {
     const TwPair *cst;
     __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
