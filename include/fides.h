@@ -163,6 +163,27 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
 /*
+ * Rescale that allocates nothing.  The paper has no counterpart: this entry
+ * point serves callers that cannot allocate device memory when they call it
+ * (a host application that owns every device allocation and hands the library
+ * fixed buffers, or a service that reserves all device memory at start-up).
+ * It computes exactly what fides_rescale computes, with the same arguments and
+ * rules, but its scratch (2 * N words) lives in a static device array of
+ * FIDES_NOALLOC_SCRATCH_WORDS = 2 * 65536 words (1 MiB) instead of the
+ * context's pool; every GPU that loads the library holds that array until the
+ * process exits.  The caller passes the inputs and outputs.
+ *   - N above 65536 is rejected with FIDES_ERR_UNSUPPORTED.
+ *   - The context's device must be current (FIDES_ERR_ARG otherwise).
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Every call shares the one array, which keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race on it.  Each call writes every scratch word before reading it.
+ */
+int fides_rescale_noalloc(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
+
+/*
  * Tracing (a profiling aid, not part of the method).  While enabled, every
  * kernel launch and every public operation is bracketed by CUDA events on its
  * stream.  fides_trace_read() waits for the recorded events and writes one

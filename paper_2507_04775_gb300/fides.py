@@ -25,7 +25,8 @@ ERRORS = {-1: "FIDES_ERR_ARG", -2: "FIDES_ERR_UNSUPPORTED", -3: "FIDES_ERR_NOMEM
 EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_create", "fides_ctx_destroy",
            "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
            "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale",
-           "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches"]
+           "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches",
+           "fides_rescale_noalloc"]
 
 
 class FidesError(RuntimeError):
@@ -75,6 +76,7 @@ def lib():
         L.fides_hmult.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
         L.fides_rotate.argtypes = [_vp, ctp, ctypes.c_int64, _vp, ctp, _vp]
         L.fides_rescale.argtypes = [_vp, ctp, ctp, _vp]
+        L.fides_rescale_noalloc.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_trace_enable.argtypes = [_i]
         L.fides_trace_reset.restype = None
         L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
@@ -230,4 +232,11 @@ class Context:
     def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
         _check(lib().fides_rescale(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def rescale_noalloc(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        """Rescale whose scratch is a static device array (no allocation);
+        see fides_rescale_noalloc in include/fides.h."""
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
+        _check(lib().fides_rescale_noalloc(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
         return co.scale
