@@ -112,8 +112,12 @@ struct fides_ctx {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
 
-// a >= m ? a - m : a
-__device__ __forceinline__ u64 csub(u64 a, u64 m) { return a >= m ? a - m : a; }
+// a >= m ? a - m : a, for a, m < 2^63 (the sign of a - m decides)
+__device__ __forceinline__ u64 csub(u64 a, u64 m)
+{
+    const long long d = (long long)(a - m);
+    return d < 0 ? a : (u64)d;
+}
 
 // a * w mod q in [0, 2q) for any 64-bit a (Shoup).
 __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wp, u64 q)

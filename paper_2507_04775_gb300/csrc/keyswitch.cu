@@ -13,11 +13,14 @@ namespace {
 // ---------------------------------------------------------------------------
 // Fast base conversion (Eq. 1): for every target prime p and coefficient n,
 //   y_p[n] = ( sum_i [x_i[n] * qhat_i^-1]_{q_i} * [qhat_i]_p ) mod p.
-// One thread per coefficient: the scaled source values stay in registers and
-// are reused for every target; the partial dot products accumulate in 128
-// bits and are reduced once per output (Sec. III-F3: lazy 128-bit
-// accumulation, one reduction before the write-back).  The conversion matrix
-// of the targets is staged in shared memory (every thread reads the same entry).
+// One thread per coefficient and per group of up to BCONV_TG targets: the
+// scaled source values stay in registers and are reused for every target of
+// the group; the partial dot products accumulate in 128 bits (four 32-bit
+// words, one carry chain per partial product) and are reduced once per output
+// (Sec. III-F3: lazy 128-bit accumulation, one reduction before the
+// write-back).  The conversion matrix of the group is staged in shared memory
+// (every thread reads the same entry).  NS is the exact number of source limbs
+// (0: any number up to FIDES_MAX_SRC, with guarded loops).
 // ---------------------------------------------------------------------------
 struct BConvRun {
     u64 *dst;
@@ -41,25 +44,54 @@ struct BConvArgs {
     BConvJob job[FIDES_MAX_DIGITS];
 };
 
-constexpr int BCONV_MAX_DST = FIDES_MAX_PRIMES;
+constexpr int BCONV_TG = 16;     // targets per CTA
 
-template <int MAXS>
+struct Acc128 {
+    u32 w0, w1, w2, w3;
+};
+
+// c += a * b for 64-bit a, b (the full 128-bit product), as three carry chains
+// of 32-bit multiply-adds.
+__device__ __forceinline__ void mac_wide(Acc128 &c, u64 a, u64 b)
+{
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(c.w0), "+r"(c.w1), "+r"(c.w2), "+r"(c.w3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ u64 reduce_acc(const Acc128 &c, const PrimeInfo &p)
+{
+    return reduce128(((u64)c.w3 << 32) | c.w2, ((u64)c.w1 << 32) | c.w0, p);
+}
+
+template <int NS>
 __global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__restrict__ P, int logN)
 {
+    constexpr int MS = NS > 0 ? NS : FIDES_MAX_SRC;
     const BConvJob &B = A.job[blockIdx.y];
-    __shared__ u64 smat[BCONV_MAX_DST * MAXS];
-    __shared__ PrimeInfo sp[BCONV_MAX_DST];
-    __shared__ u64 *sdst[BCONV_MAX_DST];
-    __shared__ int ndst;
+    __shared__ u64 smat[BCONV_TG * MS];
+    __shared__ PrimeInfo sp[BCONV_TG];
+    __shared__ u64 *sdst[BCONV_TG];
     const int N = 1 << logN;
+    const int ns = NS > 0 ? NS : B.n_src;
 
-    if (threadIdx.x == 0) {
-        int nd = 0;
-        for (int r = 0; r < B.nrun; ++r) nd += B.run[r].count;
-        ndst = nd;
-    }
-    for (int d = threadIdx.x; d < BCONV_MAX_DST; d += blockDim.x) {
-        int rem = d, pz = -1;
+    int ndst = 0;
+    for (int r = 0; r < B.nrun; ++r) ndst += B.run[r].count;
+    const int d0 = blockIdx.z * BCONV_TG;
+    const int nd = min(BCONV_TG, ndst - d0);
+    if (nd <= 0) return;
+    if (threadIdx.x < nd) {
+        int rem = d0 + threadIdx.x, pz = 0;
         u64 *ptr = nullptr;
         for (int r = 0; r < B.nrun; ++r) {
             if (rem < B.run[r].count) {
@@ -69,19 +101,17 @@ __global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__r
             }
             rem -= B.run[r].count;
         }
-        if (pz >= 0) {
-            sp[d] = P[pz];
-            sdst[d] = ptr;
-            for (int i = 0; i < B.n_src; ++i) smat[d * MAXS + i] = B.mat[(size_t)i * B.ld + pz];
-        }
+        sp[threadIdx.x] = P[pz];
+        sdst[threadIdx.x] = ptr;
+        for (int i = 0; i < ns; ++i) smat[threadIdx.x * MS + i] = B.mat[(size_t)i * B.ld + pz];
     }
     __syncthreads();
 
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    u64 v[MAXS];
+    u64 v[MS];
 #pragma unroll
-    for (int i = 0; i < MAXS; ++i) {
-        if (i < B.n_src) {
+    for (int i = 0; i < MS; ++i) {
+        if (NS > 0 || i < ns) {
             const u64 qi = P[B.src_prime0 + i].q;
             const u64 x = B.src[(size_t)i * N + n];
             v[i] = csub(mul_shoup(x, B.scale[i], qi), qi);
@@ -89,25 +119,75 @@ __global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__r
             v[i] = 0;
         }
     }
-    const int nd = ndst;
-    for (int d = 0; d < nd; ++d) {
-        U128 acc = {0, 0};
-        const u64 *m = smat + d * MAXS;
+    int d = 0;
+    for (; d + 1 < nd; d += 2) {
+        Acc128 c0 = {0, 0, 0, 0}, c1 = {0, 0, 0, 0};
+        const u64 *m0 = smat + d * MS, *m1 = m0 + MS;
 #pragma unroll
-        for (int i = 0; i < MAXS; ++i)
-            if (i < B.n_src) mac128(acc, v[i], m[i]);
-        sdst[d][n] = reduce128(acc.hi, acc.lo, sp[d]);
+        for (int i = 0; i < MS; ++i) {
+            if (NS > 0 || i < ns) {
+                mac_wide(c0, v[i], m0[i]);
+                mac_wide(c1, v[i], m1[i]);
+            }
+        }
+        sdst[d][n] = reduce_acc(c0, sp[d]);
+        sdst[d + 1][n] = reduce_acc(c1, sp[d + 1]);
+    }
+    if (d < nd) {
+        Acc128 c0 = {0, 0, 0, 0};
+        const u64 *m0 = smat + d * MS;
+#pragma unroll
+        for (int i = 0; i < MS; ++i)
+            if (NS > 0 || i < ns) mac_wide(c0, v[i], m0[i]);
+        sdst[d][n] = reduce_acc(c0, sp[d]);
     }
 }
 
-int launch_bconv(const fides_ctx *c, const BConvArgs &A, int max_src, cudaStream_t st)
+template <int NS>
+void launch_bconv_ns(const fides_ctx *c, const BConvArgs &A, int max_dst, cudaStream_t st)
+{
+    dim3 grid(c->N / 256, A.njob, (max_dst + BCONV_TG - 1) / BCONV_TG), block(256);
+    FIDES_LAUNCH("k_bconv", st, k_bconv<NS><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
+}
+
+// Launches one conversion per distinct source count (a ragged last digit
+// gets its own launch, so every launch runs fully unrolled loops).
+int launch_bconv(const fides_ctx *c, const BConvArgs &A, int /*max_src*/, cudaStream_t st)
 {
     if (A.njob == 0) return FIDES_OK;
-    dim3 grid(c->N / 256, A.njob), block(256);
-    if (max_src <= 8) FIDES_LAUNCH("k_bconv", st, k_bconv<8><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
-    else if (max_src <= 16) FIDES_LAUNCH("k_bconv", st, k_bconv<16><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
-    else FIDES_LAUNCH("k_bconv", st, k_bconv<32><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
-    return fides_check_cuda(cudaGetLastError(), "bconv launch");
+    bool done[FIDES_MAX_DIGITS] = {false};
+    for (int j = 0; j < A.njob; ++j) {
+        if (done[j]) continue;
+        const int ns = A.job[j].n_src;
+        BConvArgs G;
+        memset(&G, 0, sizeof(G));
+        int max_dst = 0;
+        for (int k = j; k < A.njob; ++k) {
+            if (done[k] || A.job[k].n_src != ns) continue;
+            done[k] = true;
+            G.job[G.njob++] = A.job[k];
+            int nd = 0;
+            for (int r = 0; r < A.job[k].nrun; ++r) nd += A.job[k].run[r].count;
+            max_dst = std::max(max_dst, nd);
+        }
+        switch (ns) {
+        case 1: launch_bconv_ns<1>(c, G, max_dst, st); break;
+        case 2: launch_bconv_ns<2>(c, G, max_dst, st); break;
+        case 3: launch_bconv_ns<3>(c, G, max_dst, st); break;
+        case 4: launch_bconv_ns<4>(c, G, max_dst, st); break;
+        case 5: launch_bconv_ns<5>(c, G, max_dst, st); break;
+        case 6: launch_bconv_ns<6>(c, G, max_dst, st); break;
+        case 7: launch_bconv_ns<7>(c, G, max_dst, st); break;
+        case 8: launch_bconv_ns<8>(c, G, max_dst, st); break;
+        case 9: launch_bconv_ns<9>(c, G, max_dst, st); break;
+        case 10: launch_bconv_ns<10>(c, G, max_dst, st); break;
+        case 11: launch_bconv_ns<11>(c, G, max_dst, st); break;
+        case 12: launch_bconv_ns<12>(c, G, max_dst, st); break;
+        default: launch_bconv_ns<0>(c, G, max_dst, st); break;
+        }
+        if (int rc = fides_check_cuda(cudaGetLastError(), "bconv launch")) return rc;
+    }
+    return FIDES_OK;
 }
 
 // ---------------------------------------------------------------------------

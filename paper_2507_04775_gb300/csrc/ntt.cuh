@@ -19,12 +19,23 @@
 // shared memory (k-major for columns, XOR-swizzled rows otherwise, both free
 // of bank conflicts).  Loads and stores are coalesced: where the thread-to-
 // element map of the first/last round is strided, the tile is staged through
-// shared memory instead.
+// shared memory instead.  The column pass reads its 255 twiddles (shared by
+// every column) from shared memory; the row pass reads per-row twiddles
+// through L1.
 //
-// Arithmetic is lazy: values stay in [0, 2q) between butterflies (primes are
-// below 2^61, so 4q fits in 64 bits); each butterfly costs one Shoup product.
+// Twiddle index of a butterfly.  In round rho (bit offset b of the round's four
+// bits in the local index k) the thread's elements are k(r) = X' | r << b | low
+// bits, and the forward stage s = S0 + 4 rho + a of the lower element r uses
+// index 2^s + (X << a) + (r >> (4 - a)); the inverse stage s = S0 + S - 1 -
+// 4 rho - a uses 2^s + (X << (3 - a)) + (r >> (a + 1)).  X collects the bits of
+// the global index above the round's bits (the row for row passes).
+//
+// Arithmetic is lazy (Harvey): forward values stay in [0, 4q) between
+// stages, inverse values in [0, 2q); primes are below 2^61, so 4q < 2^63.
+// Each butterfly costs one Shoup product and one conditional subtraction.
 // Prologue and epilogue functors let callers fuse element-wise work into the
-// first load and the last store (Sec. III-F5 "Operation Fusions").
+// first load and the last store (Sec. III-F5 "Operation Fusions"); epilogues
+// receive values in [0, 2q).
 #pragma once
 
 #include "fides_internal.cuh"
@@ -35,14 +46,16 @@ __device__ __forceinline__ int kmap(int u, int r, int b)
     return ((u >> b) << (b + 4)) | (r << b) | (u & ((1 << b) - 1));
 }
 
+// Forward butterfly: x, y in [0, 4q) -> x + w y, x - w y in [0, 4q).
 __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, u64 q2)
 {
-    u64 t = mul_shoup(y, w, q);          // [0, 2q)
-    u64 a = x;                            // [0, 2q)
-    x = csub(a + t, q2);
-    y = csub(a + q2 - t, q2);
+    u64 a = csub(x, q2);                  // [0, 2q)
+    u64 t = mul_shoup(y, w, q);           // [0, 2q)
+    x = a + t;
+    y = a + q2 - t;
 }
 
+// Inverse butterfly: x, y in [0, 2q) -> x + y, (x - y) w in [0, 2q).
 __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, u64 q2)
 {
     u64 a = x, b = y;
@@ -88,32 +101,62 @@ struct EpiSubMul {
     }
 };
 
-// KIND: 0 = column pass (16 strided columns), 1 = row pass (16 rows),
+// One round of four radix-2 stages on the thread's 16 registers.
+// X: the global-index bits above the round (see the header comment);
+// TWS: twiddles come from shared memory (index < 256) instead of global.
+template <bool INV, int S0, int S, int RHO, bool TWS>
+__device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__restrict__ tw,
+                                          const TwPair *stw, u64 q, u64 q2)
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int s = INV ? S0 + S - 1 - 4 * RHO - a : S0 + 4 * RHO + a;
+        const int h = INV ? (1 << a) : (8 >> a);
+        const int base = (1 << s) + (INV ? (X << (3 - a)) : (X << a));
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (r & h) continue;
+            const int idx = base + (INV ? (r >> (a + 1)) : (r >> (4 - a)));
+            const TwPair w = TWS ? stw[idx] : tw[idx];
+            if (INV) gs_bfly(x[r], x[r + h], w, q, q2);
+            else ct_bfly(x[r], x[r + h], w, q, q2);
+        }
+    }
+}
+
+// KIND: 0 = column pass (16 strided columns, S = 8, stages 0..7 of logN=16),
+//       1 = row pass (16 rows, S = 8, stages 8..15 of logN=16),
 //       2 = whole limb (S == LOGN == 12).
 // INV selects Gentleman-Sande stages in reverse order; NINV multiplies by
 // N^-1 before the epilogue.
 template <int LOGN, int S, int KIND, bool INV, bool NINV, class Pro, class Epi>
-__global__ void __launch_bounds__(256) k_ntt(LimbSet set, const PrimeInfo *__restrict__ P,
-                                             const TwPair *__restrict__ TW, Pro pro, Epi epi)
+__global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__restrict__ P,
+                                                const TwPair *__restrict__ TW, Pro pro, Epi epi)
 {
     constexpr int C = 4096 >> S;                  // sub-transforms per tile
     constexpr int R = S / 4;                      // rounds of four stages
     constexpr int S0 = (KIND == 1) ? (LOGN - S) : 0;
     constexpr int SH = LOGN - S;                  // column stride shift
+    constexpr bool TWS = (KIND == 0);             // column twiddles staged in shared memory
     static_assert(S % 4 == 0 && C * (1 << S) == 4096, "tile shape");
+    static_assert(KIND != 1 || S == 8, "row pass handles rows of 256");
     __shared__ u64 sm[4096];
+    __shared__ TwPair stw[TWS ? 256 : 1];
 
     const int t = threadIdx.x;
     const Job J = get_job(set, blockIdx.y, 1 << LOGN);
     const PrimeInfo pr = P[J.prime];
     const TwPair *__restrict__ tw = TW + ((size_t)J.prime << LOGN);
     const u64 q = pr.q, q2 = pr.q2;
+    if (TWS) {
+        stw[t] = tw[t];
+    }
 
     int c, u;
     if (KIND == 0) { c = t % C; u = t / C; }
     else if (KIND == 1) { u = t & 15; c = t >> 4; }
     else { u = t; c = 0; }
-    const int cbase = (KIND == 2) ? 0 : (int)blockIdx.x * C + c;
+    const int cbase = (KIND == 2) ? 0 : (int)blockIdx.x * C + c;   // column (KIND 0) or row (KIND 1)
 
     auto gidx = [&](int cb, int k) -> u32 {
         if (KIND == 0) return (u32)(cb + (k << SH));
@@ -124,6 +167,8 @@ __global__ void __launch_bounds__(256) k_ntt(LimbSet set, const PrimeInfo *__res
         if (KIND == 0) return k * C + cc;
         return cc * (1 << S) + (k ^ ((k >> 4) & 15));
     };
+    // the global-index bits above round rho's four bits
+    auto Xof = [&](int b) -> int { return (KIND == 1 ? (cbase << (4 - b)) : 0) | (u >> b); };
 
     u64 x[16];
 
@@ -132,6 +177,7 @@ __global__ void __launch_bounds__(256) k_ntt(LimbSet set, const PrimeInfo *__res
         const int b0 = INV ? 0 : S - 4;
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = pro(J, gidx(cbase, kmap(u, r, b0)), pr);
+        if (TWS) __syncthreads();
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -146,34 +192,28 @@ __global__ void __launch_bounds__(256) k_ntt(LimbSet set, const PrimeInfo *__res
     }
 
     // ---------------- rounds ----------------
-#pragma unroll
-    for (int rho = 0; rho < R; ++rho) {
-        const int b = INV ? 4 * rho : S - 4 - 4 * rho;
-        if (rho > 0) {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, b))];
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int s = INV ? S0 + S - 1 - (4 * rho + a) : S0 + 4 * rho + a;
-            const int h = INV ? (1 << a) : (8 >> a);
-#pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                if (r & h) continue;
-                const u32 j = gidx(cbase, kmap(u, r, b));
-                const TwPair w = tw[(1u << s) + (j >> (LOGN - s))];
-                if (INV) gs_bfly(x[r], x[r + h], w, q, q2);
-                else ct_bfly(x[r], x[r + h], w, q, q2);
-            }
-        }
-        if (rho < R - 1) {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, b))] = x[r];
-            __syncthreads();
-        }
+#define FIDES_NTT_ROUND(RHO)                                                                 \
+    if (RHO < R) {                                                                           \
+        const int b = INV ? 4 * RHO : S - 4 - 4 * RHO;                                       \
+        if (RHO > 0) {                                                                       \
+            _Pragma("unroll") for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, b))]; \
+        }                                                                                    \
+        ntt_round<INV, S0, S, (RHO < R ? RHO : 0), TWS>(x, Xof(b), tw, stw, q, q2);          \
+        if (RHO < R - 1) {                                                                   \
+            _Pragma("unroll") for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, b))] = x[r]; \
+            __syncthreads();                                                                 \
+        }                                                                                    \
     }
+    FIDES_NTT_ROUND(0)
+    FIDES_NTT_ROUND(1)
+    FIDES_NTT_ROUND(2)
+#undef FIDES_NTT_ROUND
 
     // ---------------- store ----------------
+    if (!INV) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = csub(x[r], q2);      // [0, 4q) -> [0, 2q)
+    }
     if (NINV) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = mul_shoup(x[r], pr.ninv, pr.ninvp, q);
@@ -183,7 +223,7 @@ __global__ void __launch_bounds__(256) k_ntt(LimbSet set, const PrimeInfo *__res
 #pragma unroll
         for (int r = 0; r < 16; ++r) epi(J, gidx(cbase, kmap(u, r, bl)), x[r], pr);
     } else {
-        if (R > 1) __syncthreads();   // every thread has read its last-round inputs
+        __syncthreads();   // the last round's shared-memory reads are done
 #pragma unroll
         for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, 0))] = x[r];
         __syncthreads();
