@@ -199,6 +199,15 @@ typedef struct {
     double total_ms;
 } fides_trace_stat;
 
+/*
+ * Measured ALU roofline (a profiling aid): the sustained rate, in 10^9
+ * modular products per second, of the library's 64-bit Shoup product
+ * (Sec. III-F2) run register-resident on every SM of the current device.
+ * *ms_out (optional) receives the duration of one measurement launch.
+ * Allocates a small device buffer for the kernel's output and synchronises.
+ */
+int fides_measure_modmul_peak(double *gmodmul_per_s, double *ms_out);
+
 int fides_trace_enable(int on);
 void fides_trace_reset(void);
 int fides_trace_read(fides_trace_stat *out, int max, int *n_out);

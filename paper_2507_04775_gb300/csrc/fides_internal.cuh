@@ -16,6 +16,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "fides.h"
@@ -196,13 +197,42 @@ int fides_trace_begin(const char *name, cudaStream_t st);
 void fides_trace_end(int id, cudaStream_t st);
 void fides_count_launch();
 
-// Launch a kernel: count it and, when tracing is on, bracket it with events.
-#define FIDES_LAUNCH(name, st, ...)                   \
-    do {                                              \
-        int fides_trace_id_ = fides_trace_begin(name, st); \
-        __VA_ARGS__;                                  \
-        fides_trace_end(fides_trace_id_, st);         \
-        fides_count_launch();                         \
+// Programmatic dependent launch: every kernel of the library lets the next
+// kernel in its stream launch as soon as all of its CTAs are running, and waits
+// for the previous kernel to finish (and its memory to be visible) before it
+// reads anything.  The next kernel's CTAs thus occupy SMs freed during this
+// kernel's last wave instead of after a launch gap.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... Params, typename... Args>
+inline cudaError_t fides_launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, cudaStream_t st,
+                                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Launch a kernel (with programmatic dependent launch): count it and, when
+// tracing is on, bracket it with events.
+#define FIDES_LAUNCH(name, st, kern, grid, block, ...)                  \
+    do {                                                                \
+        int fides_trace_id_ = fides_trace_begin(name, st);              \
+        fides_launch_kernel(kern, grid, block, st, __VA_ARGS__);        \
+        fides_trace_end(fides_trace_id_, st);                           \
+        fides_count_launch();                                           \
     } while (0)
 
 // Bracket a whole public operation with events when tracing is on.

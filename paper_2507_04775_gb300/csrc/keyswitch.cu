@@ -78,6 +78,7 @@ template <int NS>
 __global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__restrict__ P, int logN)
 {
     constexpr int MS = NS > 0 ? NS : FIDES_MAX_SRC;
+    pdl_enter();
     const BConvJob &B = A.job[blockIdx.y];
     __shared__ u64 smat[BCONV_TG * MS];
     __shared__ PrimeInfo sp[BCONV_TG];
@@ -147,7 +148,7 @@ template <int NS>
 void launch_bconv_ns(const fides_ctx *c, const BConvArgs &A, int max_dst, cudaStream_t st)
 {
     dim3 grid(c->N / 256, A.njob, (max_dst + BCONV_TG - 1) / BCONV_TG), block(256);
-    FIDES_LAUNCH("k_bconv", st, k_bconv<NS><<<grid, block, 0, st>>>(A, c->d_prime, c->logN));
+    FIDES_LAUNCH("k_bconv", st, k_bconv<NS>, grid, block, A, c->d_prime, c->logN);
 }
 
 // Launches one conversion per distinct source count (a ragged last digit
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(256) k_inner(const u64 *__restrict__ ext, int 
                                                const u64 *__restrict__ evk, int L, int nfull,
                                                u64 *__restrict__ acc, const PrimeInfo *__restrict__ P, int logN)
 {
+    pdl_enter();
     const int N = 1 << logN;
     const int z = blockIdx.y;
     const int pz = z < nl ? z : L + (z - nl);
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(256) k_tensor(const u64 *__restrict__ a, const
                                                 u64 *__restrict__ d0, u64 *__restrict__ d1, u64 *__restrict__ d2,
                                                 const PrimeInfo *__restrict__ P, int logN)
 {
+    pdl_enter();
     const int N = 1 << logN;
     const int i = blockIdx.y;
     const PrimeInfo pr = P[i];
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(256) k_tensor(const u64 *__restrict__ a, const
 __global__ void __launch_bounds__(256) k_permute(const u64 *__restrict__ in, u64 *__restrict__ out,
                                                  int n_limbs, u64 g, int logN)
 {
+    pdl_enter();
     const int N = 1 << logN;
     const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 rj = __brev(j) >> (32 - logN);
@@ -389,7 +393,8 @@ int do_keyswitch(const fides_ctx *c, const u64 *d, int nl, const u64 *evk, u64 *
     int rc;
     if ((rc = do_modup(c, d, nl, s.ext, s, st))) return rc;
     dim3 grid(N / 256, ne);
-    FIDES_LAUNCH("k_inner", st, k_inner<<<grid, 256, 0, st>>>(s.ext, beta, nl, ne, evk, c->L, c->L + K, s.acc, c->d_prime, c->logN));
+    FIDES_LAUNCH("k_inner", st, k_inner, grid, dim3(256), (const u64 *)s.ext, beta, nl, ne, evk, c->L, c->L + K, s.acc,
+                 (const PrimeInfo *)c->d_prime, c->logN);
     if ((rc = fides_check_cuda(cudaGetLastError(), "inner product launch"))) return rc;
     const u64 *xs[2] = {s.acc, s.acc + (size_t)ne * N};
     u64 *outs[2] = {out0, out1};
@@ -490,8 +495,8 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult", st);
     Scratch s = carve(c);
-    FIDES_LAUNCH("k_tensor", st, k_tensor<<<dim3(c->N / 256, nl), 256, 0, st>>>(a->data, b->data, nl, out->data, out->data + S, s.dsrc,
-                                                    c->d_prime, c->logN));
+    FIDES_LAUNCH("k_tensor", st, k_tensor, dim3(c->N / 256, nl), dim3(256), (const u64 *)a->data, (const u64 *)b->data, nl,
+                 out->data, out->data + S, s.dsrc, (const PrimeInfo *)c->d_prime, c->logN);
     if (int rc = fides_check_cuda(cudaGetLastError(), "tensor launch")) return rc;
     int rc = do_keyswitch(c, s.dsrc, nl, rlk, out->data, out->data + S, 1, 1, s, st);
     if (!rc) out->scale = a->scale * b->scale;
@@ -511,8 +516,9 @@ extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, cons
     OpTrace op("op_rotate", st);
     Scratch s = carve(c);
     const u64 g = fides_galois_elt(c, steps);
-    FIDES_LAUNCH("k_permute", st, k_permute<<<c->N / 256, 256, 0, st>>>(a->data, out->data, nl, g, c->logN));
-    FIDES_LAUNCH("k_permute", st, k_permute<<<c->N / 256, 256, 0, st>>>(a->data + S, s.dsrc, nl, g, c->logN));
+    FIDES_LAUNCH("k_permute", st, k_permute, dim3(c->N / 256), dim3(256), (const u64 *)a->data, out->data, nl, g, c->logN);
+    FIDES_LAUNCH("k_permute", st, k_permute, dim3(c->N / 256), dim3(256), (const u64 *)(a->data + S), s.dsrc, nl, g,
+                 c->logN);
     if (int rc = fides_check_cuda(cudaGetLastError(), "permute launch")) return rc;
     int rc = do_keyswitch(c, s.dsrc, nl, rk, out->data, out->data + S, 1, 0, s, st);
     if (!rc) out->scale = a->scale;

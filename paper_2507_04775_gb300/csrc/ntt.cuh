@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
     __shared__ u64 sm[4096];
     __shared__ TwPair stw[TWS ? 256 : 1];
 
+    pdl_enter();
     const int t = threadIdx.x;
     const Job J = get_job(set, blockIdx.y, 1 << LOGN);
     const PrimeInfo pr = P[J.prime];
@@ -247,11 +248,14 @@ int ntt_forward(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaSt
     dim3 block(256);
     if (c->logN == 16) {
         dim3 grid(16, set.total);
-        FIDES_LAUNCH("k_ntt_fwd_cols", st, k_ntt<16, 8, 0, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, EpiLazy{}));
-        FIDES_LAUNCH("k_ntt_fwd_rows", st, k_ntt<16, 8, 1, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, ProDst{}, epi));
+        auto k1 = k_ntt<16, 8, 0, false, false, Pro, EpiLazy>;
+        auto k2 = k_ntt<16, 8, 1, false, false, ProDst, Epi>;
+        FIDES_LAUNCH("k_ntt_fwd_cols", st, k1, grid, block, set, c->d_prime, c->d_tw, pro, EpiLazy{});
+        FIDES_LAUNCH("k_ntt_fwd_rows", st, k2, grid, block, set, c->d_prime, c->d_tw, ProDst{}, epi);
     } else {
         dim3 grid(1, set.total);
-        FIDES_LAUNCH("k_ntt_fwd_limb", st, k_ntt<12, 12, 2, false, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_tw, pro, epi));
+        auto k1 = k_ntt<12, 12, 2, false, false, Pro, Epi>;
+        FIDES_LAUNCH("k_ntt_fwd_limb", st, k1, grid, block, set, c->d_prime, c->d_tw, pro, epi);
     }
     return fides_check_cuda(cudaGetLastError(), "ntt forward launch");
 }
@@ -263,11 +267,14 @@ int ntt_inverse(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaSt
     dim3 block(256);
     if (c->logN == 16) {
         dim3 grid(16, set.total);
-        FIDES_LAUNCH("k_ntt_inv_rows", st, k_ntt<16, 8, 1, true, false><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, EpiLazy{}));
-        FIDES_LAUNCH("k_ntt_inv_cols", st, k_ntt<16, 8, 0, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, ProDst{}, epi));
+        auto k1 = k_ntt<16, 8, 1, true, false, Pro, EpiLazy>;
+        auto k2 = k_ntt<16, 8, 0, true, true, ProDst, Epi>;
+        FIDES_LAUNCH("k_ntt_inv_rows", st, k1, grid, block, set, c->d_prime, c->d_itw, pro, EpiLazy{});
+        FIDES_LAUNCH("k_ntt_inv_cols", st, k2, grid, block, set, c->d_prime, c->d_itw, ProDst{}, epi);
     } else {
         dim3 grid(1, set.total);
-        FIDES_LAUNCH("k_ntt_inv_limb", st, k_ntt<12, 12, 2, true, true><<<grid, block, 0, st>>>(set, c->d_prime, c->d_itw, pro, epi));
+        auto k1 = k_ntt<12, 12, 2, true, true, Pro, Epi>;
+        FIDES_LAUNCH("k_ntt_inv_limb", st, k1, grid, block, set, c->d_prime, c->d_itw, pro, epi);
     }
     return fides_check_cuda(cudaGetLastError(), "ntt inverse launch");
 }

@@ -26,7 +26,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
            "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale",
            "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches",
-           "fides_rescale_noalloc"]
+           "fides_rescale_noalloc", "fides_measure_modmul_peak"]
 
 
 class FidesError(RuntimeError):
@@ -81,6 +81,7 @@ def lib():
         L.fides_trace_reset.restype = None
         L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
         L.fides_kernel_launches.restype = ctypes.c_uint64
+        L.fides_measure_modmul_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -110,6 +111,13 @@ def trace_read() -> dict:
     buf = (fides_trace_stat * max(1, n.value))()
     _check(lib().fides_trace_read(buf, n.value, ctypes.byref(n)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+
+def measure_modmul_peak() -> float:
+    """Sustained 10^9 Shoup products per second of the current device."""
+    g, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().fides_measure_modmul_peak(ctypes.byref(g), ctypes.byref(ms)))
+    return g.value
 
 
 def kernel_launches() -> int:
