@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 128-ciphertext batched workload")
+    ap.add_argument("--batch-ops", type=int, default=128)
     ap.add_argument("--small", action="store_true",
                     help="one ciphertext pair and two keys (for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -323,6 +325,11 @@ def run_fides(args, world, rank, local):
     roof["other_bound"] = alu if roof["bound"] == "hbm" else hbm
     roof["clock_mhz_median"] = clk
 
+    # ---------------- batched workload (many ciphertexts, uneven levels) ----------------
+    batched = None
+    if not args.no_batched and not args.small:
+        batched = run_batched(args, ctx, dA, dB, rlk, rks, P, scale)
+
     # ---------------- end to end through host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -343,6 +350,7 @@ def run_fides(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": ck,
         "e2e": e2e,
+        "batched": batched,
     }
     if mismatch:
         result["launch_model_mismatch"] = mismatch
@@ -351,6 +359,71 @@ def run_fides(args, world, rank, local):
     elif rank == 0:
         result["cpu_baseline"] = None
     return result
+
+
+def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
+    """128 ciphertext pairs at levels drawn uniformly from {4..30}; each pair
+    does HMult+relin then one HRotate (by a seeded power of two) of the
+    product.  The batch runs as one captured CUDA graph (one launch per key-
+    switch step per stage for the whole batch) and, for comparison, as one
+    library call per operation on the same buffers."""
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+    st = si.Stream(si.workload_seed(2), 1)
+    n = args.batch_ops
+    levels = [4 + st.below(27) for _ in range(n)]
+    rots = [st.below(N_ROT) for _ in range(n)]
+    N = ctx.N
+    ops, plain = [], []
+    for i, nl in enumerate(levels):
+        src_a, src_b = dA[i % POOL].view(2, P.nq, N), dB[i % POOL].view(2, P.nq, N)
+        a = src_a[:, :nl].contiguous().view(-1)
+        b = src_b[:, :nl].contiguous().view(-1)
+        m = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+        r = torch.empty_like(m)
+        ops.append(fides.Op(fides.OP_HMULT, a, nl, m, b=b, key=rlk, stage=0, scale_a=scale, scale_b=scale))
+        ops.append(fides.Op(fides.OP_ROTATE, m, nl, r, key=rks[rots[i]], steps=1 << rots[i], stage=1,
+                            scale_a=scale * scale))
+        plain.append((a, b, m, r, nl, rots[i]))
+    batch = fides.Batch(ctx, ops)
+    info = batch.info()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.capture(stream)
+        for _ in range(2):
+            batch.run(stream)
+        stream.synchronize()
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            batch.run(stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms_batch = e0.elapsed_time(e1) / reps
+
+        def plain_run():
+            for a, b, m, r, nl, k in plain:
+                ctx.hmult(a, b, nl, rlk, m, scale, scale, stream=stream)
+                ctx.rotate(m, nl, 1 << k, rks[k], r, scale * scale, stream=stream)
+        plain_run()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(2):
+            plain_run()
+        e1.record(stream)
+        stream.synchronize()
+        ms_plain = e0.elapsed_time(e1) / 2
+    batch.close()
+    nops = 2 * n
+    limbs = sum(levels)
+    return {"workload": "%d ciphertexts, levels uniform on {4..30} (mean %.1f limbs), HMult+relin then HRotate" % (n, limbs / n),
+            "ops": nops, "value": round(nops / (ms_batch / 1e3), 1), "unit": "ops/s",
+            "ms_per_batch": round(ms_batch, 3), "plain_value": round(nops / (ms_plain / 1e3), 1),
+            "plain_ms": round(ms_plain, 3), "speedup": round(ms_plain / ms_batch, 3),
+            "graph": True, "kernels_per_batch": info["launches"],
+            "kernels_plain": n * 25, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2)}
 
 
 def load_traffic(kernel, bytes_per_launch):

@@ -163,6 +163,50 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
 /*
+ * Batched operations (Sec. III-F1 hides launch overhead with limb batching;
+ * here whole operations are batched).  A batch is a fixed list of HMult,
+ * HRotate and Rescale operations on ciphertexts at any levels; each op names
+ * its caller-owned input and output buffers, which must stay allocated and at
+ * the same addresses for the life of the batch.  Ops carry a stage number:
+ * every op of stage s runs after every op of stages < s and may read their
+ * outputs; ops of one stage must be independent (no op writes what another
+ * op of its stage reads or writes).
+ *
+ * fides_batch_create validates every op (FIDES_ERR_ARG naming the op on
+ * error), sets each op's out.scale, allocates the batch's own scratch (one
+ * key switch's worth per HMult/HRotate, two limbs per Rescale) and uploads
+ * device tables describing every launch; it synchronises.
+ * fides_batch_run enqueues the whole batch on `stream`: one launch per step
+ * of the key switch per stage, covering every op of the stage.  Results are
+ * identical to calling fides_hmult / fides_rotate / fides_rescale op by op.
+ * fides_batch_capture records one run into a CUDA graph (stream must not be
+ * NULL); later fides_batch_run calls launch that graph.
+ * fides_batch_info reports the kernels one run launches and the device bytes
+ * the batch owns.  Runs of one batch must not overlap on the GPU.
+ */
+#define FIDES_OP_HMULT 1    /* out = HMult+relin(a, b) with key = relinearisation key */
+#define FIDES_OP_ROTATE 2   /* out = HRotate(a, steps) with key = rotation key of 5^steps */
+#define FIDES_OP_RESCALE 3  /* out = Rescale(a), out.n_limbs = a.n_limbs - 1 */
+
+typedef struct {
+    int type;
+    int stage;
+    fides_ct a;
+    fides_ct b;
+    fides_ct out;
+    const uint64_t *key;
+    int64_t steps;
+} fides_op;
+
+typedef struct fides_batch fides_batch;
+
+int fides_batch_create(fides_ctx *ctx, fides_op *ops, int n_ops, fides_batch **out);
+int fides_batch_run(fides_batch *batch, void *stream);
+int fides_batch_capture(fides_batch *batch, void *stream);
+int fides_batch_info(const fides_batch *batch, int *launches, size_t *scratch_bytes, size_t *table_bytes);
+void fides_batch_destroy(fides_batch *batch);
+
+/*
  * Rescale that allocates nothing.  The paper has no counterpart: this entry
  * point serves callers that cannot allocate device memory when they call it
  * (a host application that owns every device allocation and hands the library

@@ -5,4 +5,5 @@ sm_103a kernels behind the C ABI of ``include/fides.h``); ``fides`` is its
 ctypes binding.  Build with ``paper_2507_04775_gb300.build.build()``.
 """
 from .fides import (Context, FidesError, find_primes, lib, to_device, to_host, version, EXPORTS,  # noqa: F401
-                    LIB_PATH, trace_enable, trace_reset, trace_read, kernel_launches, measure_modmul_peak)
+                    LIB_PATH, trace_enable, trace_reset, trace_read, kernel_launches, measure_modmul_peak, Batch, Op,
+                    OP_HMULT, OP_ROTATE, OP_RESCALE)

@@ -55,15 +55,21 @@ struct Seg {
     u64 *dst;
     const u64 *aux;
     u64 *out;
+    const TwPair *cst;  // per-prime constants of a fused epilogue (indexed by prime), or null
     int count;
     int prime0;
     int src_step;   // 1: src advances one limb per limb; 0: every limb reads the same src limb
     int mode;
 };
 
+// The segments of a launch: inline (dseg == nullptr) or, for batches, a
+// device-resident table dseg[0..nseg) with exclusive prefix sums dpre of the
+// segment counts.
 struct LimbSet {
     int nseg;
     int total;
+    const Seg *dseg;
+    const int *dpre;
     Seg seg[FIDES_MAX_SEG];
 };
 
@@ -73,6 +79,7 @@ struct Job {
     u64 *dst;
     const u64 *aux;
     u64 *out;
+    const TwPair *cst;
     int prime;
     int mode;
 };
@@ -165,25 +172,35 @@ __device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b)
     acc.hi += hi + (acc.lo < lo ? 1 : 0);
 }
 
-__device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
+__device__ __forceinline__ Job job_of(const Seg &g, int z, int N)
 {
     Job j;
+    j.src = g.src + (size_t)z * g.src_step * N;
+    j.dst = g.dst ? g.dst + (size_t)z * N : nullptr;
+    j.aux = g.aux ? g.aux + (size_t)z * N : nullptr;
+    j.out = g.out ? g.out + (size_t)z * N : nullptr;
+    j.cst = g.cst;
+    j.prime = g.prime0 + z;
+    j.mode = g.mode;
+    return j;
+}
+
+__device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
+{
+    if (S.dseg) {
+        int lo = 0, hi = S.nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(S.dpre + mid) <= z) lo = mid; else hi = mid - 1;
+        }
+        return job_of(S.dseg[lo], z - __ldg(S.dpre + lo), N);
+    }
     #pragma unroll 1
     for (int s = 0; s < S.nseg; ++s) {
-        const Seg &g = S.seg[s];
-        if (z < g.count) {
-            j.src = g.src + (size_t)z * g.src_step * N;
-            j.dst = g.dst ? g.dst + (size_t)z * N : nullptr;
-            j.aux = g.aux ? g.aux + (size_t)z * N : nullptr;
-            j.out = g.out ? g.out + (size_t)z * N : nullptr;
-            j.prime = g.prime0 + z;
-            j.mode = g.mode;
-            return j;
-        }
-        z -= g.count;
+        if (z < S.seg[s].count) return job_of(S.seg[s], z, N);
+        z -= S.seg[s].count;
     }
-    j.src = nullptr; j.dst = nullptr; j.aux = nullptr; j.out = nullptr; j.prime = 0; j.mode = 0;
-    return j;
+    return job_of(S.seg[0], 0, N);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,6 +213,7 @@ int fides_check_cuda(cudaError_t e, const char *what);
 int fides_trace_begin(const char *name, cudaStream_t st);
 void fides_trace_end(int id, cudaStream_t st);
 void fides_count_launch();
+int fides_trace_set(int on);
 
 // Programmatic dependent launch: every kernel of the library lets the next
 // kernel in its stream launch as soon as all of its CTAs are running, and waits

@@ -1,0 +1,395 @@
+// Key-switching kernels shared by the single-operation path (keyswitch.cu)
+// and the batched path (batch.cu): fast base conversion (Sec. III-F3, Eq. 1),
+// the key inner product (Sec. III-F5 "Dot product fusion") and the element-
+// wise preparation of a key-switch input (the HMult tensor product of Table I,
+// or the automorphism of HRotate).  Every kernel reads its work descriptors
+// either inline from its parameters (one operation) or from a device-resident
+// table built once for a batch.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "fides_internal.cuh"
+#include "ntt.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Fast base conversion (Eq. 1): for every target prime p and coefficient n,
+//   y_p[n] = ( sum_i [x_i[n] * qhat_i^-1]_{q_i} * [qhat_i]_p ) mod p.
+// One thread per coefficient and per group of up to BCONV_TG targets: the
+// scaled source values stay in registers and are reused for every target of
+// the group; the partial dot products accumulate in 128 bits (four 32-bit
+// words, one carry chain per partial product) and are reduced once per output
+// (Sec. III-F3: lazy 128-bit accumulation, one reduction before the
+// write-back).  The conversion matrix of the group is staged in shared memory
+// (every thread reads the same entry).  NS is the exact number of source limbs
+// (0: any number up to FIDES_MAX_SRC, with guarded loops).
+// ---------------------------------------------------------------------------
+struct BConvRun {
+    u64 *dst;
+    int count;
+    int prime0;
+};
+
+struct BConvJob {
+    const u64 *src;          // n_src contiguous coefficient-form limbs
+    int n_src;
+    int src_prime0;
+    const TwPair *scale;     // [n_src] qhat_i^-1 mod q_i
+    const u64 *mat;          // [n_src][ld]: [qhat_i]_{prime z}
+    int ld;
+    int nrun;
+    BConvRun run[3];
+};
+
+// Jobs inline (djob == nullptr) or in device memory (djob[0..njob)).
+struct BConvArgs {
+    int njob;
+    const BConvJob *djob;
+    BConvJob job[FIDES_MAX_DIGITS];
+};
+
+constexpr int BCONV_TG = 16;     // targets per CTA
+
+struct Acc128 {
+    u32 w0, w1, w2, w3;
+};
+
+// c += a * b for 64-bit a, b (the full 128-bit product), as three carry chains
+// of 32-bit multiply-adds.
+__device__ __forceinline__ void mac_wide(Acc128 &c, u64 a, u64 b)
+{
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(c.w0), "+r"(c.w1), "+r"(c.w2), "+r"(c.w3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ u64 reduce_acc(const Acc128 &c, const PrimeInfo &p)
+{
+    return reduce128(((u64)c.w3 << 32) | c.w2, ((u64)c.w1 << 32) | c.w0, p);
+}
+
+template <int NS>
+__device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *__restrict__ P, int logN)
+{
+    constexpr int MS = NS > 0 ? NS : FIDES_MAX_SRC;
+    __shared__ u64 smat[BCONV_TG * MS];
+    __shared__ PrimeInfo sp[BCONV_TG];
+    __shared__ u64 *sdst[BCONV_TG];
+    const int N = 1 << logN;
+    const int ns = NS > 0 ? NS : B.n_src;
+
+    int ndst = 0;
+    for (int r = 0; r < B.nrun; ++r) ndst += B.run[r].count;
+    const int d0 = blockIdx.z * BCONV_TG;
+    const int nd = min(BCONV_TG, ndst - d0);
+    if (nd <= 0) return;
+    if (threadIdx.x < nd) {
+        int rem = d0 + threadIdx.x, pz = 0;
+        u64 *ptr = nullptr;
+        for (int r = 0; r < B.nrun; ++r) {
+            if (rem < B.run[r].count) {
+                pz = B.run[r].prime0 + rem;
+                ptr = B.run[r].dst + (size_t)rem * N;
+                break;
+            }
+            rem -= B.run[r].count;
+        }
+        sp[threadIdx.x] = P[pz];
+        sdst[threadIdx.x] = ptr;
+        for (int i = 0; i < ns; ++i) smat[threadIdx.x * MS + i] = B.mat[(size_t)i * B.ld + pz];
+    }
+    __syncthreads();
+
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *src = B.src;
+    u64 v[MS];
+#pragma unroll
+    for (int i = 0; i < MS; ++i) {
+        if (NS > 0 || i < ns) {
+            const u64 qi = P[B.src_prime0 + i].q;
+            const u64 x = src[(size_t)i * N + n];
+            v[i] = csub(mul_shoup(x, B.scale[i], qi), qi);
+        } else {
+            v[i] = 0;
+        }
+    }
+    int d = 0;
+    for (; d + 1 < nd; d += 2) {
+        Acc128 c0 = {0, 0, 0, 0}, c1 = {0, 0, 0, 0};
+        const u64 *m0 = smat + d * MS, *m1 = m0 + MS;
+#pragma unroll
+        for (int i = 0; i < MS; ++i) {
+            if (NS > 0 || i < ns) {
+                mac_wide(c0, v[i], m0[i]);
+                mac_wide(c1, v[i], m1[i]);
+            }
+        }
+        sdst[d][n] = reduce_acc(c0, sp[d]);
+        sdst[d + 1][n] = reduce_acc(c1, sp[d + 1]);
+    }
+    if (d < nd) {
+        Acc128 c0 = {0, 0, 0, 0};
+        const u64 *m0 = smat + d * MS;
+#pragma unroll
+        for (int i = 0; i < MS; ++i)
+            if (NS > 0 || i < ns) mac_wide(c0, v[i], m0[i]);
+        sdst[d][n] = reduce_acc(c0, sp[d]);
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__restrict__ P, int logN)
+{
+    pdl_enter();
+    if (A.djob) bconv_body<NS>(A.djob[blockIdx.y], P, logN);
+    else bconv_body<NS>(A.job[blockIdx.y], P, logN);
+}
+
+template <int NS>
+void launch_bconv_ns(const fides_ctx *c, const BConvArgs &A, int max_dst, cudaStream_t st)
+{
+    dim3 grid(c->N / 256, A.njob, (max_dst + BCONV_TG - 1) / BCONV_TG), block(256);
+    FIDES_LAUNCH("k_bconv", st, k_bconv<NS>, grid, block, A, c->d_prime, c->logN);
+}
+
+// One launch for jobs that all have `ns` source limbs (inline or device jobs).
+inline int launch_bconv_group(const fides_ctx *c, const BConvArgs &G, int ns, int max_dst, cudaStream_t st)
+{
+    switch (ns) {
+    case 1: launch_bconv_ns<1>(c, G, max_dst, st); break;
+    case 2: launch_bconv_ns<2>(c, G, max_dst, st); break;
+    case 3: launch_bconv_ns<3>(c, G, max_dst, st); break;
+    case 4: launch_bconv_ns<4>(c, G, max_dst, st); break;
+    case 5: launch_bconv_ns<5>(c, G, max_dst, st); break;
+    case 6: launch_bconv_ns<6>(c, G, max_dst, st); break;
+    case 7: launch_bconv_ns<7>(c, G, max_dst, st); break;
+    case 8: launch_bconv_ns<8>(c, G, max_dst, st); break;
+    case 9: launch_bconv_ns<9>(c, G, max_dst, st); break;
+    case 10: launch_bconv_ns<10>(c, G, max_dst, st); break;
+    case 11: launch_bconv_ns<11>(c, G, max_dst, st); break;
+    case 12: launch_bconv_ns<12>(c, G, max_dst, st); break;
+    default: launch_bconv_ns<0>(c, G, max_dst, st); break;
+    }
+    return fides_check_cuda(cudaGetLastError(), "bconv launch");
+}
+
+inline int bconv_targets(const BConvJob &j)
+{
+    int nd = 0;
+    for (int r = 0; r < j.nrun; ++r) nd += j.run[r].count;
+    return nd;
+}
+
+// Launches one conversion per distinct source count of inline jobs (a ragged
+// last digit gets its own launch, so every launch runs fully unrolled loops).
+inline int launch_bconv(const fides_ctx *c, const BConvArgs &A, cudaStream_t st)
+{
+    if (A.njob == 0) return FIDES_OK;
+    bool done[FIDES_MAX_DIGITS] = {false};
+    for (int j = 0; j < A.njob; ++j) {
+        if (done[j]) continue;
+        const int ns = A.job[j].n_src;
+        BConvArgs G;
+        memset(&G, 0, sizeof(G));
+        int max_dst = 0;
+        for (int k = j; k < A.njob; ++k) {
+            if (done[k] || A.job[k].n_src != ns) continue;
+            done[k] = true;
+            G.job[G.njob++] = A.job[k];
+            max_dst = std::max(max_dst, bconv_targets(A.job[k]));
+        }
+        if (int rc = launch_bconv_group(c, G, ns, max_dst, st)) return rc;
+    }
+    return FIDES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Key inner product: acc_t[z] = sum_j d~_j[z] * evk_{j,t}[key limb of z],
+// t = 0, 1, over the nl q-limbs and the K special limbs; 128-bit lazy sums.
+// d~_j[z] is the ModUp output ext_j[z], except on the limbs of digit j itself,
+// where it is the key-switch input d[z] (read from dsrc, no copy is made).
+// ---------------------------------------------------------------------------
+struct IPOp {
+    const u64 *ext;     // [beta][ne][N]
+    const u64 *dsrc;    // [nl][N] evaluation-form input
+    const u64 *evk;     // [dnum][2][L+K][N]
+    u64 *acc;           // [2][ne][N]
+    int nl, ne, beta, alpha;
+};
+
+// One op inline (dop == nullptr; grid.y = its ne limbs) or a device table of
+// ops with exclusive prefix sums of their ne (grid.y = the total).
+struct IPArgs {
+    const IPOp *dop;
+    const int *dpre;
+    int nop;
+    IPOp one;
+};
+
+__device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfull, const PrimeInfo *__restrict__ P,
+                                           int logN)
+{
+    const int N = 1 << logN;
+    const int nl = op.nl, ne = op.ne, beta = op.beta;
+    const int pz = z < nl ? z : L + (z - nl);
+    const int own = z < nl ? z / op.alpha : -1;
+    const PrimeInfo pr = P[pz];
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *__restrict__ ext = op.ext;
+    const u64 *__restrict__ evk = op.evk;
+    const u64 *__restrict__ dsrc = op.dsrc;
+    U128 a0 = {0, 0}, a1 = {0, 0};
+    for (int j = 0; j < beta; ++j) {
+        const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
+        const u64 e = src[n];
+        const u64 k0 = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
+        const u64 k1 = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
+        mac128(a0, e, k0);
+        mac128(a1, e, k1);
+    }
+    u64 *acc = op.acc;
+    acc[(size_t)z * N + n] = reduce128(a0.hi, a0.lo, pr);
+    acc[((size_t)ne + z) * N + n] = reduce128(a1.hi, a1.lo, pr);
+}
+
+// index of the op holding row z in a table with exclusive prefix sums
+__device__ __forceinline__ int find_op(const int *__restrict__ pre, int nop, int z)
+{
+    int lo = 0, hi = nop - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pre + mid) <= z) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
+{
+    pdl_enter();
+    const int z = blockIdx.y;
+    if (A.dop) {
+        const int k = find_op(A.dpre, A.nop, z);
+        inner_body(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
+    } else {
+        inner_body(A.one, z, L, nfull, P, logN);
+    }
+}
+
+inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, cudaStream_t st)
+{
+    dim3 grid(c->N / 256, total_limbs);
+    FIDES_LAUNCH("k_inner", st, k_inner, grid, dim3(256), A, c->L, c->L + c->K, (const PrimeInfo *)c->d_prime,
+                 c->logN);
+    return fides_check_cuda(cudaGetLastError(), "inner product launch");
+}
+
+// ---------------------------------------------------------------------------
+// Preparation of a key-switch input, element-wise over the nl limbs:
+//   HMult (Table I):  o0 = a0 b0, o1 = a0 b1 + a1 b0, o2 = a1 b1
+//   HRotate:          o0 = sigma_g(a0), o2 = sigma_g(a1), with the
+//                     automorphism in evaluation form (Sec. III-F1, a
+//                     dependency within one limb):
+//                     sigma_g(a)[j] = a[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)]
+// ---------------------------------------------------------------------------
+enum { PREP_TENSOR = 0, PREP_PERMUTE = 1 };
+
+struct PrepOp {
+    const u64 *a;    // [2][nl][N]
+    const u64 *b;    // [2][nl][N] (tensor only)
+    u64 *o0, *o1, *o2;
+    u64 g;
+    int nl, kind;
+};
+
+struct PrepArgs {
+    const PrepOp *dop;
+    const int *dpre;
+    int nop;
+    PrepOp one;
+};
+
+__device__ __forceinline__ void prep_body(const PrepOp &op, int i, const PrimeInfo *__restrict__ P, int logN)
+{
+    const int N = 1 << logN;
+    const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t o = (size_t)i * N + j;
+    const size_t S = (size_t)op.nl * N;
+    const u64 *__restrict__ a = op.a;
+    if (op.kind == PREP_TENSOR) {
+        const u64 *__restrict__ b = op.b;
+        const PrimeInfo pr = P[i];
+        const u64 a0 = a[o], a1 = a[S + o], b0 = b[o], b1 = b[S + o];
+        op.o0[o] = mul_mod(a0, b0, pr);
+        U128 m = {0, 0};
+        mac128(m, a0, b1);
+        mac128(m, a1, b0);
+        op.o1[o] = reduce128(m.hi, m.lo, pr);
+        op.o2[o] = mul_mod(a1, b1, pr);
+    } else {
+        const u32 rj = __brev(j) >> (32 - logN);
+        const u64 e = ((2 * (u64)rj + 1) * op.g) & (2 * (u64)N - 1);
+        const size_t src = (size_t)i * N + (__brev((u32)((e - 1) >> 1)) >> (32 - logN));
+        op.o0[o] = a[src];
+        op.o2[o] = a[S + src];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_prep(PrepArgs A, const PrimeInfo *__restrict__ P, int logN)
+{
+    pdl_enter();
+    const int i = blockIdx.y;
+    if (A.dop) {
+        const int k = find_op(A.dpre, A.nop, i);
+        prep_body(A.dop[k], i - __ldg(A.dpre + k), P, logN);
+    } else {
+        prep_body(A.one, i, P, logN);
+    }
+}
+
+inline int launch_prep(const fides_ctx *c, const PrepArgs &A, int total_limbs, cudaStream_t st)
+{
+    dim3 grid(c->N / 256, total_limbs);
+    FIDES_LAUNCH("k_prep", st, k_prep, grid, dim3(256), A, (const PrimeInfo *)c->d_prime, c->logN);
+    return fides_check_cuda(cudaGetLastError(), "prep launch");
+}
+
+// ---------------------------------------------------------------------------
+// Limb-set helpers
+// ---------------------------------------------------------------------------
+inline Seg seg_of(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux = nullptr, u64 *out = nullptr,
+                  int src_step = 1, int mode = 0, const TwPair *cst = nullptr)
+{
+    Seg s;
+    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.cst = cst;
+    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = mode;
+    return s;
+}
+
+inline void add_seg(LimbSet &S, const Seg &g)
+{
+    if (g.count <= 0) return;
+    S.seg[S.nseg++] = g;
+    S.total += g.count;
+}
+
+inline LimbSet empty_set()
+{
+    LimbSet S;
+    memset(&S, 0, sizeof(S));
+    return S;
+}
+
+}  // namespace

@@ -49,10 +49,11 @@ int scratch_address(int dev, u64 **out)
     return FIDES_OK;
 }
 
-Seg make_seg(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux, u64 *out, int src_step)
+Seg make_seg(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux, u64 *out, int src_step,
+             const TwPair *cst)
 {
     Seg s;
-    s.src = src; s.dst = dst; s.aux = aux; s.out = out;
+    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.cst = cst;
     s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = 0;
     return s;
 }
@@ -88,7 +89,7 @@ extern "C" int fides_rescale_noalloc(fides_ctx *c, const fides_ct *a, fides_ct *
     LimbSet last;
     memset(&last, 0, sizeof(last));
     for (int t = 0; t < 2; ++t) {
-        last.seg[last.nseg++] = make_seg(a->data + t * Sin + (size_t)l * N, scr + t * N, 1, l, nullptr, nullptr, 1);
+        last.seg[last.nseg++] = make_seg(a->data + t * Sin + (size_t)l * N, scr + t * N, 1, l, nullptr, nullptr, 1, nullptr);
         last.total += 1;
     }
     int rc = ntt_inverse(c, last, ProSrc{}, EpiCanon{}, st);
@@ -97,10 +98,11 @@ extern "C" int fides_rescale_noalloc(fides_ctx *c, const fides_ct *a, fides_ct *
     LimbSet fin;
     memset(&fin, 0, sizeof(fin));
     for (int t = 0; t < 2; ++t) {
-        fin.seg[fin.nseg++] = make_seg(scr + t * N, out->data + t * Sout, l, 0, a->data + t * Sin, out->data + t * Sout, 0);
+        fin.seg[fin.nseg++] = make_seg(scr + t * N, out->data + t * Sout, l, 0, a->data + t * Sin, out->data + t * Sout, 0,
+                                       c->d_rs_qlinv + (size_t)l * c->L);
         fin.total += l;
     }
-    rc = ntt_forward(c, fin, ProSwitchMod{}, EpiSubMul{c->d_rs_qlinv + (size_t)l * c->L}, st);
+    rc = ntt_forward(c, fin, ProSwitchMod{}, EpiSubMul{}, st);
     if (!rc) out->scale = a->scale / (double)c->primes[l];
     return rc;
 }

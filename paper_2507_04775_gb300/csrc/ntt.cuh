@@ -91,11 +91,10 @@ struct EpiCanon {
 // out = c_i (aux - v) mod q_i, or out += that when the segment's mode is 1
 // (ModDown with c = P^-1, Rescale with c = q_l^-1; Sec. III-F5).
 struct EpiSubMul {
-    const TwPair *cst;
     __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
     {
         u64 y = csub(v, p.q);
-        u64 r = csub(mul_shoup(J.aux[j] + p.q - y, cst[J.prime], p.q), p.q);
+        u64 r = csub(mul_shoup(J.aux[j] + p.q - y, J.cst[J.prime], p.q), p.q);
         if (J.mode == 1) r = csub(r + J.out[j], p.q);
         J.out[j] = r;
     }

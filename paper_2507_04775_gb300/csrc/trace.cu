@@ -110,3 +110,13 @@ extern "C" int fides_trace_read(fides_trace_stat *out, int max, int *n_out)
     *n_out = n;
     return FIDES_OK;
 }
+
+// Sets the tracing state and returns the previous one (used to keep event
+// records out of captured graphs).
+int fides_trace_set(int on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int was = g_on ? 1 : 0;
+    g_on = on != 0;
+    return was;
+}

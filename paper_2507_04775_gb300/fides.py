@@ -26,7 +26,10 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
            "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale",
            "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches",
-           "fides_rescale_noalloc", "fides_measure_modmul_peak"]
+           "fides_rescale_noalloc", "fides_measure_modmul_peak", "fides_batch_create", "fides_batch_run",
+           "fides_batch_capture", "fides_batch_info", "fides_batch_destroy"]
+
+OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 
 
 class FidesError(RuntimeError):
@@ -41,6 +44,11 @@ class fides_trace_stat(ctypes.Structure):
 
 class fides_ct(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("n_limbs", ctypes.c_int), ("scale", ctypes.c_double)]
+
+
+class fides_op(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("stage", ctypes.c_int), ("a", fides_ct), ("b", fides_ct),
+                ("out", fides_ct), ("key", ctypes.c_void_p), ("steps", ctypes.c_int64)]
 
 
 _lib = None
@@ -81,6 +89,13 @@ def lib():
         L.fides_trace_reset.restype = None
         L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
         L.fides_kernel_launches.restype = ctypes.c_uint64
+        L.fides_batch_create.argtypes = [_vp, ctypes.POINTER(fides_op), _i, ctypes.POINTER(_vp)]
+        L.fides_batch_run.argtypes = [_vp, _vp]
+        L.fides_batch_capture.argtypes = [_vp, _vp]
+        L.fides_batch_info.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.fides_batch_destroy.argtypes = [_vp]
+        L.fides_batch_destroy.restype = None
         L.fides_measure_modmul_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
@@ -248,3 +263,56 @@ class Context:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
         _check(lib().fides_rescale_noalloc(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
         return co.scale
+
+
+class Op:
+    """One operation of a batch: ``kind`` is OP_HMULT, OP_ROTATE or OP_RESCALE;
+    a, b, out are CUDA tensors of ciphertexts [2][n_limbs][N]."""
+
+    def __init__(self, kind, a, n_limbs, out, b=None, key=None, steps=0, stage=0, scale_a=1.0, scale_b=1.0):
+        self.kind, self.a, self.n_limbs, self.out, self.b = kind, a, n_limbs, out, b
+        self.key, self.steps, self.stage, self.scale_a, self.scale_b = key, steps, stage, scale_a, scale_b
+        self.out_scale = None
+
+
+class Batch:
+    """A fixed batch of operations run with one launch per key-switch step per
+    stage (fides_batch_*).  Keeps references to every tensor it was built on."""
+
+    def __init__(self, ctx: "Context", ops):
+        self.ctx, self.ops = ctx, list(ops)
+        arr = (fides_op * max(1, len(self.ops)))()
+        N = ctx.N
+        for i, o in enumerate(self.ops):
+            out_limbs = o.n_limbs - 1 if o.kind == OP_RESCALE else o.n_limbs
+            arr[i].type, arr[i].stage = o.kind, o.stage
+            arr[i].a = fides_ct(_ptr(o.a, 2 * o.n_limbs * N, "a").value, o.n_limbs, o.scale_a)
+            if o.b is not None:
+                arr[i].b = fides_ct(_ptr(o.b, 2 * o.n_limbs * N, "b").value, o.n_limbs, o.scale_b)
+            arr[i].out = fides_ct(_ptr(o.out, 2 * out_limbs * N, "out").value, out_limbs, 0.0)
+            arr[i].key = _ptr(o.key, ctx.key_words(), "key").value if o.key is not None else None
+            arr[i].steps = o.steps
+        h = ctypes.c_void_p()
+        _check(lib().fides_batch_create(ctx._h, arr, len(self.ops), ctypes.byref(h)))
+        self._h = h
+        for i, o in enumerate(self.ops):
+            o.out_scale = arr[i].out.scale
+
+    def run(self, stream=None):
+        _check(lib().fides_batch_run(self._h, _stream(stream)))
+
+    def capture(self, stream):
+        """Record one run into a CUDA graph; later runs launch the graph."""
+        _check(lib().fides_batch_capture(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        n, sb, tb = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(lib().fides_batch_info(self._h, ctypes.byref(n), ctypes.byref(sb), ctypes.byref(tb)))
+        return {"launches": n.value, "scratch_bytes": sb.value, "table_bytes": tb.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fides_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close

@@ -1,0 +1,150 @@
+"""GPU parity of the batched path: a batch of HMult / HRotate / Rescale
+operations at uneven levels, in two dependent stages, must give the same
+residues as the same operations run one by one (single-op path) and as the CPU
+oracle, with and without CUDA-graph capture."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2507_04775_gb300 import (OP_HMULT, OP_RESCALE, OP_ROTATE, Batch, Context, FidesError, Op,  # noqa: E402
+                                    find_primes, to_device, to_host)
+
+
+def make_pair(P):
+    q = find_primes(P.logN, P.q_bits, P.nq)
+    p = find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    return Context(P.logN, q, p, P.dnum), oracle.Context(P.logN, q, p, P.dnum)
+
+
+def rand_ct(st, o, nl):
+    return np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+
+
+def rand_key(st, o):
+    return np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
+
+
+def zeros(o, nl):
+    return torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
+
+
+def build_case(P, levels, seed):
+    """Stage 0: HMult of (a_i, b_i) at each level, HRotate of a_i, Rescale of
+    a_i; stage 1: HRotate and Rescale of every stage-0 product."""
+    g, o = make_pair(P)
+    st = si.Stream(seed, 1)
+    rlk, rk = rand_key(st, o), rand_key(st, o)
+    drlk, drk = to_device(rlk), to_device(rk)
+    host, ops = [], []
+    for i, nl in enumerate(levels):
+        a, b = rand_ct(st, o, nl), rand_ct(st, o, nl)
+        da, db = to_device(a), to_device(b)
+        steps = [1, -2, 7, 1 << (P.logN - 2)][i % 4]
+        m = Op(OP_HMULT, da, nl, zeros(o, nl), b=db, key=drlk, stage=0, scale_a=2.0**40, scale_b=2.0**40)
+        r = Op(OP_ROTATE, da, nl, zeros(o, nl), key=drk, steps=steps, stage=0, scale_a=2.0**40)
+        ops += [m, r]
+        entry = {"nl": nl, "a": a, "b": b, "steps": steps, "m": m, "r": r}
+        if nl >= 2:
+            entry["s"] = Op(OP_RESCALE, da, nl, zeros(o, nl - 1), stage=0, scale_a=2.0**40)
+            entry["ms"] = Op(OP_RESCALE, m.out, nl, zeros(o, nl - 1), stage=1, scale_a=2.0**80)
+            ops += [entry["s"], entry["ms"]]
+        entry["mr"] = Op(OP_ROTATE, m.out, nl, zeros(o, nl), key=drk, steps=3, stage=1, scale_a=2.0**80)
+        ops.append(entry["mr"])
+        host.append(entry)
+    return g, o, rlk, rk, drlk, drk, host, ops
+
+
+def single_op_reference(g, host, drlk, drk):
+    """The same operations through the single-op entry points."""
+    ref = []
+    for e in host:
+        nl = e["nl"]
+        da, db = to_device(e["a"]), to_device(e["b"])
+        m, r, mr = zeros(g, nl), zeros(g, nl), zeros(g, nl)
+        g.hmult(da, db, nl, drlk, m)
+        g.rotate(da, nl, e["steps"], drk, r)
+        g.rotate(m, nl, 3, drk, mr)
+        d = {"m": m, "r": r, "mr": mr}
+        if nl >= 2:
+            s, ms = zeros(g, nl - 1), zeros(g, nl - 1)
+            g.rescale(da, nl, s)
+            g.rescale(m, nl, ms)
+            d["s"], d["ms"] = s, ms
+        ref.append(d)
+    return ref
+
+
+@pytest.mark.parametrize("P,levels", [(si.MID, [12, 5, 1, 9, 4]), (si.SMALL, [3, 1, 2])],
+                         ids=["logN12-L12", "logN12-L3"])
+def test_batch_matches_single_op_and_oracle(P, levels):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o, rlk, rk, drlk, drk, host, ops = build_case(P, levels, 501)
+    batch = Batch(g, ops)
+    info = batch.info()
+    assert info["launches"] > 0 and info["scratch_bytes"] > 0
+    batch.run()
+    torch.cuda.synchronize()
+    ref = single_op_reference(g, host, drlk, drk)
+    torch.cuda.synchronize()
+    for e, r in zip(host, ref):
+        for k in ("m", "r", "mr", "s", "ms"):
+            if k in r:
+                assert np.array_equal(to_host(e[k].out), to_host(r[k])), (e["nl"], k)
+        nl = e["nl"]
+        assert np.array_equal(to_host(e["m"].out).reshape(2, nl, o.N), o.hmult(e["a"], e["b"], rlk))
+        assert np.array_equal(to_host(e["r"].out).reshape(2, nl, o.N), o.rotate(e["a"], e["steps"], rk))
+        assert e["m"].out_scale == 2.0**80 and e["r"].out_scale == 2.0**40
+        if nl >= 2:
+            assert e["ms"].out_scale == 2.0**80 / o.q[nl - 1]
+    batch.close()
+    g.close()
+
+
+def test_batch_graph_capture_full_size():
+    """logN=16, 30-limb chain at uneven levels, captured in a CUDA graph and
+    replayed twice: identical to the oracle and to the uncaptured run."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.FULL
+    g, o, rlk, rk, drlk, drk, host, ops = build_case(P, [30, 17, 4], 502)
+    batch = Batch(g, ops)
+    batch.run()
+    torch.cuda.synchronize()
+    first = [to_host(op.out).copy() for op in ops]
+    for op in ops:
+        op.out.zero_()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.capture(s)
+        batch.run(s)
+        batch.run(s)
+    s.synchronize()
+    for op, f in zip(ops, first):
+        assert np.array_equal(to_host(op.out), f)
+    e = host[1]
+    nl = e["nl"]
+    prod = o.hmult(e["a"], e["b"], rlk)
+    assert np.array_equal(to_host(e["m"].out).reshape(2, nl, o.N), prod)
+    assert np.array_equal(to_host(e["mr"].out).reshape(2, nl, o.N), o.rotate(prod, 3, rk))
+    assert np.array_equal(to_host(e["ms"].out).reshape(2, nl - 1, o.N), o.rescale(prod))
+    batch.close()
+    g.close()
+
+
+def test_batch_rejects_bad_ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o = make_pair(si.SMALL)
+    a = zeros(o, 3)
+    with pytest.raises(FidesError) as e:
+        Batch(g, [Op(OP_HMULT, a, 3, zeros(o, 3), b=None, key=None)])
+    assert e.value.code == -1
+    with pytest.raises(FidesError):
+        Batch(g, [Op(OP_RESCALE, a, 1, zeros(o, 1))])
+    g.close()
