@@ -232,6 +232,11 @@ def run_fides(args, world, rank, local):
     q = fides.find_primes(P.logN, P.q_bits, P.nq)
     p = fides.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
     ctx = fides.Context(P.logN, q, p, P.dnum)
+    t_tune = time.perf_counter()
+    ctx.autotune(128)
+    t_tune = time.perf_counter() - t_tune
+    tiles = {name: {n: ctx.ntt_tile(k, n) for n in (2, 20, 30, 58, 60, 90, 128)}
+             for k, name in enumerate(("fwd_cols", "fwd_rows", "inv_rows", "inv_cols"))}
     N, nl = ctx.N, P.nq
     A, B, keys = workload_inputs(P, q, p, si.workload_seed(1) + 1000 * rank)
     dA = [fides.to_device(x) for x in A]
@@ -351,6 +356,7 @@ def run_fides(args, world, rank, local):
         "clocks": ck,
         "e2e": e2e,
         "batched": batched,
+        "autotune": {"seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
     }
     if mismatch:
         result["launch_model_mismatch"] = mismatch

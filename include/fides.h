@@ -94,6 +94,22 @@ int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, in
 int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out);
 void fides_ctx_destroy(fides_ctx *ctx);
 
+/*
+ * Autotuner of the NTT launch shape (Sec. III-F1 tunes a limb-batch parameter
+ * per GPU; every launch here covers all limbs of a step, and what is tuned is
+ * the tile width of each pass, which sets the CTA count and hence how full the
+ * last wave is).  Times each tile variant (16, 8 or 4 columns or rows per CTA)
+ * of each logN=16 pass for every limb count 1..max_limbs (at most 128; larger
+ * launches use the choice for 128) on this context's scratch, and keeps the
+ * fastest.  Without it a wave-count estimate is used.  Results are unchanged
+ * by the choice.  Synchronises `stream`; do not run it while other work uses
+ * this context.  logN = 12 has a single variant (returns FIDES_OK at once).
+ * fides_ctx_ntt_tile reports the tile width chosen for pass 0..3 (forward
+ * columns, forward rows, inverse rows, inverse columns) at n_limbs.
+ */
+int fides_ctx_autotune(fides_ctx *ctx, int max_limbs, void *stream);
+int fides_ctx_ntt_tile(const fides_ctx *ctx, int pass, int n_limbs);
+
 /* Number of digits in use at n_limbs limbs: ceil(n_limbs / alpha). */
 int fides_ctx_beta(const fides_ctx *ctx, int n_limbs);
 /* psi of prime index i (0..L+K-1), or 0 for a bad index. */

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fides_internal.cuh"
+#include "ntt.cuh"
 
 typedef unsigned __int128 u128;
 
@@ -220,6 +221,7 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     fides_ctx *c = (fides_ctx *)calloc(1, sizeof(fides_ctx));
     if (!c) return fides_set_error(FIDES_ERR_NOMEM, "fides_ctx_create: host allocation");
     cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->logN = logN; c->N = N; c->L = L; c->K = K; c->dnum = dnum; c->alpha = alpha;
     memcpy(c->primes, primes, sizeof(u64) * np);
 
@@ -319,6 +321,7 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
         fides_ctx_destroy(c);
         return rc;
     }
+    ntt_default_variants(c);
     *out = c;
     return FIDES_OK;
 }

@@ -28,6 +28,7 @@ typedef uint32_t u32;
 #define FIDES_MAX_SEG 24
 #define FIDES_MAX_DIGITS 8
 #define FIDES_MAX_SRC 32
+#define FIDES_TUNE_MAX 128   // NTT tile variants are kept per limb count up to this
 
 // A twiddle or constant with its Shoup companion.
 struct __align__(16) TwPair {
@@ -113,6 +114,11 @@ struct fides_ctx {
     // Scratch pool for one operation at the top level.
     u64 *scratch;
     size_t scratch_words;
+
+    // NTT tile variant per pass kind (forward columns, forward rows, inverse
+    // rows, inverse columns) and limb count (ntt.cu)
+    int sms;
+    unsigned char ntt_var[4][FIDES_TUNE_MAX + 1];
 };
 
 // ---------------------------------------------------------------------------

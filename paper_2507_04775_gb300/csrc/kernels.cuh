@@ -82,7 +82,7 @@ __device__ __forceinline__ u64 reduce_acc(const Acc128 &c, const PrimeInfo &p)
 }
 
 template <int NS>
-__device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *__restrict__ P, int logN)
+__device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *__restrict__ P, int logN, int tg)
 {
     constexpr int MS = NS > 0 ? NS : FIDES_MAX_SRC;
     __shared__ u64 smat[BCONV_TG * MS];
@@ -93,8 +93,8 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
 
     int ndst = 0;
     for (int r = 0; r < B.nrun; ++r) ndst += B.run[r].count;
-    const int d0 = blockIdx.z * BCONV_TG;
-    const int nd = min(BCONV_TG, ndst - d0);
+    const int d0 = blockIdx.z * tg;
+    const int nd = min(tg, ndst - d0);
     if (nd <= 0) return;
     if (threadIdx.x < nd) {
         int rem = d0 + threadIdx.x, pz = 0;
@@ -151,18 +151,42 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
 }
 
 template <int NS>
-__global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__restrict__ P, int logN)
+__global__ void __launch_bounds__(256) k_bconv(BConvArgs A, const PrimeInfo *__restrict__ P, int logN, int tg)
 {
     pdl_enter();
-    if (A.djob) bconv_body<NS>(A.djob[blockIdx.y], P, logN);
-    else bconv_body<NS>(A.job[blockIdx.y], P, logN);
+    if (A.djob) bconv_body<NS>(A.djob[blockIdx.y], P, logN, tg);
+    else bconv_body<NS>(A.job[blockIdx.y], P, logN, tg);
+}
+
+// Targets per CTA: the group size minimising (waves of CTAs) x (per-CTA time),
+// with a CTA's time modelled as tg + 4 target-equivalents (the scaling of the
+// sources and the loads are paid once per CTA) and 4 resident CTAs per SM.
+inline int bconv_group(const fides_ctx *c, int njob, int max_dst)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const long slots = 4L * sms, cols = (long)(c->N / 256) * njob;
+    int best = BCONV_TG;
+    long best_cost = -1;
+    for (int tg = BCONV_TG; tg >= 1; --tg) {
+        const long ctas = cols * ((max_dst + tg - 1) / tg);
+        const long cost = ((ctas + slots - 1) / slots) * (tg + 4);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = tg; }
+    }
+    return best;
 }
 
 template <int NS>
 void launch_bconv_ns(const fides_ctx *c, const BConvArgs &A, int max_dst, cudaStream_t st)
 {
-    dim3 grid(c->N / 256, A.njob, (max_dst + BCONV_TG - 1) / BCONV_TG), block(256);
-    FIDES_LAUNCH("k_bconv", st, k_bconv<NS>, grid, block, A, c->d_prime, c->logN);
+    const int tg = bconv_group(c, A.njob, max_dst);
+    dim3 grid(c->N / 256, A.njob, (max_dst + tg - 1) / tg), block(256);
+    FIDES_LAUNCH("k_bconv", st, k_bconv<NS>, grid, block, A, c->d_prime, c->logN, tg);
 }
 
 // One launch for jobs that all have `ns` source limbs (inline or device jobs).
@@ -251,14 +275,24 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const u64 *__restrict__ ext = op.ext;
     const u64 *__restrict__ evk = op.evk;
     const u64 *__restrict__ dsrc = op.dsrc;
+    // issue every load before the first product (the kernel is bound by HBM)
+    u64 e[FIDES_MAX_DIGITS], k0[FIDES_MAX_DIGITS], k1[FIDES_MAX_DIGITS];
+#pragma unroll
+    for (int j = 0; j < FIDES_MAX_DIGITS; ++j) {
+        if (j < beta) {
+            const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
+            e[j] = src[n];
+            k0[j] = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
+            k1[j] = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
+        }
+    }
     U128 a0 = {0, 0}, a1 = {0, 0};
-    for (int j = 0; j < beta; ++j) {
-        const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
-        const u64 e = src[n];
-        const u64 k0 = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
-        const u64 k1 = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
-        mac128(a0, e, k0);
-        mac128(a1, e, k1);
+#pragma unroll
+    for (int j = 0; j < FIDES_MAX_DIGITS; ++j) {
+        if (j < beta) {
+            mac128(a0, e[j], k0[j]);
+            mac128(a1, e[j], k1[j]);
+        }
     }
     u64 *acc = op.acc;
     acc[(size_t)z * N + n] = reduce128(a0.hi, a0.lo, pr);

@@ -6,13 +6,16 @@
 // explicit bit reversal is needed.  Stage s (m = 2^s blocks) of the forward
 // transform pairs j and j + N/2^(s+1) and uses twiddle psi^brv(m + (j >> (logN-s))).
 //
-// Decomposition.  A CTA of 256 threads transforms a 4096-element tile held in
-// registers (16 elements per thread) and shared memory:
-//   * logN = 12: the whole limb is one tile (KIND 2, one pass);
+// Decomposition.  A CTA transforms a tile held in registers (16 elements per
+// thread) and shared memory:
+//   * logN = 12: the whole limb is one tile of 256 threads (KIND 2, one pass);
 //   * logN = 16: two passes as in the paper's hierarchical 2-D NTT -- a column
-//     pass (KIND 0) runs stages 0..7 on 16 columns of stride 256, a row pass
-//     (KIND 1) runs stages 8..15 on 16 contiguous rows of 256.  Four global
-//     accesses per element, as in the paper.
+//     pass (KIND 0) runs stages 0..7 on CT columns of stride 256, a row pass
+//     (KIND 1) runs stages 8..15 on CT contiguous rows of 256, with 16*CT
+//     threads.  Four global accesses per element, as in the paper.  CT is 16,
+//     8 or 4; narrower tiles split a small launch into more CTAs so its last
+//     wave costs less (the choice per pass and limb count is autotuned, see
+//     ntt.cu).
 // Inside a pass, stages are grouped four at a time ("rounds"): in a round every
 // thread owns 16 elements whose local indices differ only in the round's four
 // bits, so four radix-2 stages run in registers; rounds exchange data through
@@ -35,7 +38,8 @@
 // Each butterfly costs one Shoup product and one conditional subtraction.
 // Prologue and epilogue functors let callers fuse element-wise work into the
 // first load and the last store (Sec. III-F5 "Operation Fusions"); epilogues
-// receive values in [0, 2q).
+// receive values in [0, 2q), except the raw intermediate store of a forward
+// column pass, which keeps [0, 4q) (the row pass accepts it).
 #pragma once
 
 #include "fides_internal.cuh"
@@ -63,7 +67,7 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, 
     y = mul_shoup(a + q2 - b, w, q);
 }
 
-// ---- prologue functors: value of input element j, in [0, 2q) ----
+// ---- prologue functors: value of input element j, in [0, 4q) ----
 struct ProSrc {
     __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return J.src[j]; }
 };
@@ -78,19 +82,24 @@ struct ProSwitchMod {
     }
 };
 
-// ---- epilogue functors: v in [0, 2q) ----
+// ---- epilogue functors ----
+// intermediate store of the first pass (raw: forward values stay in [0, 4q))
 struct EpiLazy {
+    static constexpr bool kRaw = true;
     __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &) const { J.dst[j] = v; }
 };
 struct EpiCanon {
+    static constexpr bool kRaw = false;
     __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
     {
         J.dst[j] = csub(v, p.q);
     }
 };
-// out = c_i (aux - v) mod q_i, or out += that when the segment's mode is 1
-// (ModDown with c = P^-1, Rescale with c = q_l^-1; Sec. III-F5).
+// out = c_i (aux - v) mod q_i, or out += that when the segment's mode is 1,
+// with c from the segment's constant table (ModDown with c = P^-1, Rescale
+// with c = q_l^-1; Sec. III-F5).
 struct EpiSubMul {
+    static constexpr bool kRaw = false;
     __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
     {
         u64 y = csub(v, p.q);
@@ -123,23 +132,24 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__r
     }
 }
 
-// KIND: 0 = column pass (16 strided columns, S = 8, stages 0..7 of logN=16),
-//       1 = row pass (16 rows, S = 8, stages 8..15 of logN=16),
-//       2 = whole limb (S == LOGN == 12).
+// KIND: 0 = column pass (CT strided columns, S = 8, stages 0..7 of logN=16),
+//       1 = row pass (CT rows, S = 8, stages 8..15 of logN=16),
+//       2 = whole limb (S == LOGN == 12, 256 threads; CT ignored).
 // INV selects Gentleman-Sande stages in reverse order; NINV multiplies by
-// N^-1 before the epilogue.
-template <int LOGN, int S, int KIND, bool INV, bool NINV, class Pro, class Epi>
-__global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__restrict__ P,
-                                                const TwPair *__restrict__ TW, Pro pro, Epi epi)
+// N^-1 before the epilogue.  MINB is the resident-CTA target per SM.
+template <int LOGN, int S, int KIND, bool INV, bool NINV, int CT, int MINB, class Pro, class Epi>
+__global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
+    k_ntt(LimbSet set, const PrimeInfo *__restrict__ P, const TwPair *__restrict__ TW, Pro pro, Epi epi)
 {
-    constexpr int C = 4096 >> S;                  // sub-transforms per tile
-    constexpr int R = S / 4;                      // rounds of four stages
+    constexpr int C = (KIND == 2) ? 1 : CT;            // sub-transforms per tile
+    constexpr int THREADS = (C << S) / 16;             // 16 elements per thread
+    constexpr int R = S / 4;                           // rounds of four stages
     constexpr int S0 = (KIND == 1) ? (LOGN - S) : 0;
-    constexpr int SH = LOGN - S;                  // column stride shift
-    constexpr bool TWS = (KIND == 0);             // column twiddles staged in shared memory
-    static_assert(S % 4 == 0 && C * (1 << S) == 4096, "tile shape");
+    constexpr int SH = LOGN - S;                       // column stride shift
+    constexpr bool TWS = (KIND == 0);                  // column twiddles staged in shared memory
+    static_assert(S % 4 == 0, "tile shape");
     static_assert(KIND != 1 || S == 8, "row pass handles rows of 256");
-    __shared__ u64 sm[4096];
+    __shared__ u64 sm[C << S];
     __shared__ TwPair stw[TWS ? 256 : 1];
 
     pdl_enter();
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
     const TwPair *__restrict__ tw = TW + ((size_t)J.prime << LOGN);
     const u64 q = pr.q, q2 = pr.q2;
     if (TWS) {
-        stw[t] = tw[t];
+        for (int i = t; i < 256; i += THREADS) stw[i] = tw[i];
     }
 
     int c, u;
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            int e = t + 256 * i;
+            int e = t + THREADS * i;
             int cc = e >> S, k = e & ((1 << S) - 1);
             int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
             sm[widx(cc, k)] = pro(J, gidx(cb, k), pr);
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
 #undef FIDES_NTT_ROUND
 
     // ---------------- store ----------------
-    if (!INV) {
+    if (!INV && !Epi::kRaw) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = csub(x[r], q2);      // [0, 4q) -> [0, 2q)
     }
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            int e = t + 256 * i;
+            int e = t + THREADS * i;
             int cc = e >> S, k = e & ((1 << S) - 1);
             int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
             epi(J, gidx(cb, k), sm[widx(cc, k)], pr);
@@ -237,43 +247,32 @@ __global__ void __launch_bounds__(256, 3) k_ntt(LimbSet set, const PrimeInfo *__
     }
 }
 
-// Forward NTT of every limb of `set`: prologue `pro` on the input, epilogue
-// `epi` on the output.  The intermediate of a two-pass transform is written
-// to each job's dst.
-template <class Pro, class Epi>
-int ntt_forward(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// Launchers (ntt.cu).  Forward: prologue on the input, the intermediate of a
+// two-pass transform in each job's dst, epilogue on the output.  Inverse:
+// includes N^-1.
+// ---------------------------------------------------------------------------
+int ntt_fwd_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProSrc, EpiCanon
+int ntt_fwd_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);          // ProSrc, EpiSubMul
+int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);   // ProSwitchMod, EpiSubMul
+int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProSrc, EpiCanon
+
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {
-    if (set.total == 0) return FIDES_OK;
-    dim3 block(256);
-    if (c->logN == 16) {
-        dim3 grid(16, set.total);
-        auto k1 = k_ntt<16, 8, 0, false, false, Pro, EpiLazy>;
-        auto k2 = k_ntt<16, 8, 1, false, false, ProDst, Epi>;
-        FIDES_LAUNCH("k_ntt_fwd_cols", st, k1, grid, block, set, c->d_prime, c->d_tw, pro, EpiLazy{});
-        FIDES_LAUNCH("k_ntt_fwd_rows", st, k2, grid, block, set, c->d_prime, c->d_tw, ProDst{}, epi);
-    } else {
-        dim3 grid(1, set.total);
-        auto k1 = k_ntt<12, 12, 2, false, false, Pro, Epi>;
-        FIDES_LAUNCH("k_ntt_fwd_limb", st, k1, grid, block, set, c->d_prime, c->d_tw, pro, epi);
-    }
-    return fides_check_cuda(cudaGetLastError(), "ntt forward launch");
+    return ntt_fwd_canon(c, s, st);
+}
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiSubMul, cudaStream_t st)
+{
+    return ntt_fwd_submul(c, s, st);
+}
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSwitchMod, EpiSubMul, cudaStream_t st)
+{
+    return ntt_fwd_switch_submul(c, s, st);
+}
+inline int ntt_inverse(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
+{
+    return ntt_inv_canon(c, s, st);
 }
 
-template <class Pro, class Epi>
-int ntt_inverse(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaStream_t st)
-{
-    if (set.total == 0) return FIDES_OK;
-    dim3 block(256);
-    if (c->logN == 16) {
-        dim3 grid(16, set.total);
-        auto k1 = k_ntt<16, 8, 1, true, false, Pro, EpiLazy>;
-        auto k2 = k_ntt<16, 8, 0, true, true, ProDst, Epi>;
-        FIDES_LAUNCH("k_ntt_inv_rows", st, k1, grid, block, set, c->d_prime, c->d_itw, pro, EpiLazy{});
-        FIDES_LAUNCH("k_ntt_inv_cols", st, k2, grid, block, set, c->d_prime, c->d_itw, ProDst{}, epi);
-    } else {
-        dim3 grid(1, set.total);
-        auto k1 = k_ntt<12, 12, 2, true, true, Pro, Epi>;
-        FIDES_LAUNCH("k_ntt_inv_limb", st, k1, grid, block, set, c->d_prime, c->d_itw, pro, epi);
-    }
-    return fides_check_cuda(cudaGetLastError(), "ntt inverse launch");
-}
+// Default NTT tile variant of each pass kind for each limb count (ntt.cu).
+void ntt_default_variants(fides_ctx *c);

@@ -27,7 +27,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_moddown", "fides_keyswitch", "fides_hmult", "fides_rotate", "fides_rescale",
            "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches",
            "fides_rescale_noalloc", "fides_measure_modmul_peak", "fides_batch_create", "fides_batch_run",
-           "fides_batch_capture", "fides_batch_info", "fides_batch_destroy"]
+           "fides_batch_capture", "fides_batch_info", "fides_batch_destroy", "fides_ctx_autotune",
+           "fides_ctx_ntt_tile"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 
@@ -89,6 +90,8 @@ def lib():
         L.fides_trace_reset.restype = None
         L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
         L.fides_kernel_launches.restype = ctypes.c_uint64
+        L.fides_ctx_autotune.argtypes = [_vp, _i, _vp]
+        L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
         L.fides_batch_create.argtypes = [_vp, ctypes.POINTER(fides_op), _i, ctypes.POINTER(_vp)]
         L.fides_batch_run.argtypes = [_vp, _vp]
         L.fides_batch_capture.argtypes = [_vp, _vp]
@@ -208,6 +211,14 @@ class Context:
 
     def galois_elt(self, steps: int) -> int:
         return int(lib().fides_galois_elt(self._h, steps))
+
+    def autotune(self, max_limbs: int = 128, stream=None):
+        """Time the NTT tile variants per pass and limb count; keep the fastest."""
+        _check(lib().fides_ctx_autotune(self._h, max_limbs, _stream(stream)))
+
+    def ntt_tile(self, pass_kind: int, n_limbs: int) -> int:
+        """Tile width chosen for pass 0..3 (fwd cols, fwd rows, inv rows, inv cols)."""
+        return int(lib().fides_ctx_ntt_tile(self._h, pass_kind, n_limbs))
 
     # -- primitives --------------------------------------------------------
     def ntt(self, t, first_prime: int, n_limbs: int, batch: int = 1, stream=None):
