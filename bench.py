@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 128-ciphertext batched workload")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default NTT tile widths")
     ap.add_argument("--batch-ops", type=int, default=128)
     ap.add_argument("--small", action="store_true",
                     help="one ciphertext pair and two keys (for profiler captures; not a bench line)")
@@ -233,9 +234,10 @@ def run_fides(args, world, rank, local):
     p = fides.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
     ctx = fides.Context(P.logN, q, p, P.dnum)
     t_tune = time.perf_counter()
-    ctx.autotune(128)
+    if not args.no_autotune:
+        ctx.autotune(128)
     t_tune = time.perf_counter() - t_tune
-    tiles = {name: {n: ctx.ntt_tile(k, n) for n in (2, 20, 30, 58, 60, 90, 128)}
+    tiles = {name: {n: "%d/%d" % (ctx.ntt_tile(k, n) >> 8, ctx.ntt_tile(k, n) & 255) for n in (2, 20, 30, 58, 60, 90, 128)}
              for k, name in enumerate(("fwd_cols", "fwd_rows", "inv_rows", "inv_cols"))}
     N, nl = ctx.N, P.nq
     A, B, keys = workload_inputs(P, q, p, si.workload_seed(1) + 1000 * rank)
@@ -356,7 +358,7 @@ def run_fides(args, world, rank, local):
         "clocks": ck,
         "e2e": e2e,
         "batched": batched,
-        "autotune": {"seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
+        "autotune": {"ran": not args.no_autotune, "seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
     }
     if mismatch:
         result["launch_model_mismatch"] = mismatch
@@ -459,45 +461,67 @@ def sources_sha() -> str:
 
 def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     """Same steps through the public API with host buffers: every step copies
-    its input pair from pinned host memory and reads its three results back."""
+    its input pair from pinned host memory and reads its three results back.
+    Copies run on their own streams, double-buffered, so the input copy of
+    step k+1 and the output copy of step k-1 overlap the compute of step k."""
     import torch
     steps = max(5, min(args.steps, 50))
     hA = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in A]
     hB = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in B]
-    da, db = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda"), torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
-    om, orr = torch.empty_like(da), torch.empty_like(da)
-    os_ = torch.empty(2 * (nl - 1) * N, dtype=torch.int64, device="cuda")
-    hm = torch.empty(om.shape, dtype=torch.int64).pin_memory()
-    hr = torch.empty(orr.shape, dtype=torch.int64).pin_memory()
-    hs = torch.empty(os_.shape, dtype=torch.int64).pin_memory()
+
+    def dev(words):
+        return torch.empty(words, dtype=torch.int64, device="cuda")
+
+    w_in, w_rs = 2 * nl * N, 2 * (nl - 1) * N
+    slots = []
+    for _ in range(2):
+        slots.append({"a": dev(w_in), "b": dev(w_in), "m": dev(w_in), "r": dev(w_in), "s": dev(w_rs),
+                      "hm": torch.empty(w_in, dtype=torch.int64).pin_memory(),
+                      "hr": torch.empty(w_in, dtype=torch.int64).pin_memory(),
+                      "hs": torch.empty(w_rs, dtype=torch.int64).pin_memory(),
+                      "in_ready": torch.cuda.Event(), "computed": torch.cuda.Event(), "drained": torch.cuda.Event()})
+    comp, h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
     def step(k):
-        i = k % POOL
-        da.copy_(hA[i], non_blocking=True)
-        db.copy_(hB[i], non_blocking=True)
-        s = ctx.hmult(da, db, nl, rlk, om, scale, scale)
-        ctx.rescale(om, nl, os_, s)
-        ctx.rotate(da, nl, 1 << (k % N_ROT), rks[k % N_ROT], orr, scale)
-        hm.copy_(om, non_blocking=True)
-        hs.copy_(os_, non_blocking=True)
-        hr.copy_(orr, non_blocking=True)
+        sl, i = slots[k % 2], k % POOL
+        with torch.cuda.stream(h2d):
+            h2d.wait_event(sl["drained"])          # outputs of step k-2 copied out, inputs consumed
+            sl["a"].copy_(hA[i], non_blocking=True)
+            sl["b"].copy_(hB[i], non_blocking=True)
+            sl["in_ready"].record(h2d)
+        with torch.cuda.stream(comp):
+            comp.wait_event(sl["in_ready"])
+            s = ctx.hmult(sl["a"], sl["b"], nl, rlk, sl["m"], scale, scale, stream=comp)
+            ctx.rescale(sl["m"], nl, sl["s"], s, stream=comp)
+            ctx.rotate(sl["a"], nl, 1 << (k % N_ROT), rks[k % N_ROT], sl["r"], scale, stream=comp)
+            sl["computed"].record(comp)
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(sl["computed"])
+            sl["hm"].copy_(sl["m"], non_blocking=True)
+            sl["hs"].copy_(sl["s"], non_blocking=True)
+            sl["hr"].copy_(sl["r"], non_blocking=True)
+            sl["drained"].record(d2h)
 
+    for sl in slots:
+        sl["drained"].record(d2h)
     for k in range(3):
         step(k)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
-    e0.record()
+    e0.record(h2d)
     for k in range(steps):
         step(k)
-    e1.record()
+    d2h.synchronize()
+    e1.record(d2h)
     torch.cuda.synchronize()
     barrier(world)
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     return {"value": round(2 * steps * world / (ms / 1e3), 2), "unit": "ops/s", "steps": steps,
             "h2d_bytes_per_step": 2 * hA[0].numel() * 8,
-            "d2h_bytes_per_step": (hm.numel() + hr.numel() + hs.numel()) * 8}
+            "d2h_bytes_per_step": (2 * w_in + w_rs) * 8,
+            "pipelined": "input copies, compute and result copies on three streams, two buffers deep"}
 
 
 # ---------------------------------------------------------------------------

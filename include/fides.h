@@ -98,14 +98,15 @@ void fides_ctx_destroy(fides_ctx *ctx);
  * Autotuner of the NTT launch shape (Sec. III-F1 tunes a limb-batch parameter
  * per GPU; every launch here covers all limbs of a step, and what is tuned is
  * the tile width of each pass, which sets the CTA count and hence how full the
- * last wave is).  Times each tile variant (16, 8 or 4 columns or rows per CTA)
- * of each logN=16 pass for every limb count 1..max_limbs (at most 128; larger
+ * last wave is).  Times each tile variant (16, 8 or 4 columns or rows per CTA,
+ * with a 64- or 80-register budget) of each logN=16 pass for every limb count 1..max_limbs (at most 128; larger
  * launches use the choice for 128) on this context's scratch, and keeps the
- * fastest.  Without it a wave-count estimate is used.  Results are unchanged
+ * fastest.  Without it 8 columns / 4 rows per CTA are used.  Results are unchanged
  * by the choice.  Synchronises `stream`; do not run it while other work uses
  * this context.  logN = 12 has a single variant (returns FIDES_OK at once).
- * fides_ctx_ntt_tile reports the tile width chosen for pass 0..3 (forward
- * columns, forward rows, inverse rows, inverse columns) at n_limbs.
+ * fides_ctx_ntt_tile reports the variant chosen for pass 0..3 (forward
+ * columns, forward rows, inverse rows, inverse columns) at n_limbs as
+ * (tile width << 8) | resident CTAs per SM.
  */
 int fides_ctx_autotune(fides_ctx *ctx, int max_limbs, void *stream);
 int fides_ctx_ntt_tile(const fides_ctx *ctx, int pass, int n_limbs);

@@ -28,6 +28,7 @@ struct Launch {
     BConvArgs bc;      // L_BCONV (device jobs)
     int ns, max_dst;
     IPArgs ip;         // L_INNER
+    int max_beta;      // L_INNER
     PrepArgs pp;       // L_PREP
     int total;         // grid.y of L_INNER / L_PREP
 };
@@ -106,6 +107,9 @@ void add_bconv(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T, const
     }
 }
 
+inline int ip_beta(const IPOp &o) { return o.beta; }
+inline int ip_beta(const PrepOp &) { return 0; }
+
 template <class Op>
 void add_table_launch(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T, LaunchKind kind,
                       const std::vector<Op> &ops, const std::vector<int> &rows, int which_op, int which_pre)
@@ -118,8 +122,12 @@ void add_table_launch(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T
     int tot = 0;
     for (size_t i = 0; i < ops.size(); ++i) { pre[i] = tot; tot += rows[i]; }
     l.total = tot;
-    if (kind == L_INNER) l.ip.nop = (int)ops.size();
-    else l.pp.nop = (int)ops.size();
+    if (kind == L_INNER) {
+        l.ip.nop = (int)ops.size();
+        for (const Op &o : ops) l.max_beta = std::max(l.max_beta, ip_beta(o));
+    } else {
+        l.pp.nop = (int)ops.size();
+    }
     L.push_back(l);
     const int id = (int)L.size() - 1;
     P.push_back(Pending{id, which_op, T.add(ops.data(), sizeof(Op) * ops.size())});
@@ -162,7 +170,7 @@ int run_launches(fides_batch *b, cudaStream_t st)
         case L_NTT_SUBMUL: rc = ntt_forward(c, l.set, ProSrc{}, EpiSubMul{}, st); break;
         case L_NTT_SWITCH_SUBMUL: rc = ntt_forward(c, l.set, ProSwitchMod{}, EpiSubMul{}, st); break;
         case L_BCONV: rc = launch_bconv_group(c, l.bc, l.ns, l.max_dst, st); break;
-        case L_INNER: rc = launch_inner(c, l.ip, l.total, st); break;
+        case L_INNER: rc = launch_inner(c, l.ip, l.total, l.max_beta, st); break;
         }
         if (rc) return rc;
     }

@@ -263,6 +263,7 @@ struct IPArgs {
     IPOp one;
 };
 
+template <int MAXB>
 __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfull, const PrimeInfo *__restrict__ P,
                                            int logN)
 {
@@ -276,9 +277,9 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const u64 *__restrict__ evk = op.evk;
     const u64 *__restrict__ dsrc = op.dsrc;
     // issue every load before the first product (the kernel is bound by HBM)
-    u64 e[FIDES_MAX_DIGITS], k0[FIDES_MAX_DIGITS], k1[FIDES_MAX_DIGITS];
+    u64 e[MAXB], k0[MAXB], k1[MAXB];
 #pragma unroll
-    for (int j = 0; j < FIDES_MAX_DIGITS; ++j) {
+    for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
             const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
             e[j] = src[n];
@@ -288,7 +289,7 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     }
     U128 a0 = {0, 0}, a1 = {0, 0};
 #pragma unroll
-    for (int j = 0; j < FIDES_MAX_DIGITS; ++j) {
+    for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
             mac128(a0, e[j], k0[j]);
             mac128(a1, e[j], k1[j]);
@@ -310,23 +311,38 @@ __device__ __forceinline__ int find_op(const int *__restrict__ pre, int nop, int
     return lo;
 }
 
+// MAXB: the largest digit count of the ops in the launch (loads for digits
+// >= an op's own count are predicated off).
+template <int MAXB>
 __global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
 {
     pdl_enter();
     const int z = blockIdx.y;
     if (A.dop) {
         const int k = find_op(A.dpre, A.nop, z);
-        inner_body(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
+        inner_body<MAXB>(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
     } else {
-        inner_body(A.one, z, L, nfull, P, logN);
+        inner_body<MAXB>(A.one, z, L, nfull, P, logN);
     }
 }
 
-inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, cudaStream_t st)
+template <int MAXB>
+void launch_inner_b(const fides_ctx *c, const IPArgs &A, int total_limbs, cudaStream_t st)
 {
     dim3 grid(c->N / 256, total_limbs);
-    FIDES_LAUNCH("k_inner", st, k_inner, grid, dim3(256), A, c->L, c->L + c->K, (const PrimeInfo *)c->d_prime,
+    FIDES_LAUNCH("k_inner", st, k_inner<MAXB>, grid, dim3(256), A, c->L, c->L + c->K, (const PrimeInfo *)c->d_prime,
                  c->logN);
+}
+
+inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, int max_beta, cudaStream_t st)
+{
+    switch (max_beta) {
+    case 1: launch_inner_b<1>(c, A, total_limbs, st); break;
+    case 2: launch_inner_b<2>(c, A, total_limbs, st); break;
+    case 3: launch_inner_b<3>(c, A, total_limbs, st); break;
+    case 4: launch_inner_b<4>(c, A, total_limbs, st); break;
+    default: launch_inner_b<FIDES_MAX_DIGITS>(c, A, total_limbs, st); break;
+    }
     return fides_check_cuda(cudaGetLastError(), "inner product launch");
 }
 

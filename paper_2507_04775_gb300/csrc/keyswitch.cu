@@ -47,7 +47,7 @@ int run_keyswitch(const fides_ctx *c, const KsBuffers &B, cudaStream_t st)
     IPArgs ip;
     memset(&ip, 0, sizeof(ip));
     ip.one = ks_ip_op(c, B);
-    if (int rc = launch_inner(c, ip, B.nl + c->K, st)) return rc;
+    if (int rc = launch_inner(c, ip, B.nl + c->K, ks_beta(c, B.nl), st)) return rc;
     std::vector<Seg> v;
     std::vector<BConvJob> jb;
     ks_pinv_segs(c, B, v);

@@ -6,11 +6,11 @@
 // to tune is the tile width of each pass, which decides how many CTAs a launch
 // has and so how much of its last wave is empty.  Three variants of each
 // logN=16 pass are compiled -- 16, 8 or 4 columns/rows per CTA (256, 128 or 64
-// threads, 3, 6 or 12 resident CTAs per SM) -- and the context keeps, per pass
-// kind and limb count, the variant to launch: a wave-count estimate by
-// default, or the fastest measured one after fides_ctx_autotune.
+// threads) with up to 80 registers (3, 6 or 12 resident CTAs per SM), and 4
+// or 8 per CTA with up to 64 registers (16 or 8 per SM) -- and the context keeps, per pass
+// kind and limb count, the variant to launch: a fixed default, or the fastest
+// measured one after fides_ctx_autotune.
 #include <algorithm>
-#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -19,10 +19,9 @@
 
 namespace {
 
-constexpr int NVAR = 3;
-constexpr int VAR_CT[NVAR] = {16, 8, 4};
-constexpr int VAR_MINB[NVAR] = {3, 6, 12};
-constexpr double VAR_OVERHEAD[NVAR] = {0.0, 0.08, 0.2};   // per-element cost of narrower tiles (estimate)
+constexpr int NVAR = 5;
+constexpr int VAR_CT[NVAR] = {16, 8, 4, 4, 8};
+constexpr int VAR_MINB[NVAR] = {3, 6, 12, 16, 8};   // 3/6/12: up to 80 registers; 16/8: up to 64
 
 enum PassKind { FWD_COLS = 0, FWD_ROWS = 1, INV_ROWS = 2, INV_COLS = 3 };
 
@@ -48,7 +47,9 @@ void launch_pass_v(int v, const fides_ctx *c, const LimbSet &set, const TwPair *
     switch (v) {
     case 0: launch_pass<0, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
     case 1: launch_pass<1, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
-    default: launch_pass<2, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
+    case 2: launch_pass<2, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
+    case 3: launch_pass<3, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
+    default: launch_pass<4, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
     }
 }
 
@@ -107,21 +108,16 @@ int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 }
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { return inverse(c, s, ProSrc{}, EpiCanon{}, st); }
 
-// Estimated time of a pass over n limbs with variant v: whole waves of CTAs
-// times the CTA's share of a limb, times a per-variant overhead.
+// Default variants before autotuning: 8 columns per CTA for column passes and
+// 4 rows per CTA for row passes (the choice the autotuner makes on GB300 for
+// almost every limb count between 1 and 128).
 void ntt_default_variants(fides_ctx *c)
 {
-    const int sms = c->sms > 0 ? c->sms : 1;
     for (int n = 0; n <= FIDES_TUNE_MAX; ++n) {
-        int best = 0;
-        double best_cost = 0;
-        for (int v = 0; v < NVAR; ++v) {
-            const double tiles = (double)(n > 0 ? n : 1) * (256 / VAR_CT[v]);
-            const double slots = (double)sms * VAR_MINB[v];
-            const double cost = std::ceil(tiles / slots) * VAR_CT[v] * (1.0 + VAR_OVERHEAD[v]);
-            if (v == 0 || cost < best_cost - 1e-9) { best_cost = cost; best = v; }
-        }
-        for (int k = 0; k < 4; ++k) c->ntt_var[k][n] = (unsigned char)best;
+        c->ntt_var[FWD_COLS][n] = 1;
+        c->ntt_var[INV_COLS][n] = 1;
+        c->ntt_var[FWD_ROWS][n] = 2;
+        c->ntt_var[INV_ROWS][n] = 2;
     }
 }
 
@@ -181,6 +177,7 @@ extern "C" int fides_ctx_autotune(fides_ctx *c, int max_limbs, void *stream)
 extern "C" int fides_ctx_ntt_tile(const fides_ctx *c, int pass, int n_limbs)
 {
     if (!c || pass < 0 || pass > 3 || n_limbs < 0) return 0;
-    if (c->logN != 16) return 1;
-    return VAR_CT[variant_of(c, pass, n_limbs)];
+    if (c->logN != 16) return (1 << 8) | 3;
+    const int v = variant_of(c, pass, n_limbs);
+    return (VAR_CT[v] << 8) | VAR_MINB[v];
 }

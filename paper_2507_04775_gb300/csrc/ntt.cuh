@@ -83,14 +83,22 @@ struct ProSwitchMod {
 };
 
 // ---- epilogue functors ----
+// Each epilogue has a load step (the global reads it needs for element j) and
+// a store step, so that the kernel can issue the loads of several elements
+// before computing any of them.
 // intermediate store of the first pass (raw: forward values stay in [0, 4q))
 struct EpiLazy {
     static constexpr bool kRaw = true;
-    __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &) const { J.dst[j] = v; }
+    __device__ __forceinline__ void load(const Job &, u32, u64 &, u64 &) const {}
+    __device__ __forceinline__ void store(const Job &J, u32 j, u64 v, u64, u64, const PrimeInfo &) const
+    {
+        J.dst[j] = v;
+    }
 };
 struct EpiCanon {
     static constexpr bool kRaw = false;
-    __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
+    __device__ __forceinline__ void load(const Job &, u32, u64 &, u64 &) const {}
+    __device__ __forceinline__ void store(const Job &J, u32 j, u64 v, u64, u64, const PrimeInfo &p) const
     {
         J.dst[j] = csub(v, p.q);
     }
@@ -100,11 +108,16 @@ struct EpiCanon {
 // with c = q_l^-1; Sec. III-F5).
 struct EpiSubMul {
     static constexpr bool kRaw = false;
-    __device__ __forceinline__ void operator()(const Job &J, u32 j, u64 v, const PrimeInfo &p) const
+    __device__ __forceinline__ void load(const Job &J, u32 j, u64 &a, u64 &o) const
+    {
+        a = J.aux[j];
+        o = J.mode == 1 ? J.out[j] : 0;
+    }
+    __device__ __forceinline__ void store(const Job &J, u32 j, u64 v, u64 a, u64 o, const PrimeInfo &p) const
     {
         u64 y = csub(v, p.q);
-        u64 r = csub(mul_shoup(J.aux[j] + p.q - y, J.cst[J.prime], p.q), p.q);
-        if (J.mode == 1) r = csub(r + J.out[j], p.q);
+        u64 r = csub(mul_shoup(a + p.q - y, J.cst[J.prime], p.q), p.q);
+        if (J.mode == 1) r = csub(r + o, p.q);
         J.out[j] = r;
     }
 };
@@ -231,18 +244,34 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
     if (INV || KIND == 0) {
         const int bl = INV ? S - 4 : 0;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) epi(J, gidx(cbase, kmap(u, r, bl)), x[r], pr);
+        for (int h = 0; h < 16; h += 8) {
+            u64 pa[8], po[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) epi.load(J, gidx(cbase, kmap(u, h + r, bl)), pa[r], po[r]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) epi.store(J, gidx(cbase, kmap(u, h + r, bl)), x[h + r], pa[r], po[r], pr);
+        }
     } else {
         __syncthreads();   // the last round's shared-memory reads are done
 #pragma unroll
         for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, 0))] = x[r];
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            int e = t + THREADS * i;
-            int cc = e >> S, k = e & ((1 << S) - 1);
-            int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
-            epi(J, gidx(cb, k), sm[widx(cc, k)], pr);
+        for (int h = 0; h < 16; h += 8) {
+            u64 pa[8], po[8];
+            u32 jj[8];
+            int ww[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int e = t + THREADS * (h + i);
+                const int cc = e >> S, k = e & ((1 << S) - 1);
+                const int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
+                jj[i] = gidx(cb, k);
+                ww[i] = widx(cc, k);
+                epi.load(J, jj[i], pa[i], po[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) epi.store(J, jj[i], sm[ww[i]], pa[i], po[i], pr);
         }
     }
 }
