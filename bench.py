@@ -176,33 +176,35 @@ def launch_model(nl, K, alpha, N):
     ne = nl + K
     L = []
 
-    def ntt(direction, limbs, extra_bytes=0, extra_mm=0, ninv=False):
-        # two passes; the second carries any fused epilogue
-        L.append(("k_ntt_%s_%s" % (direction, "rows" if direction == "inv" else "cols"), 2 * W * limbs, half_bfly * limbs))
+    def ntt(direction, limbs, extra_bytes=0, extra_mm=0, ninv=False, first_bytes=0, first_mm=0):
+        # two passes; the first carries any fused prologue, the second any fused epilogue
+        L.append(("k_ntt_%s_%s" % (direction, "rows" if direction == "inv" else "cols"),
+                  2 * W * limbs + first_bytes, half_bfly * limbs + first_mm))
         L.append(("k_ntt_%s_%s" % (direction, "cols" if direction == "inv" else "rows"),
                   2 * W * limbs + extra_bytes, half_bfly * limbs + extra_mm + (N * limbs if ninv else 0)))
 
-    def keyswitch(mode0, mode1):
-        ntt("inv", nl, ninv=True)                                    # ModUp: coefficient form of d
+    def keyswitch(mode0, mode1, prep):
+        # ModUp INTT; its first pass also prepares d (HMult: reads a, b and
+        # writes d0, d1, d2 with 4 products; HRotate: gathers c0, c1 and
+        # writes sigma(c0), sigma(c1))
+        fb, fm = (6 * W * nl, 4 * N * nl) if prep == "tensor" else (3 * W * nl, 0)
+        ntt("inv", nl, ninv=True, first_bytes=fb, first_mm=fm)
         ntgt = beta * ne - nl
-        L.append(("k_bconv", W * (nl + ntgt), N * (nl + sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta)))))
+        L.append(("k_bconv", W * (nl + ntgt), N * sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta))))
         ntt("fwd", ntgt)
         L.append(("k_inner", W * (beta * ne + 2 * beta * ne + 2 * ne), N * 2 * beta * ne))
         ntt("inv", 2 * K, ninv=True)                                 # ModDown: P-limbs to coefficients
-        L.append(("k_bconv", W * (2 * K + 2 * nl), N * 2 * (K + K * nl)))
+        L.append(("k_bconv", W * (2 * K + 2 * nl), N * 2 * K * nl))
         extra = W * nl * (2 + mode0 + mode1)                         # aux reads (+ out reads when accumulating)
         ntt("fwd", 2 * nl, extra_bytes=extra, extra_mm=2 * N * nl)
 
     # HMult+relin
-    L.append(("k_tensor", W * (4 * nl + 3 * nl), 4 * N * nl))
-    keyswitch(1, 1)
+    keyswitch(1, 1, "tensor")
     # Rescale of the product
     ntt("inv", 2, ninv=True)
     ntt("fwd", 2 * (nl - 1), extra_bytes=W * 2 * (nl - 1), extra_mm=N * 4 * (nl - 1))
     # HRotate
-    L.append(("k_permute", W * 2 * nl, 0))
-    L.append(("k_permute", W * 2 * nl, 0))
-    keyswitch(1, 0)
+    keyswitch(1, 0, "permute")
     return L
 
 
@@ -431,7 +433,7 @@ def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
             "ms_per_batch": round(ms_batch, 3), "plain_value": round(nops / (ms_plain / 1e3), 1),
             "plain_ms": round(ms_plain, 3), "speedup": round(ms_plain / ms_batch, 3),
             "graph": True, "kernels_per_batch": info["launches"],
-            "kernels_plain": n * 25, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2)}
+            "kernels_plain": n * 22, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2)}
 
 
 def load_traffic(kernel, bytes_per_launch):

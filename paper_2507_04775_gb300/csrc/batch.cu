@@ -20,7 +20,7 @@
 
 namespace {
 
-enum LaunchKind { L_PREP, L_INTT, L_BCONV, L_NTT, L_INNER, L_NTT_SUBMUL, L_NTT_SWITCH_SUBMUL };
+enum LaunchKind { L_INTT, L_BCONV, L_NTT, L_INNER, L_NTT_SUBMUL, L_NTT_SWITCH_SUBMUL };
 
 struct Launch {
     LaunchKind kind;
@@ -29,8 +29,7 @@ struct Launch {
     int ns, max_dst;
     IPArgs ip;         // L_INNER
     int max_beta;      // L_INNER
-    PrepArgs pp;       // L_PREP
-    int total;         // grid.y of L_INNER / L_PREP
+    int total;         // grid.y of L_INNER
 };
 
 // Host image of the device tables, with their offsets in the device buffer.
@@ -62,7 +61,7 @@ namespace {
 // the buffer is allocated, so launches record offsets and are patched later.
 struct Pending {
     int launch;
-    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.dpre, 5: pp.dop, 6: pp.dpre
+    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.dpre
     size_t off;
 };
 
@@ -107,31 +106,23 @@ void add_bconv(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T, const
     }
 }
 
-inline int ip_beta(const IPOp &o) { return o.beta; }
-inline int ip_beta(const PrepOp &) { return 0; }
-
-template <class Op>
-void add_table_launch(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T, LaunchKind kind,
-                      const std::vector<Op> &ops, const std::vector<int> &rows, int which_op, int which_pre)
+void add_inner(std::vector<Launch> &L, std::vector<Pending> &P, Tables &T, const std::vector<IPOp> &ops,
+               const std::vector<int> &rows)
 {
     if (ops.empty()) return;
     Launch l;
     memset(&l, 0, sizeof(l));
-    l.kind = kind;
+    l.kind = L_INNER;
     std::vector<int> pre(ops.size());
     int tot = 0;
     for (size_t i = 0; i < ops.size(); ++i) { pre[i] = tot; tot += rows[i]; }
     l.total = tot;
-    if (kind == L_INNER) {
-        l.ip.nop = (int)ops.size();
-        for (const Op &o : ops) l.max_beta = std::max(l.max_beta, ip_beta(o));
-    } else {
-        l.pp.nop = (int)ops.size();
-    }
+    l.ip.nop = (int)ops.size();
+    for (const IPOp &o : ops) l.max_beta = std::max(l.max_beta, o.beta);
     L.push_back(l);
     const int id = (int)L.size() - 1;
-    P.push_back(Pending{id, which_op, T.add(ops.data(), sizeof(Op) * ops.size())});
-    P.push_back(Pending{id, which_pre, T.add(pre.data(), sizeof(int) * pre.size())});
+    P.push_back(Pending{id, 3, T.add(ops.data(), sizeof(IPOp) * ops.size())});
+    P.push_back(Pending{id, 4, T.add(pre.data(), sizeof(int) * pre.size())});
 }
 
 int validate(const fides_ctx *c, const fides_op &o, int i)
@@ -164,7 +155,6 @@ int run_launches(fides_batch *b, cudaStream_t st)
     for (const Launch &l : b->launches) {
         int rc = FIDES_OK;
         switch (l.kind) {
-        case L_PREP: rc = launch_prep(c, l.pp, l.total, st); break;
         case L_INTT: rc = ntt_inverse(c, l.set, ProSrc{}, EpiCanon{}, st); break;
         case L_NTT: rc = ntt_forward(c, l.set, ProSrc{}, EpiCanon{}, st); break;
         case L_NTT_SUBMUL: rc = ntt_forward(c, l.set, ProSrc{}, EpiSubMul{}, st); break;
@@ -218,8 +208,7 @@ extern "C" int fides_batch_create(fides_ctx *c, fides_op *ops, int n_ops, fides_
         std::vector<Seg> intt, ntt, pinv, fin, rsfin;
         std::vector<BConvJob> up, down;
         std::vector<IPOp> ip;
-        std::vector<PrepOp> prep;
-        std::vector<int> ip_rows, prep_rows;
+        std::vector<int> ip_rows;
         for (int i = 0; i < n_ops; ++i) {
             fides_op &o = ops[i];
             if (o.stage != s) continue;
@@ -234,15 +223,16 @@ extern "C" int fides_batch_create(fides_ctx *c, fides_op *ops, int n_ops, fides_
             }
             const bool hm = o.type == FIDES_OP_HMULT;
             u64 *dsrc = base;
-            prep.push_back(hm ? PrepOp{o.a.data, o.b.data, o.out.data, o.out.data + S, dsrc, 0, nl, PREP_TENSOR}
-                              : PrepOp{o.a.data, nullptr, o.out.data, nullptr, dsrc, fides_galois_elt(c, o.steps), nl,
-                                       PREP_PERMUTE});
-            prep_rows.push_back(nl);
             KsBuffers B;
             memset(&B, 0, sizeof(B));
             B.d = dsrc; B.nl = nl; B.evk = o.key;
             B.out0 = o.out.data; B.out1 = o.out.data + S;
             B.mode0 = 1; B.mode1 = hm ? 1 : 0;
+            B.prep = hm ? 1 : 2;
+            B.pa = o.a.data;
+            B.pb = hm ? o.b.data : nullptr;
+            B.pout = o.out.data;
+            B.g = hm ? 0 : fides_galois_elt(c, o.steps);
             ks_carve(c, B, dsrc + S);
             ks_intt_segs(c, B, intt);
             ks_modup_jobs(c, B, up);
@@ -255,11 +245,10 @@ extern "C" int fides_batch_create(fides_ctx *c, fides_op *ops, int n_ops, fides_
             o.out.scale = hm ? o.a.scale * o.b.scale : o.a.scale;
         }
         std::vector<Launch> &L = b->launches;
-        add_table_launch(L, pend, T, L_PREP, prep, prep_rows, 5, 6);
         add_ntt(L, pend, T, L_INTT, intt);
         add_bconv(L, pend, T, up);
         add_ntt(L, pend, T, L_NTT, ntt);
-        add_table_launch(L, pend, T, L_INNER, ip, ip_rows, 3, 4);
+        add_inner(L, pend, T, ip, ip_rows);
         add_ntt(L, pend, T, L_INTT, pinv);
         add_bconv(L, pend, T, down);
         add_ntt(L, pend, T, L_NTT_SUBMUL, fin);
@@ -281,8 +270,6 @@ extern "C" int fides_batch_create(fides_ctx *c, fides_op *ops, int n_ops, fides_
         case 2: l.bc.djob = (const BConvJob *)a; break;
         case 3: l.ip.dop = (const IPOp *)a; break;
         case 4: l.ip.dpre = (const int *)a; break;
-        case 5: l.pp.dop = (const PrepOp *)a; break;
-        case 6: l.pp.dpre = (const int *)a; break;
         }
     }
     *out = b;

@@ -159,6 +159,8 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_md_mat);
     cudaFree(c->d_md_pinv);
     cudaFree(c->d_rs_qlinv);
+    cudaFree(c->d_mu_nscale);
+    cudaFree(c->d_md_nscale);
     cudaFree(c->scratch);
     free(c);
 }
@@ -303,6 +305,22 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     for (int l = 1; l < L; ++l)
         for (int i = 0; i < l; ++i) rs[(size_t)l * L + i] = pair_of(hinv(primes[l] % primes[i], primes[i]), primes[i]);
 
+    // combined N^-1 * qhat^-1 constants of the inverse NTTs feeding a conversion
+    std::vector<TwPair> mu_ns((size_t)L * (L + 1) / 2), md_ns((size_t)np);
+    for (int nl = 1; nl <= L; ++nl) {
+        for (int i = 0; i < nl; ++i) {
+            const int j = i / alpha, lo = j * alpha, hi = std::min(lo + alpha, nl);
+            u64 qi = primes[i], prod = 1;
+            for (int k = lo; k < hi; ++k)
+                if (k != i) prod = hmul(prod, primes[k] % qi, qi);
+            mu_ns[(size_t)nl * (nl - 1) / 2 + i] = pair_of(hmul(hinv(prod, qi), pinfo[i].ninv, qi), qi);
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        u64 pk = primes[L + k];
+        md_ns[L + k] = pair_of(hmul(md_scale[k].w, pinfo[L + k].ninv, pk), pk);
+    }
+
     int rc = FIDES_OK;
     if (!rc) rc = upload(&c->d_prime, pinfo, "tables");
     if (!rc) rc = upload(&c->d_tw, tw, "twiddles");
@@ -313,6 +331,8 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     if (!rc) rc = upload(&c->d_md_mat, md_mat, "moddown tables");
     if (!rc) rc = upload(&c->d_md_pinv, md_pinv, "moddown tables");
     if (!rc) rc = upload(&c->d_rs_qlinv, rs, "rescale tables");
+    if (!rc) rc = upload(&c->d_mu_nscale, mu_ns, "modup tables");
+    if (!rc) rc = upload(&c->d_md_nscale, md_ns, "moddown tables");
     if (!rc) {
         c->scratch_words = scratch_words_for(L, K, dnum, alpha, N);
         rc = fides_check_cuda(cudaMalloc((void **)&c->scratch, c->scratch_words * sizeof(u64)), "scratch pool");

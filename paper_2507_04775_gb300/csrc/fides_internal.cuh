@@ -56,11 +56,14 @@ struct Seg {
     u64 *dst;
     const u64 *aux;
     u64 *out;
-    const TwPair *cst;  // per-prime constants of a fused epilogue (indexed by prime), or null
+    u64 *side;          // second output of a fused prologue (the key-switch input), or null
+    const TwPair *cst;  // per-prime constants of a fused step (indexed by prime), or null
+    u64 g;              // Galois element of a fused automorphism
     int count;
     int prime0;
     int src_step;   // 1: src advances one limb per limb; 0: every limb reads the same src limb
-    int mode;
+    int mode;       // prologue (inverse NTT) or epilogue (forward NTT) variant
+    int pstride;    // words from polynomial 0 to polynomial 1 of a ciphertext operand
 };
 
 // The segments of a launch: inline (dseg == nullptr) or, for batches, a
@@ -80,9 +83,12 @@ struct Job {
     u64 *dst;
     const u64 *aux;
     u64 *out;
+    u64 *side;
     const TwPair *cst;
+    u64 g;
     int prime;
     int mode;
+    int pstride;
 };
 
 struct fides_ctx {
@@ -110,6 +116,13 @@ struct fides_ctx {
 
     // Rescale: [L][L], entry (l, i) = q_l^-1 mod q_i
     TwPair *d_rs_qlinv;
+
+    // Combined final constants of the inverse NTTs that feed a base conversion
+    // (the N^-1 of the INTT times the conversion's qhat^-1):
+    //   d_mu_nscale[nl(nl-1)/2 + i] = N^-1 qhat_{j(i),i}^-1 mod q_i, i < nl
+    //   d_md_nscale[L + k]          = N^-1 Phat_k^-1 mod p_k
+    TwPair *d_mu_nscale;
+    TwPair *d_md_nscale;
 
     // Scratch pool for one operation at the top level.
     u64 *scratch;
@@ -185,9 +198,12 @@ __device__ __forceinline__ Job job_of(const Seg &g, int z, int N)
     j.dst = g.dst ? g.dst + (size_t)z * N : nullptr;
     j.aux = g.aux ? g.aux + (size_t)z * N : nullptr;
     j.out = g.out ? g.out + (size_t)z * N : nullptr;
+    j.side = g.side ? g.side + (size_t)z * N : nullptr;
     j.cst = g.cst;
+    j.g = g.g;
     j.prime = g.prime0 + z;
     j.mode = g.mode;
+    j.pstride = g.pstride;
     return j;
 }
 

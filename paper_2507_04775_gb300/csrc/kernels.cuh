@@ -1,8 +1,7 @@
 // Key-switching kernels shared by the single-operation path (keyswitch.cu)
 // and the batched path (batch.cu): fast base conversion (Sec. III-F3, Eq. 1),
-// the key inner product (Sec. III-F5 "Dot product fusion") and the element-
-// wise preparation of a key-switch input (the HMult tensor product of Table I,
-// or the automorphism of HRotate).  Every kernel reads its work descriptors
+// and the key inner product (Sec. III-F5 "Dot product fusion").  Every kernel
+// reads its work descriptors
 // either inline from its parameters (one operation) or from a device-resident
 // table built once for a batch.
 #pragma once
@@ -36,6 +35,7 @@ struct BConvRun {
 struct BConvJob {
     const u64 *src;          // n_src contiguous coefficient-form limbs
     int n_src;
+    int prescaled;           // 1: the sources already hold [x_i qhat_i^-1]_{q_i}
     int src_prime0;
     const TwPair *scale;     // [n_src] qhat_i^-1 mod q_i
     const u64 *mat;          // [n_src][ld]: [qhat_i]_{prime z}
@@ -119,9 +119,13 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
 #pragma unroll
     for (int i = 0; i < MS; ++i) {
         if (NS > 0 || i < ns) {
-            const u64 qi = P[B.src_prime0 + i].q;
             const u64 x = src[(size_t)i * N + n];
-            v[i] = csub(mul_shoup(x, B.scale[i], qi), qi);
+            if (B.prescaled) {
+                v[i] = x;
+            } else {
+                const u64 qi = P[B.src_prime0 + i].q;
+                v[i] = csub(mul_shoup(x, B.scale[i], qi), qi);
+            }
         } else {
             v[i] = 0;
         }
@@ -347,84 +351,14 @@ inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, in
 }
 
 // ---------------------------------------------------------------------------
-// Preparation of a key-switch input, element-wise over the nl limbs:
-//   HMult (Table I):  o0 = a0 b0, o1 = a0 b1 + a1 b0, o2 = a1 b1
-//   HRotate:          o0 = sigma_g(a0), o2 = sigma_g(a1), with the
-//                     automorphism in evaluation form (Sec. III-F1, a
-//                     dependency within one limb):
-//                     sigma_g(a)[j] = a[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)]
-// ---------------------------------------------------------------------------
-enum { PREP_TENSOR = 0, PREP_PERMUTE = 1 };
-
-struct PrepOp {
-    const u64 *a;    // [2][nl][N]
-    const u64 *b;    // [2][nl][N] (tensor only)
-    u64 *o0, *o1, *o2;
-    u64 g;
-    int nl, kind;
-};
-
-struct PrepArgs {
-    const PrepOp *dop;
-    const int *dpre;
-    int nop;
-    PrepOp one;
-};
-
-__device__ __forceinline__ void prep_body(const PrepOp &op, int i, const PrimeInfo *__restrict__ P, int logN)
-{
-    const int N = 1 << logN;
-    const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t o = (size_t)i * N + j;
-    const size_t S = (size_t)op.nl * N;
-    const u64 *__restrict__ a = op.a;
-    if (op.kind == PREP_TENSOR) {
-        const u64 *__restrict__ b = op.b;
-        const PrimeInfo pr = P[i];
-        const u64 a0 = a[o], a1 = a[S + o], b0 = b[o], b1 = b[S + o];
-        op.o0[o] = mul_mod(a0, b0, pr);
-        U128 m = {0, 0};
-        mac128(m, a0, b1);
-        mac128(m, a1, b0);
-        op.o1[o] = reduce128(m.hi, m.lo, pr);
-        op.o2[o] = mul_mod(a1, b1, pr);
-    } else {
-        const u32 rj = __brev(j) >> (32 - logN);
-        const u64 e = ((2 * (u64)rj + 1) * op.g) & (2 * (u64)N - 1);
-        const size_t src = (size_t)i * N + (__brev((u32)((e - 1) >> 1)) >> (32 - logN));
-        op.o0[o] = a[src];
-        op.o2[o] = a[S + src];
-    }
-}
-
-__global__ void __launch_bounds__(256) k_prep(PrepArgs A, const PrimeInfo *__restrict__ P, int logN)
-{
-    pdl_enter();
-    const int i = blockIdx.y;
-    if (A.dop) {
-        const int k = find_op(A.dpre, A.nop, i);
-        prep_body(A.dop[k], i - __ldg(A.dpre + k), P, logN);
-    } else {
-        prep_body(A.one, i, P, logN);
-    }
-}
-
-inline int launch_prep(const fides_ctx *c, const PrepArgs &A, int total_limbs, cudaStream_t st)
-{
-    dim3 grid(c->N / 256, total_limbs);
-    FIDES_LAUNCH("k_prep", st, k_prep, grid, dim3(256), A, (const PrimeInfo *)c->d_prime, c->logN);
-    return fides_check_cuda(cudaGetLastError(), "prep launch");
-}
-
-// ---------------------------------------------------------------------------
 // Limb-set helpers
 // ---------------------------------------------------------------------------
 inline Seg seg_of(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux = nullptr, u64 *out = nullptr,
                   int src_step = 1, int mode = 0, const TwPair *cst = nullptr)
 {
     Seg s;
-    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.cst = cst;
-    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = mode;
+    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.side = nullptr; s.cst = cst; s.g = 0;
+    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = mode; s.pstride = 0;
     return s;
 }
 

@@ -148,7 +148,7 @@ extern "C" int fides_moddown(fides_ctx *c, const uint64_t *x, int nl, uint64_t *
     cudaStream_t st = as_stream(stream);
     KsBuffers B = ks_buffers(c, nullptr, nl, nullptr, out, nullptr, 0, 0, carve(c));
     const size_t N = c->N;
-    std::vector<Seg> v(1, seg_of(x + (size_t)nl * N, B.pc, c->K, c->L));
+    std::vector<Seg> v(1, seg_of(x + (size_t)nl * N, B.pc, c->K, c->L, nullptr, nullptr, 1, 0, c->d_md_nscale));
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
     std::vector<BConvJob> jb;
     ks_moddown_jobs(c, B, jb);
@@ -182,12 +182,12 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult", st);
-    Scratch s = carve(c);
-    PrepArgs pa;
-    memset(&pa, 0, sizeof(pa));
-    pa.one = PrepOp{a->data, b->data, out->data, out->data + S, s.dsrc, 0, nl, PREP_TENSOR};
-    if (int rc = launch_prep(c, pa, nl, st)) return rc;
-    int rc = run_keyswitch(c, ks_buffers(c, s.dsrc, nl, rlk, out->data, out->data + S, 1, 1, s), st);
+    KsBuffers B = ks_buffers(c, carve(c).dsrc, nl, rlk, out->data, out->data + S, 1, 1, carve(c));
+    B.prep = 1;
+    B.pa = a->data;
+    B.pb = b->data;
+    B.pout = out->data;
+    int rc = run_keyswitch(c, B, st);
     if (!rc) out->scale = a->scale * b->scale;
     return rc;
 }
@@ -203,12 +203,12 @@ extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, cons
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_rotate", st);
-    Scratch s = carve(c);
-    PrepArgs pa;
-    memset(&pa, 0, sizeof(pa));
-    pa.one = PrepOp{a->data, nullptr, out->data, nullptr, s.dsrc, fides_galois_elt(c, steps), nl, PREP_PERMUTE};
-    if (int rc = launch_prep(c, pa, nl, st)) return rc;
-    int rc = run_keyswitch(c, ks_buffers(c, s.dsrc, nl, rk, out->data, out->data + S, 1, 0, s), st);
+    KsBuffers B = ks_buffers(c, carve(c).dsrc, nl, rk, out->data, out->data + S, 1, 0, carve(c));
+    B.prep = 2;
+    B.pa = a->data;
+    B.pout = out->data;
+    B.g = fides_galois_elt(c, steps);
+    int rc = run_keyswitch(c, B, st);
     if (!rc) out->scale = a->scale;
     return rc;
 }

@@ -53,8 +53,8 @@ Seg make_seg(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux, u6
              const TwPair *cst)
 {
     Seg s;
-    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.cst = cst;
-    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = 0;
+    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.side = nullptr; s.cst = cst; s.g = 0;
+    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = 0; s.pstride = 0;
     return s;
 }
 

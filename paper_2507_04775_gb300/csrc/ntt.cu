@@ -93,7 +93,7 @@ void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStr
     switch (kind) {
     case FWD_COLS: launch_pass_v<0, false, false>(v, c, set, c->d_tw, ProSrc{}, EpiLazy{}, st, "k_ntt_tune"); break;
     case FWD_ROWS: launch_pass_v<1, false, false>(v, c, set, c->d_tw, ProDst{}, EpiCanon{}, st, "k_ntt_tune"); break;
-    case INV_ROWS: launch_pass_v<1, true, false>(v, c, set, c->d_itw, ProSrc{}, EpiLazy{}, st, "k_ntt_tune"); break;
+    case INV_ROWS: launch_pass_v<1, true, false>(v, c, set, c->d_itw, ProPrep{16}, EpiLazy{}, st, "k_ntt_tune"); break;
     default: launch_pass_v<0, true, true>(v, c, set, c->d_itw, ProDst{}, EpiCanon{}, st, "k_ntt_tune"); break;
     }
 }
@@ -106,7 +106,10 @@ int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 {
     return forward(c, s, ProSwitchMod{}, EpiSubMul{}, st);
 }
-int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { return inverse(c, s, ProSrc{}, EpiCanon{}, st); }
+int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
+{
+    return inverse(c, s, ProPrep{c->logN}, EpiCanon{}, st);
+}
 
 // Default variants before autotuning: 8 columns per CTA for column passes and
 // 4 rows per CTA for row passes (the choice the autotuner makes on GB300 for
@@ -141,8 +144,8 @@ extern "C" int fides_ctx_autotune(fides_ctx *c, int max_limbs, void *stream)
         for (int z0 = 0; z0 < n && S.nseg < FIDES_MAX_SEG; z0 += np) {
             Seg &g = S.seg[S.nseg++];
             u64 *p = c->scratch + (size_t)z0 * c->N;
-            g.src = p; g.dst = p; g.aux = nullptr; g.out = nullptr; g.cst = nullptr;
-            g.count = std::min(np, n - z0); g.prime0 = 0; g.src_step = 1; g.mode = 0;
+            g.src = p; g.dst = p; g.aux = nullptr; g.out = nullptr; g.side = nullptr; g.cst = nullptr; g.g = 0;
+            g.count = std::min(np, n - z0); g.prime0 = 0; g.src_step = 1; g.mode = 0; g.pstride = 0;
             S.total += g.count;
         }
         for (int kind = 0; kind < 4 && !rc; ++kind) {

@@ -82,6 +82,43 @@ struct ProSwitchMod {
     }
 };
 
+// Inverse-NTT prologue with a run-time variant (the segment's mode), which
+// fuses the element-wise step that produces a key-switch input:
+//   0: the input limb as is;
+//   1: HMult tensor product (Table I): src / aux are limbs of ciphertexts a
+//      and b (polynomial 1 at +pstride words); d0 = a0 b0 goes to out,
+//      d1 = a0 b1 + a1 b0 to out + pstride, d2 = a1 b1 to side, and d2 is
+//      transformed;
+//   2: HRotate automorphism sigma_g in evaluation form (Sec. III-F1):
+//      sigma_g(a)[j] = a[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)]; sigma_g(c0)
+//      goes to out, sigma_g(c1) to side, and sigma_g(c1) is transformed.
+struct ProPrep {
+    int logN;
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
+    {
+        if (J.mode == 0) return J.src[j];
+        const size_t S = (size_t)J.pstride;
+        if (J.mode == 1) {
+            const u64 a0 = J.src[j], a1 = J.src[S + j], b0 = J.aux[j], b1 = J.aux[S + j];
+            J.out[j] = mul_mod(a0, b0, p);
+            U128 m = {0, 0};
+            mac128(m, a0, b1);
+            mac128(m, a1, b0);
+            J.out[S + j] = reduce128(m.hi, m.lo, p);
+            const u64 d2 = mul_mod(a1, b1, p);
+            J.side[j] = d2;
+            return d2;
+        }
+        const u32 rj = __brev(j) >> (32 - logN);
+        const u64 e = ((2 * (u64)rj + 1) * J.g) & ((2ull << logN) - 1);
+        const u32 src = __brev((u32)((e - 1) >> 1)) >> (32 - logN);
+        J.out[j] = J.src[src];
+        const u64 v = J.src[S + src];
+        J.side[j] = v;
+        return v;
+    }
+};
+
 // ---- epilogue functors ----
 // Each epilogue has a load step (the global reads it needs for element j) and
 // a store step, so that the kernel can issue the loads of several elements
@@ -238,8 +275,11 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
         for (int r = 0; r < 16; ++r) x[r] = csub(x[r], q2);      // [0, 4q) -> [0, 2q)
     }
     if (NINV) {
+        // N^-1, or the segment's combined constant (N^-1 times the qhat^-1 of
+        // the base conversion that reads this output, Eq. 1)
+        const TwPair nc = J.cst ? J.cst[J.prime] : TwPair{pr.ninv, pr.ninvp};
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = mul_shoup(x[r], pr.ninv, pr.ninvp, q);
+        for (int r = 0; r < 16; ++r) x[r] = mul_shoup(x[r], nc, q);
     }
     if (INV || KIND == 0) {
         const int bl = INV ? S - 4 : 0;
@@ -284,7 +324,7 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
 int ntt_fwd_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProSrc, EpiCanon
 int ntt_fwd_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);          // ProSrc, EpiSubMul
 int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);   // ProSwitchMod, EpiSubMul
-int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProSrc, EpiCanon
+int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep, EpiCanon
 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {

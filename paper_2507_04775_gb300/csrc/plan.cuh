@@ -16,8 +16,16 @@ namespace {
 // ModDown of both accumulators, whose results are stored (mode 0) or added
 // (mode 1) into out0 / out1.
 struct KsBuffers {
-    const u64 *d;       // [nl]
+    const u64 *d;       // [nl]  key-switch input (written by a fused prep, see below)
     int nl;
+    // optional element-wise step fused into the first INTT (ProPrep): 0 none,
+    // 1 HMult tensor product of ciphertexts pa, pb (d0, d1 into pout, d2 into
+    // d), 2 HRotate automorphism g of ciphertext pa (sigma(c0) into pout,
+    // sigma(c1) into d)
+    int prep;
+    const u64 *pa, *pb;
+    u64 *pout;
+    u64 g;
     const u64 *evk;     // [dnum][2][L+K]
     u64 *out0, *out1;   // [nl] each
     int mode0, mode1;
@@ -49,10 +57,18 @@ inline u64 *ks_carve(const fides_ctx *c, KsBuffers &B, u64 *p)
     return p;
 }
 
-// 1. ModUp, INTT of d into coefficient form (canonical, as Eq. 1 requires).
-inline void ks_intt_segs(const fides_ctx *, const KsBuffers &B, std::vector<Seg> &v)
+// 1. ModUp, INTT of d into coefficient form, with the conversion's scaling
+//    qhat_i^-1 folded into the final N^-1 (the conversion reads [x_i qhat_i^-1]),
+//    and with the preparation of d fused into its first pass.
+inline void ks_intt_segs(const fides_ctx *c, const KsBuffers &B, std::vector<Seg> &v)
 {
-    v.push_back(seg_of(B.d, B.coeff, B.nl, 0));
+    const size_t nl = B.nl;
+    Seg g = seg_of(B.prep ? B.pa : B.d, B.coeff, B.nl, 0, B.pb, B.pout, 1, B.prep,
+                   c->d_mu_nscale + nl * (nl - 1) / 2);
+    g.side = B.prep ? const_cast<u64 *>(B.d) : nullptr;
+    g.g = B.g;
+    g.pstride = (int)(nl * c->N);
+    v.push_back(g);
 }
 
 // 2. ModUp, base conversion of every digit D_j (contiguous blocks of alpha
@@ -67,6 +83,7 @@ inline void ks_modup_jobs(const fides_ctx *c, const KsBuffers &B, std::vector<BC
         memset(&J, 0, sizeof(J));
         J.src = B.coeff + (size_t)lo * N;
         J.n_src = hi - lo;
+        J.prescaled = 1;
         J.src_prime0 = lo;
         const size_t off = ((size_t)(nl - 1) * c->dnum + j) * alpha;
         J.scale = c->d_mu_scale + off;
@@ -106,7 +123,8 @@ inline void ks_pinv_segs(const fides_ctx *c, const KsBuffers &B, std::vector<Seg
 {
     const size_t N = c->N, ne = (size_t)B.nl + c->K;
     for (int t = 0; t < 2; ++t)
-        v.push_back(seg_of(B.acc + (t * ne + B.nl) * N, B.pc + (size_t)t * c->K * N, c->K, c->L));
+        v.push_back(seg_of(B.acc + (t * ne + B.nl) * N, B.pc + (size_t)t * c->K * N, c->K, c->L, nullptr, nullptr, 1,
+                           0, c->d_md_nscale));
 }
 
 // 6. ModDown, base conversion P -> Q_l of both accumulators.
@@ -118,6 +136,7 @@ inline void ks_moddown_jobs(const fides_ctx *c, const KsBuffers &B, std::vector<
         memset(&J, 0, sizeof(J));
         J.src = B.pc + (size_t)t * c->K * N;
         J.n_src = c->K;
+        J.prescaled = 1;
         J.src_prime0 = c->L;
         J.scale = c->d_md_scale;
         J.mat = c->d_md_mat;
