@@ -55,6 +55,14 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 128-ciphertext batched workload")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default NTT tile widths")
     ap.add_argument("--batch-ops", type=int, default=128)
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-server workload")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-lanes", type=int, default=2)
+    ap.add_argument("--serve-max-batch", type=int, default=32)
+    ap.add_argument("--serve-saturate", type=int, default=6000, help="requests of the closed-loop run")
+    ap.add_argument("--serve-depth", type=int, default=256, help="outstanding requests of the closed-loop run")
     ap.add_argument("--small", action="store_true",
                     help="one ciphertext pair and two keys (for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -340,6 +348,11 @@ def run_fides(args, world, rank, local):
     if not args.no_batched and not args.small:
         batched = run_batched(args, ctx, dA, dB, rlk, rks, P, scale)
 
+    # ---------------- request server (continuous batching) ----------------
+    serving = None
+    if not args.no_serving and not args.small:
+        serving = run_serving(args, ctx, dA, dK, P, scale)
+
     # ---------------- end to end through host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -361,6 +374,7 @@ def run_fides(args, world, rank, local):
         "clocks": ck,
         "e2e": e2e,
         "batched": batched,
+        "serving": serving,
         "autotune": {"ran": not args.no_autotune, "seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
     }
     if mismatch:
@@ -435,6 +449,156 @@ def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
             "plain_ms": round(ms_plain, 3), "speedup": round(ms_plain / ms_batch, 3),
             "graph": True, "kernels_per_batch": info["launches"],
             "kernels_plain": n * 22, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2)}
+
+
+SERVE_STEPS = [k for k in range(1, 33)] + [-k for k in range(1, 33)]    # 64 resident rotation keys
+
+
+def serving_requests(n, rate, levels_lo, levels_hi, seed_index=3):
+    """Seeded request stream: Poisson arrivals at `rate` per second, HMult+relin
+    and HRotate with probability 1/2 each, levels uniform on [lo, hi], steps
+    uniform over the 64 resident rotation keys."""
+    st = si.Stream(si.workload_seed(seed_index), 1)
+    gaps = -np.log(1.0 - st.unit(n)) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for i in range(n):
+        kind = 1 + st.below(2)                        # OP_HMULT = 1, OP_ROTATE = 2
+        nl = levels_lo + st.below(levels_hi - levels_lo + 1)
+        reqs.append((kind, nl, st.below(1 << 20), SERVE_STEPS[st.below(len(SERVE_STEPS))]))
+    return arrivals, reqs
+
+
+def run_serving(args, ctx, dA, dK, P, scale):
+    """Request server under a Poisson stream of HMult+relin / HRotate requests
+    at levels 2..30 on a resident pool of 256 ciphertexts, with the
+    relinearisation key and 64 rotation keys resident and admission bounded by
+    a 120 GB budget for keys + pool + the server's arena.  Reports latency
+    percentiles (request submitted -> completion observed), the served rate, a
+    closed-loop saturation run, and the same request mix one call per op."""
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+    N, nq = ctx.N, P.nq
+    lo, hi = 2, nq
+    # resident keys: 1 relinearisation + 64 rotation keys, separate buffers (120 MiB each)
+    rlk = dK[0].clone()
+    rot = {k: dK[1 + i % (len(dK) - 1)].clone() for i, k in enumerate(SERVE_STEPS)}
+    # resident operand pool: 256 ciphertexts, levels 2..30 round-robin
+    pool_lv = [lo + i % (hi - lo + 1) for i in range(256)]
+    pool = [dA[i % len(dA)].view(2, nq, N)[:, :nl].contiguous().view(-1) for i, nl in enumerate(pool_lv)]
+    by_level = {}
+    for i, nl in enumerate(pool_lv):
+        by_level.setdefault(nl, []).append(i)
+    resident = (rlk.numel() + sum(t.numel() for t in rot.values()) + sum(t.numel() for t in pool)) * 8
+    budget = int(args.serve_budget_gb * 1e9)
+    arena = budget - resident
+    torch.cuda.synchronize()
+
+    def operands(r):
+        kind, nl, pick, steps = r
+        idx = by_level[nl]
+        a = pool[idx[pick % len(idx)]]
+        b = pool[idx[(pick + 1) % len(idx)]] if kind == fides.OP_HMULT else None
+        return a, b
+
+    srv = fides.Server(ctx, arena, n_lanes=args.serve_lanes, max_batch=args.serve_max_batch)
+    srv.set_relin_key(rlk)
+    for k, t in rot.items():
+        srv.add_rotation_key(k, t)
+
+    def drive(arrivals, reqs, closed_depth=0):
+        """Open loop (arrivals) or closed loop (closed_depth outstanding)."""
+        done, lag = [], []
+        n, i = len(reqs), 0
+        outstanding = 0
+        t0 = fides.now_ns()
+        while len(done) < n:
+            now = fides.now_ns()
+            if closed_depth:
+                while i < n and outstanding < closed_depth:
+                    a, b = operands(reqs[i])
+                    srv.submit(reqs[i][0], a, reqs[i][1], b=b, steps=reqs[i][3], tag=i, scale_a=scale, scale_b=scale)
+                    i += 1
+                    outstanding += 1
+            else:
+                while i < n and now - t0 >= arrivals[i] * 1e9:
+                    a, b = operands(reqs[i])
+                    srv.submit(reqs[i][0], a, reqs[i][1], b=b, steps=reqs[i][3], tag=i, scale_a=scale, scale_b=scale)
+                    lag.append(fides.now_ns() - t0 - arrivals[i] * 1e9)
+                    i += 1
+                    outstanding += 1
+            for c in srv.poll(timeout_us=0):
+                if c.status != 0:
+                    raise RuntimeError("request %d failed with status %d" % (c.tag, c.status))
+                srv.release(c.id)
+                done.append(c)
+                outstanding -= 1
+        return done, lag, t0
+
+    def summary(done, t0, n):
+        lat = np.array([c.latency_ns for c in done], dtype=np.float64) / 1e6
+        t_end = max(c.t_done_ns for c in done)
+        span = (t_end - min(c.t_submit_ns for c in done)) / 1e9
+        groups = np.array([c.group_ops for c in done])
+        return {"requests": n, "ops_per_s": round(n / span, 1), "seconds": round(span, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p90_ms": round(float(np.percentile(lat, 90)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "max_ms": round(float(lat.max()), 3),
+                "mean_group": round(float(groups.mean()), 2)}
+
+    # warm-up: one request of each kind at a few levels
+    wa, wr = serving_requests(64, 1e9, lo, hi, seed_index=4)
+    drive(wa, wr)
+    st0 = srv.stats()
+    arrivals, reqs = serving_requests(args.serve_requests, args.serve_rate, lo, hi)
+    done, lag, t0 = drive(arrivals, reqs)
+    st1 = srv.stats()
+    open_loop = summary(done, t0, len(reqs))
+    open_loop["offered_per_s"] = args.serve_rate
+    open_loop["client_lag_p99_ms"] = round(float(np.percentile(np.array(lag) / 1e6, 99)), 3)
+    open_loop["kernels"] = int(st1["kernel_launches"] - st0["kernel_launches"])
+    open_loop["groups"] = int(st1["groups"] - st0["groups"])
+    open_loop["device_busy_frac"] = round((st1["device_ms"] - st0["device_ms"]) / 1e3 / open_loop["seconds"], 3)
+    open_loop["admission_stalls"] = int(st1["admission_stalls"] - st0["admission_stalls"])
+
+    # saturation: the same mix with many requests outstanding
+    n_sat = min(len(reqs), args.serve_saturate)
+    sat_done, _, t0s = drive(None, reqs[:n_sat], closed_depth=args.serve_depth)
+    saturation = summary(sat_done, t0s, n_sat)
+    saturation["outstanding"] = args.serve_depth
+    st2 = srv.stats()
+
+    # the same requests, one library call per operation, back to back
+    n_plain = min(n_sat, 2000)
+    out = torch.empty(2 * nq * N, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def plain(rs):
+        for r in rs:
+            a, b = operands(r)
+            if r[0] == fides.OP_HMULT:
+                ctx.hmult(a, b, r[1], rlk, out, scale, scale)
+            else:
+                ctx.rotate(a, r[1], r[3], rot[r[3]], out, scale)
+    plain(reqs[:32])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain(reqs[:n_plain])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ops = n_plain / (e0.elapsed_time(e1) / 1e3)
+    srv.close()
+    del pool, rot, rlk
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson %g req/s, HMult+relin / HRotate 50/50, levels uniform {2..30}, 256 resident "
+                        "ciphertexts, rlk + 64 rotation keys resident, %g GB budget" % (args.serve_rate, args.serve_budget_gb),
+            "lanes": args.serve_lanes, "max_batch": args.serve_max_batch,
+            "resident_gb": round(resident / 1e9, 2), "arena_gb": round(arena / 1e9, 2),
+            "arena_peak_gb": round(st2["arena_peak"] / 1e9, 3),
+            "open_loop": open_loop, "saturation": saturation,
+            "plain_ops_per_s": round(plain_ops, 1), "plain_requests": n_plain,
+            "latency": "submit to completion observed by the dispatcher (host CLOCK_MONOTONIC)"}
 
 
 def load_traffic(kernel, bytes_per_launch):

@@ -53,6 +53,9 @@ extern "C" {
 #define FIDES_ERR_CUDA (-4)         /* a CUDA call failed */
 #define FIDES_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
 #define FIDES_ERR_PRIME (-6)        /* a modulus is not an NTT-friendly prime */
+#define FIDES_ERR_KEY (-7)          /* request server: no key registered for the request */
+#define FIDES_ERR_BUSY (-8)         /* request server: queue full, or request no longer queued */
+#define FIDES_ERR_CANCELLED (-9)    /* request server: the request was cancelled before it ran */
 
 typedef struct fides_ctx fides_ctx;
 
@@ -222,6 +225,129 @@ int fides_batch_run(fides_batch *batch, void *stream);
 int fides_batch_capture(fides_batch *batch, void *stream);
 int fides_batch_info(const fides_batch *batch, int *launches, size_t *scratch_bytes, size_t *table_bytes);
 void fides_batch_destroy(fides_batch *batch);
+
+/*
+ * Request server: continuous batching of HMult+relin, HRotate and Rescale
+ * requests (the paper runs one operation at a time, Sec. III-F1; this is the
+ * serving loop around that hot path).  The caller keeps ciphertexts and keys
+ * resident in device memory and submits requests that name them; a dispatcher
+ * thread owned by the server
+ *   - admits queued requests in arrival order while their device memory
+ *     (output ciphertext + key-switch scratch) fits in the server's arena, a
+ *     device allocation of cfg.arena_bytes made at creation: the arena size is
+ *     the admission budget, and the head of the queue waits (no overtaking)
+ *     until completed work or released outputs free enough of it;
+ *   - launches the admitted requests, up to cfg.max_batch, as one launch group
+ *     on the first free of cfg.n_lanes CUDA streams: one launch per step of the
+ *     key switch for the whole group (the batched path's planner), so requests
+ *     that arrive while groups run are admitted as lanes and memory free up and
+ *     their work overlaps on the device;
+ *   - queues a completion record for each request when its group finishes.
+ * Each result is bit-identical to the single-operation entry point's
+ * (fides_hmult / fides_rotate / fides_rescale) on the same inputs, whatever
+ * group it ran in.
+ *
+ * Creation: ctx may be NULL only in simulation (cfg.simulate = 1), where no
+ * device memory is touched and a group "runs" for sim_ns_per_limb x its
+ * ciphertext limbs; the shape then comes from cfg.logN/L/K/dnum.  Simulation
+ * computes no results (completions carry out.data = NULL); it exists to
+ * exercise admission, batching, cancellation, time-outs and fault injection
+ * without a GPU.  Real servers allocate the arena, cfg.n_lanes streams and
+ * per-lane launch tables, and use the context's tables (not its scratch):
+ * single-operation calls on the same context may run alongside, but
+ * fides_ctx_autotune must not.
+ *
+ * Keys: fides_server_set_relin_key / fides_server_add_rotation_key register
+ * device keys ([dnum][2][L+K][N], as for fides_hmult / fides_rotate; rotation
+ * keys by step count, modulo N/2).  Keys must stay valid until destroy.
+ *
+ * fides_server_submit validates and queues one request and returns its id:
+ *   FIDES_ERR_ARG       bad type, NULL input, level outside [1, L] (Rescale:
+ *                       [2, L]), b at another level, or the server stopping;
+ *   FIDES_ERR_KEY       no key for the request;
+ *   FIDES_ERR_NOMEM     the request alone is larger than the arena;
+ *   FIDES_ERR_BUSY      cfg.max_pending requests already queued.
+ * Nothing is queued on error.  Inputs must stay valid and unchanged until the
+ * request's completion is delivered.
+ * fides_server_poll moves up to `max` completion records to out (waits up to
+ * timeout_us for the first, < 0 = forever, 0 = no wait); *n_out = count.
+ * Statuses: FIDES_OK (out.data points into the arena and stays valid until
+ * fides_server_release(id)), FIDES_ERR_CANCELLED, FIDES_ERR_TIMEOUT (the group
+ * ran longer than cfg.timeout_us; its memory is reclaimed when the device
+ * finishes it), FIDES_ERR_CUDA or another launch error.
+ * fides_server_release returns a completed request's output memory
+ * (FIDES_ERR_ARG if the id holds no output).
+ * fides_server_cancel removes a still-queued request (its completion carries
+ * FIDES_ERR_CANCELLED); FIDES_ERR_BUSY once it has been admitted.
+ * fides_server_pause(1) holds admission (requests queue), pause(0) resumes.
+ * fides_server_inject arms a host-side fault: FIDES_FAULT_LAUNCH_ERROR makes
+ * the next `arg` groups fail at launch (nothing is enqueued; their requests
+ * complete with FIDES_ERR_CUDA), FIDES_FAULT_STALL hides the next group's
+ * completion from the dispatcher for `arg` microseconds (as a slow device
+ * would), which the time-out watchdog then sees.
+ * fides_server_destroy cancels queued requests, waits for running groups and
+ * frees everything, including unreleased outputs.
+ * All calls are thread-safe.  Timestamps are CLOCK_MONOTONIC nanoseconds, the
+ * clock of fides_now_ns().
+ */
+#define FIDES_SERVER_MAX_LANES 8
+#define FIDES_SERVER_MAX_BATCH 512
+#define FIDES_FAULT_LAUNCH_ERROR 1
+#define FIDES_FAULT_STALL 2
+
+typedef struct {
+    size_t arena_bytes;       /* admission budget: device memory for outputs + scratch */
+    int n_lanes;              /* streams with a group in flight at once, 1..8 */
+    int max_batch;            /* requests per launch group, 1..512 */
+    int max_pending;          /* queue bound, >= 1 */
+    int64_t timeout_us;       /* watchdog per group, 0 = none */
+    int simulate;             /* 1 = no device work (see above) */
+    int64_t sim_ns_per_limb;  /* simulated device time per ciphertext limb */
+    int logN, L, K, dnum;     /* shape when ctx is NULL (simulation only) */
+} fides_server_config;
+
+typedef struct {
+    int type;          /* FIDES_OP_HMULT, FIDES_OP_ROTATE or FIDES_OP_RESCALE */
+    fides_ct a, b;     /* resident device inputs (b: HMULT only) */
+    int64_t steps;     /* HRotate: slots to rotate left */
+    uint64_t tag;      /* caller's data, returned in the completion */
+} fides_request;
+
+typedef struct {
+    uint64_t id, tag;
+    int type;
+    int status;
+    fides_ct out;      /* result (n_limbs and scale always set; data NULL unless status is FIDES_OK) */
+    int64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;
+    int group_ops;     /* requests in the launch group it ran in */
+    int lane;          /* lane it ran on, -1 if it never ran */
+} fides_completion;
+
+typedef struct {
+    uint64_t submitted, rejected, cancelled, completed, failed, timed_out;
+    uint64_t groups, grouped_ops, max_group;   /* launch groups, requests in them, largest */
+    uint64_t pending, in_flight, held;         /* queued, on the device, outputs not released */
+    uint64_t arena_bytes, arena_used, arena_peak;
+    uint64_t admission_stalls;                 /* requests that waited at the head for memory */
+    uint64_t kernel_launches;                  /* kernels launched by the server */
+    double device_ms;                          /* summed device time of finished groups */
+    int max_lanes_busy;
+} fides_server_stats;
+
+typedef struct fides_server fides_server;
+
+int fides_server_create(fides_ctx *ctx, const fides_server_config *cfg, fides_server **out);
+void fides_server_destroy(fides_server *srv);
+int fides_server_set_relin_key(fides_server *srv, const uint64_t *dev_key);
+int fides_server_add_rotation_key(fides_server *srv, int64_t steps, const uint64_t *dev_key);
+int fides_server_submit(fides_server *srv, const fides_request *req, uint64_t *id_out);
+int fides_server_poll(fides_server *srv, fides_completion *out, int max, int64_t timeout_us, int *n_out);
+int fides_server_release(fides_server *srv, uint64_t id);
+int fides_server_cancel(fides_server *srv, uint64_t id);
+int fides_server_pause(fides_server *srv, int paused);
+int fides_server_inject(fides_server *srv, int fault, int64_t arg);
+int fides_server_stats_read(fides_server *srv, fides_server_stats *out);
+int64_t fides_now_ns(void);
 
 /*
  * Rescale that allocates nothing.  The paper has no counterpart: this entry

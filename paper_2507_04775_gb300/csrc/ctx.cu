@@ -185,7 +185,7 @@ extern "C" uint64_t fides_galois_elt(const fides_ctx *c, int64_t steps)
     return hpow(5, (u64)k, 2 * (u64)c->N);
 }
 
-// Scratch words one top-level operation needs (see the layout in kernels.cu).
+// Scratch words one top-level operation needs (layout: keyswitch.cu, plan.cuh).
 static size_t scratch_words_for(int L, int K, int dnum, int alpha, int N)
 {
     int beta = (L + alpha - 1) / alpha;

@@ -38,12 +38,15 @@ struct KsBuffers {
 
 inline int ks_beta(const fides_ctx *c, int nl) { return (nl + c->alpha - 1) / c->alpha; }
 
-// Words of scratch one key switch at nl limbs needs (coeff, ext, acc, pc, conv).
-inline size_t ks_scratch_words(const fides_ctx *c, int nl)
+// Words of scratch one key switch at nl limbs needs (coeff, ext, acc, pc, conv),
+// for ring degree N, K special primes and digits of alpha limbs.
+inline size_t ks_scratch_words_of(int N, int K, int alpha, int nl)
 {
-    const size_t ne = (size_t)nl + c->K;
-    return (size_t)c->N * ((size_t)nl + ks_beta(c, nl) * ne + 2 * ne + 2 * (size_t)c->K + 2 * (size_t)nl);
+    const size_t ne = (size_t)nl + K, beta = (size_t)(nl + alpha - 1) / alpha;
+    return (size_t)N * ((size_t)nl + beta * ne + 2 * ne + 2 * (size_t)K + 2 * (size_t)nl);
 }
+
+inline size_t ks_scratch_words(const fides_ctx *c, int nl) { return ks_scratch_words_of(c->N, c->K, c->alpha, nl); }
 
 // Lays out the scratch of one key switch from `p`; returns the end.
 inline u64 *ks_carve(const fides_ctx *c, KsBuffers &B, u64 *p)

@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfides.so")
 
 FIDES_OK = 0
 ERRORS = {-1: "FIDES_ERR_ARG", -2: "FIDES_ERR_UNSUPPORTED", -3: "FIDES_ERR_NOMEM", -4: "FIDES_ERR_CUDA",
-          -5: "FIDES_ERR_TIMEOUT", -6: "FIDES_ERR_PRIME"}
+          -5: "FIDES_ERR_TIMEOUT", -6: "FIDES_ERR_PRIME", -7: "FIDES_ERR_KEY", -8: "FIDES_ERR_BUSY",
+          -9: "FIDES_ERR_CANCELLED"}
+ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_KEY, ERR_BUSY, ERR_CANCELLED = -1, -3, -4, -5, -7, -8, -9
 
 EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_create", "fides_ctx_destroy",
            "fides_ctx_beta", "fides_ctx_psi", "fides_galois_elt", "fides_ntt", "fides_intt", "fides_modup",
@@ -28,9 +30,13 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_trace_enable", "fides_trace_reset", "fides_trace_read", "fides_kernel_launches",
            "fides_rescale_noalloc", "fides_measure_modmul_peak", "fides_batch_create", "fides_batch_run",
            "fides_batch_capture", "fides_batch_info", "fides_batch_destroy", "fides_ctx_autotune",
-           "fides_ctx_ntt_tile"]
+           "fides_ctx_ntt_tile", "fides_server_create", "fides_server_destroy", "fides_server_set_relin_key",
+           "fides_server_add_rotation_key", "fides_server_submit", "fides_server_poll", "fides_server_release",
+           "fides_server_cancel", "fides_server_pause", "fides_server_inject", "fides_server_stats_read",
+           "fides_now_ns"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
+FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
 
 
 class FidesError(RuntimeError):
@@ -50,6 +56,32 @@ class fides_ct(ctypes.Structure):
 class fides_op(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("stage", ctypes.c_int), ("a", fides_ct), ("b", fides_ct),
                 ("out", fides_ct), ("key", ctypes.c_void_p), ("steps", ctypes.c_int64)]
+
+
+class fides_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("n_lanes", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("max_pending", ctypes.c_int), ("timeout_us", ctypes.c_int64), ("simulate", ctypes.c_int),
+                ("sim_ns_per_limb", ctypes.c_int64), ("logN", ctypes.c_int), ("L", ctypes.c_int),
+                ("K", ctypes.c_int), ("dnum", ctypes.c_int)]
+
+
+class fides_request(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("a", fides_ct), ("b", fides_ct), ("steps", ctypes.c_int64),
+                ("tag", ctypes.c_uint64)]
+
+
+class fides_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("type", ctypes.c_int), ("status", ctypes.c_int),
+                ("out", fides_ct), ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_launch_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64), ("group_ops", ctypes.c_int),
+                ("lane", ctypes.c_int)]
+
+
+class fides_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "rejected", "cancelled", "completed", "failed", "timed_out", "groups", "grouped_ops",
+        "max_group", "pending", "in_flight", "held", "arena_bytes", "arena_used", "arena_peak",
+        "admission_stalls", "kernel_launches")] + [("device_ms", ctypes.c_double), ("max_lanes_busy", ctypes.c_int)]
 
 
 _lib = None
@@ -100,6 +132,19 @@ def lib():
         L.fides_batch_destroy.argtypes = [_vp]
         L.fides_batch_destroy.restype = None
         L.fides_measure_modmul_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.fides_server_create.argtypes = [_vp, ctypes.POINTER(fides_server_config), ctypes.POINTER(_vp)]
+        L.fides_server_destroy.argtypes = [_vp]
+        L.fides_server_destroy.restype = None
+        L.fides_server_set_relin_key.argtypes = [_vp, _vp]
+        L.fides_server_add_rotation_key.argtypes = [_vp, ctypes.c_int64, _vp]
+        L.fides_server_submit.argtypes = [_vp, ctypes.POINTER(fides_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.fides_server_poll.argtypes = [_vp, ctypes.POINTER(fides_completion), _i, ctypes.c_int64, ctypes.POINTER(_i)]
+        L.fides_server_release.argtypes = [_vp, ctypes.c_uint64]
+        L.fides_server_cancel.argtypes = [_vp, ctypes.c_uint64]
+        L.fides_server_pause.argtypes = [_vp, _i]
+        L.fides_server_inject.argtypes = [_vp, _i, ctypes.c_int64]
+        L.fides_server_stats_read.argtypes = [_vp, ctypes.POINTER(fides_server_stats)]
+        L.fides_now_ns.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -325,5 +370,123 @@ class Batch:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fides_batch_destroy(self._h)
             self._h = None
+
+    __del__ = close
+
+
+def now_ns() -> int:
+    """CLOCK_MONOTONIC nanoseconds, the clock of the server's timestamps."""
+    return int(lib().fides_now_ns())
+
+
+class _DeviceWords:
+    """A raw device range exposed through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, words: int):
+        self.__cuda_array_interface__ = {"shape": (words,), "typestr": "<i8", "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+class Completion:
+    """A completion record of the request server."""
+
+    def __init__(self, c: "fides_completion", N: int):
+        self.id, self.tag, self.type, self.status = int(c.id), int(c.tag), int(c.type), int(c.status)
+        self.ptr, self.n_limbs, self.scale = c.out.data, int(c.out.n_limbs), float(c.out.scale)
+        self.t_submit_ns, self.t_admit_ns = int(c.t_submit_ns), int(c.t_admit_ns)
+        self.t_launch_ns, self.t_done_ns = int(c.t_launch_ns), int(c.t_done_ns)
+        self.group_ops, self.lane, self._N = int(c.group_ops), int(c.lane), N
+
+    @property
+    def latency_ns(self) -> int:
+        return self.t_done_ns - self.t_submit_ns
+
+    def tensor(self):
+        """The output ciphertext [2][n_limbs][N] as a CUDA tensor aliasing the
+        server's memory (valid until the request is released)."""
+        import torch
+        if not self.ptr:
+            raise ValueError("request %d has no output (status %d)" % (self.id, self.status))
+        return torch.as_tensor(_DeviceWords(self.ptr, 2 * self.n_limbs * self._N), device="cuda")
+
+
+class Server:
+    """The request server (fides_server_*): continuous batching of HMult,
+    HRotate and Rescale requests on resident ciphertexts.  ``ctx`` may be None
+    only with ``simulate=True`` (then ``shape`` = (logN, L, K, dnum))."""
+
+    def __init__(self, ctx, arena_bytes: int, n_lanes: int = 2, max_batch: int = 32, max_pending: int = 1 << 16,
+                 timeout_us: int = 0, simulate: bool = False, sim_ns_per_limb: int = 0, shape=None):
+        cfg = fides_server_config()
+        cfg.arena_bytes, cfg.n_lanes, cfg.max_batch, cfg.max_pending = arena_bytes, n_lanes, max_batch, max_pending
+        cfg.timeout_us, cfg.simulate, cfg.sim_ns_per_limb = timeout_us, 1 if simulate else 0, sim_ns_per_limb
+        if shape is not None:
+            cfg.logN, cfg.L, cfg.K, cfg.dnum = shape
+        self.ctx = ctx
+        self.N = ctx.N if ctx is not None else (1 << cfg.logN)
+        h = ctypes.c_void_p()
+        _check(lib().fides_server_create(ctx._h if ctx is not None else None, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}     # request id -> input tensors, until completion
+        self._keys = []     # registered key tensors
+
+    @staticmethod
+    def _addr(t, words, name):
+        if isinstance(t, int):   # a raw device address (simulation)
+            return t
+        return _ptr(t, words, name).value
+
+    def set_relin_key(self, key):
+        self._keys.append(key)
+        _check(lib().fides_server_set_relin_key(self._h, self._addr(key, None, "key")))
+
+    def add_rotation_key(self, steps: int, key):
+        self._keys.append(key)
+        _check(lib().fides_server_add_rotation_key(self._h, steps, self._addr(key, None, "key")))
+
+    def submit(self, kind: int, a, n_limbs: int, b=None, steps: int = 0, tag: int = 0, scale_a: float = 1.0,
+               scale_b: float = 1.0) -> int:
+        r = fides_request()
+        r.type, r.steps, r.tag = kind, steps, tag
+        w = 2 * n_limbs * self.N
+        r.a = fides_ct(self._addr(a, w, "a"), n_limbs, scale_a)
+        if b is not None:
+            r.b = fides_ct(self._addr(b, w, "b"), n_limbs, scale_b)
+        rid = ctypes.c_uint64(0)
+        _check(lib().fides_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (a, b)
+        return rid.value
+
+    def poll(self, max_n: int = 256, timeout_us: int = 0) -> list:
+        buf = (fides_completion * max_n)()
+        n = ctypes.c_int(0)
+        _check(lib().fides_server_poll(self._h, buf, max_n, timeout_us, ctypes.byref(n)))
+        out = [Completion(buf[i], self.N) for i in range(n.value)]
+        for c in out:
+            self._keep.pop(c.id, None)
+        return out
+
+    def release(self, rid: int):
+        _check(lib().fides_server_release(self._h, rid))
+
+    def cancel(self, rid: int):
+        _check(lib().fides_server_cancel(self._h, rid))
+
+    def pause(self, on: bool = True):
+        _check(lib().fides_server_pause(self._h, 1 if on else 0))
+
+    def inject(self, fault: int, arg: int):
+        _check(lib().fides_server_inject(self._h, fault, arg))
+
+    def stats(self) -> dict:
+        st = fides_server_stats()
+        _check(lib().fides_server_stats_read(self._h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in fides_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fides_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     __del__ = close
