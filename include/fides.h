@@ -183,6 +183,61 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
 /*
+ * HSquare (Table I): HMult+relin of a with itself, identical to
+ * fides_hmult(ctx, a, a, rlk, out, stream).  out may not alias a.
+ */
+int fides_hsquare(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_rlk, fides_ct *out, void *stream);
+
+/*
+ * Conjugate (Table I): the automorphism g = 2N - 1 (every slot to its
+ * complex conjugate) with key switching by dev_ck, the switching key of
+ * s(X^(2N-1)); otherwise as fides_rotate.  out may not alias a.
+ */
+int fides_conjugate(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_ck, fides_ct *out, void *stream);
+
+/*
+ * Hoisted rotations (Sec. III-F6): n_rot rotations of one ciphertext sharing
+ * a single ModUp of c1.  The automorphism permutes evaluation points alike
+ * under every prime, so rotation k applies sigma_{g_k} (g_k = 5^steps[k] mod
+ * 2N) to every limb of every ModUp digit as the key inner product reads it,
+ * then runs its own ModDown (ModDown is not hoisted):
+ *   outs[k] = (sigma(c0) + ModDown(acc0_k), ModDown(acc1_k)),
+ *   acc_t,k = sum_j sigma(ModUp(c1)_j) * rks[k]_{j,t}.
+ * The residues differ from fides_rotate's (ModUp's approximate base
+ * conversion does not commute with the automorphism's sign flips), but both
+ * decrypt to the rotated message with the same noise bound.
+ *   steps : host array [n_rot]
+ *   rks   : host array [n_rot] of device keys (switching keys of s(X^{g_k}))
+ *   outs  : host array [n_rot] of output descriptors at a->n_limbs; none may
+ *           alias a.  out scales are set to a->scale.
+ * 1 <= n_rot <= 64.  Uses the context's scratch (one ModUp + one key
+ * switch's accumulators); rotations run one after another on `stream`.
+ */
+int fides_rotate_hoisted(fides_ctx *ctx, const fides_ct *a, int n_rot, const int64_t *steps,
+                         const uint64_t *const *dev_rks, fides_ct *outs, void *stream);
+
+/*
+ * Element-wise operations (Table I) on ciphertexts in evaluation form; out
+ * may alias a (and b).  out->n_limbs must equal a->n_limbs.
+ *   fides_hadd / fides_hsub : out = a +/- b (b at a's level); out->scale = a->scale
+ *                             (operands must carry the same scale).
+ *   fides_ptadd   : out = (c0 + pt, c1); pt is a device plaintext [n_limbs][N]
+ *                   in evaluation form encoded at a->scale.
+ *   fides_ptmult  : out = (c0 pt, c1 pt); out->scale = a->scale * pt_scale.
+ *   fides_scalar_add  : out = (c0 + k, c1), k a constant given by its residues
+ *                       k[i] mod q_i (host array [n_limbs], each < q_i).
+ *   fides_scalar_mult : out = (k c0, k c1); out->scale = a->scale * k_scale.
+ */
+int fides_hadd(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, fides_ct *out, void *stream);
+int fides_hsub(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, fides_ct *out, void *stream);
+int fides_ptadd(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_pt, fides_ct *out, void *stream);
+int fides_ptmult(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_pt, double pt_scale, fides_ct *out,
+                 void *stream);
+int fides_scalar_add(fides_ctx *ctx, const fides_ct *a, const uint64_t *k, fides_ct *out, void *stream);
+int fides_scalar_mult(fides_ctx *ctx, const fides_ct *a, const uint64_t *k, double k_scale, fides_ct *out,
+                      void *stream);
+
+/*
  * Batched operations (Sec. III-F1 hides launch overhead with limb batching;
  * here whole operations are batched).  A batch is a fixed list of HMult,
  * HRotate and Rescale operations on ciphertexts at any levels; each op names

@@ -81,6 +81,12 @@ def lib():
         L.or_automorph_eval.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, ctypes.c_uint64]
         L.or_rotate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int64, _u64p, _u64p]
         L.or_rescale.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
+        L.or_automorph_ct.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_uint64, _u64p, _u64p]
+        L.or_conjugate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p, _u64p]
+        L.or_rotate_hoisted.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _u64p,
+                                        _u64p]
+        for name in ("or_hadd", "or_hsub", "or_ptadd", "or_ptmult", "or_scalar_add", "or_scalar_mult"):
+            getattr(L, name).argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _u64p]
         L.or_from_signed.argtypes = [ctypes.c_void_p, _i64p, _intp, ctypes.c_int, _u64p]
         L.or_keygen.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p, _i64p, _u64p]
         L.or_encrypt.argtypes = [ctypes.c_void_p, ctypes.c_int, _i64p, _i64p, _u64p, _u64p, _u64p]
@@ -231,6 +237,44 @@ class Context:
     def rotate(self, a, steps: int, rk) -> np.ndarray:
         a = _u64(a); rk = _u64(rk); nl = a.shape[1]; out = np.empty_like(a)
         lib().or_rotate(self._h, _p(a), nl, steps, _p(rk), _p(out)); return out
+
+    def conjugate(self, a, ck) -> np.ndarray:
+        a = _u64(a); ck = _u64(ck); nl = a.shape[1]; out = np.empty_like(a)
+        lib().or_conjugate(self._h, _p(a), nl, _p(ck), _p(out)); return out
+
+    def rotate_hoisted(self, a, steps, rks) -> np.ndarray:
+        """[n_rot][2][nl][N]: rotation by each steps[k] with key rks[k], one shared ModUp."""
+        a = _u64(a); nl = a.shape[1]
+        st = np.ascontiguousarray(steps, dtype=np.int64)
+        keys = _u64(np.stack([_u64(k) for k in rks]))
+        out = np.empty((len(st), 2, nl, self.N), dtype=np.uint64)
+        lib().or_rotate_hoisted(self._h, _p(a), nl, len(st), st.ctypes.data, _p(keys), _p(out)); return out
+
+    def hsquare(self, a, rlk) -> np.ndarray:
+        return self.hmult(a, a, rlk)
+
+    def _ct_op(self, name, a, b):
+        a = _u64(a); b = _u64(b); nl = a.shape[1]; out = np.empty_like(a)
+        getattr(lib(), name)(self._h, _p(a), _p(b), nl, _p(out)); return out
+
+    def hadd(self, a, b) -> np.ndarray:
+        return self._ct_op("or_hadd", a, b)
+
+    def hsub(self, a, b) -> np.ndarray:
+        return self._ct_op("or_hsub", a, b)
+
+    def ptadd(self, a, pt) -> np.ndarray:
+        return self._ct_op("or_ptadd", a, pt)
+
+    def ptmult(self, a, pt) -> np.ndarray:
+        return self._ct_op("or_ptmult", a, pt)
+
+    def scalar_add(self, a, k) -> np.ndarray:
+        """k: the constant's residues, one per limb of a."""
+        return self._ct_op("or_scalar_add", a, k)
+
+    def scalar_mult(self, a, k) -> np.ndarray:
+        return self._ct_op("or_scalar_mult", a, k)
 
     def rescale(self, a) -> np.ndarray:
         a = _u64(a); nl = a.shape[1]

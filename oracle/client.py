@@ -51,6 +51,22 @@ class Client:
         g = self.ctx.galois_elt(steps)
         return self._switch_key(self.ctx.automorph_eval(self.s_eval, g))
 
+    def conjugation_key(self) -> np.ndarray:
+        """Switching key from s(X^(2N-1)) to s."""
+        return self._switch_key(self.ctx.automorph_eval(self.s_eval, 2 * self.ctx.N - 1))
+
+    # -- plaintexts and constants ------------------------------------------
+    def encode_eval(self, z: np.ndarray, nl: int, scale: float) -> np.ndarray:
+        """Plaintext of slots z at `scale` in evaluation form under q_0..q_{nl-1}."""
+        c = self.ctx
+        idx = list(range(nl))
+        return c.ntt_limbs(c.from_signed(encode(z, c.N, scale), idx), idx)
+
+    def const_residues(self, x: float, nl: int, scale: float) -> np.ndarray:
+        """Residues of round(x * scale) modulo q_0..q_{nl-1}."""
+        v = int(round(x * scale))
+        return np.array([v % q for q in self.ctx.q[:nl]], dtype=np.uint64)
+
     # -- encryption --------------------------------------------------------
     def encrypt(self, z: np.ndarray, nl: int, scale: float) -> np.ndarray:
         c = self.ctx

@@ -532,12 +532,12 @@ void or_automorph_eval(const or_ctx *c, const u64 *in, u64 *out, int nl, u64 g)
     }
 }
 
-/* HRotate (Table I): (sigma_g(c0), sigma_g(c1)) then key-switch sigma_g(c1)
- * with the key of s(X^g); out = (sigma_g(c0) + ks0, ks1).  a, out: [2][nl][N]. */
-void or_rotate(const or_ctx *c, const u64 *a, int nl, i64 steps, const u64 *rk, u64 *out)
+/* Automorphism of a ciphertext with key switching (Table I HRotate and
+ * Conjugate): (sigma_g(c0), sigma_g(c1)) then key-switch sigma_g(c1) with the
+ * key of s(X^g); out = (sigma_g(c0) + ks0, ks1).  a, out: [2][nl][N]. */
+void or_automorph_ct(const or_ctx *c, const u64 *a, int nl, u64 g, const u64 *rk, u64 *out)
 {
     u64 N = c->N, S = (u64)nl * N;
-    u64 g = or_galois_elt(c, steps);
     u64 *r = (u64 *)malloc(sizeof(u64) * 2 * S);
     or_automorph_eval(c, a, r, nl, g);
     or_automorph_eval(c, a + S, r + S, nl, g);
@@ -548,6 +548,145 @@ void or_rotate(const or_ctx *c, const u64 *a, int nl, i64 steps, const u64 *rk, 
         for (u64 n = 0; n < N; n++) out[(u64)i * N + n] = add_mod(r[(u64)i * N + n], ks0[(u64)i * N + n], q);
     }
     free(r); free(ks0);
+}
+
+/* HRotate by `steps` slots: g = 5^steps mod 2N. */
+void or_rotate(const or_ctx *c, const u64 *a, int nl, i64 steps, const u64 *rk, u64 *out)
+{
+    or_automorph_ct(c, a, nl, or_galois_elt(c, steps), rk, out);
+}
+
+/* Conjugate (Table I): g = 2N - 1 maps every slot to its complex conjugate. */
+void or_conjugate(const or_ctx *c, const u64 *a, int nl, const u64 *ck, u64 *out)
+{
+    or_automorph_ct(c, a, nl, 2 * c->N - 1, ck, out);
+}
+
+/*
+ * Hoisted rotations (Sec. III-F6): one ModUp of c1 serves every rotation.
+ * The automorphism permutes evaluation points the same way under every
+ * prime, so sigma_g is applied to each limb of each ModUp digit (q- and
+ * special limbs alike); then the inner product with that rotation's key, the
+ * ModDown of both accumulators (not hoisted), and out_k = (sigma_g(c0) + ks0,
+ * ks1).  a: [2][nl][N]; rks: [n_rot][dnum][2][nq + K][N]; outs: [n_rot][2][nl][N].
+ */
+void or_rotate_hoisted(const or_ctx *c, const u64 *a, int nl, int n_rot, const i64 *steps, const u64 *rks, u64 *outs)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    int K = c->nk, ne = nl + K, beta = or_beta(c, nl), nfull = c->nq + K;
+    u64 *ext = (u64 *)malloc(sizeof(u64) * beta * ne * N);
+    u64 *rext = (u64 *)malloc(sizeof(u64) * beta * ne * N);
+    u64 *acc = (u64 *)malloc(sizeof(u64) * 2 * ne * N);
+    u64 *r0 = (u64 *)malloc(sizeof(u64) * S);
+    or_modup(c, a + S, nl, ext);
+    for (int r = 0; r < n_rot; r++) {
+        u64 g = or_galois_elt(c, steps[r]);
+        const u64 *rk = rks + (u64)r * c->dnum * 2 * nfull * N;
+        u64 *out = outs + (u64)r * 2 * S;
+        for (int j = 0; j < beta; j++) or_automorph_eval(c, ext + (u64)j * ne * N, rext + (u64)j * ne * N, ne, g);
+        memset(acc, 0, sizeof(u64) * 2 * ne * N);
+        #pragma omp parallel for schedule(static)
+        for (int z = 0; z < ne; z++) {
+            int pi = ext_prime(c, nl, z);
+            int kz = z < nl ? z : c->nq + (z - nl);
+            u64 q = c->primes[pi];
+            for (int t = 0; t < 2; t++) {
+                u64 *ac = acc + ((u64)t * ne + z) * N;
+                for (int j = 0; j < beta; j++) {
+                    const u64 *e = rext + ((u64)j * ne + z) * N;
+                    const u64 *k = rk + (((u64)j * 2 + t) * nfull + kz) * N;
+                    for (u64 n = 0; n < N; n++) ac[n] = add_mod(ac[n], mul_mod(e[n], k[n], q), q);
+                }
+            }
+        }
+        or_moddown(c, acc, nl, r0);
+        or_moddown(c, acc + (u64)ne * N, nl, out + S);
+        u64 *sc0 = (u64 *)malloc(sizeof(u64) * S);
+        or_automorph_eval(c, a, sc0, nl, g);
+        for (int i = 0; i < nl; i++) {
+            u64 q = c->primes[i];
+            for (u64 n = 0; n < N; n++) out[(u64)i * N + n] = add_mod(sc0[(u64)i * N + n], r0[(u64)i * N + n], q);
+        }
+        free(sc0);
+    }
+    free(ext); free(rext); free(acc); free(r0);
+}
+
+/* ------------------------------------------------------------------------
+ * Element-wise operations of Table I on ciphertexts [2][nl][N] in evaluation
+ * form, where a product of polynomials is the slot-wise product of their
+ * evaluations and a constant polynomial evaluates to itself at every point.
+ * Plaintexts are [nl][N] (evaluation form); constants are given by their
+ * residues c[i] mod q_i.
+ * ---------------------------------------------------------------------- */
+void or_hadd(const or_ctx *c, const u64 *a, const u64 *b, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int t = 0; t < 2; t++)
+        for (int i = 0; i < nl; i++)
+            for (u64 n = 0; n < N; n++) {
+                u64 o = t * S + (u64)i * N + n;
+                out[o] = add_mod(a[o], b[o], c->primes[i]);
+            }
+}
+
+void or_hsub(const or_ctx *c, const u64 *a, const u64 *b, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int t = 0; t < 2; t++)
+        for (int i = 0; i < nl; i++)
+            for (u64 n = 0; n < N; n++) {
+                u64 o = t * S + (u64)i * N + n;
+                out[o] = sub_mod(a[o], b[o], c->primes[i]);
+            }
+}
+
+/* (c0 + pt, c1) */
+void or_ptadd(const or_ctx *c, const u64 *a, const u64 *pt, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int i = 0; i < nl; i++)
+        for (u64 n = 0; n < N; n++) {
+            u64 o = (u64)i * N + n;
+            out[o] = add_mod(a[o], pt[o], c->primes[i]);
+            out[S + o] = a[S + o];
+        }
+}
+
+/* (c0 pt, c1 pt) */
+void or_ptmult(const or_ctx *c, const u64 *a, const u64 *pt, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int t = 0; t < 2; t++)
+        for (int i = 0; i < nl; i++)
+            for (u64 n = 0; n < N; n++) {
+                u64 o = (u64)i * N + n;
+                out[t * S + o] = mul_mod(a[t * S + o], pt[o], c->primes[i]);
+            }
+}
+
+/* (c0 + k, c1) for the constant k with residues k[i] */
+void or_scalar_add(const or_ctx *c, const u64 *a, const u64 *k, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int i = 0; i < nl; i++)
+        for (u64 n = 0; n < N; n++) {
+            u64 o = (u64)i * N + n;
+            out[o] = add_mod(a[o], k[i], c->primes[i]);
+            out[S + o] = a[S + o];
+        }
+}
+
+/* (k c0, k c1) */
+void or_scalar_mult(const or_ctx *c, const u64 *a, const u64 *k, int nl, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    for (int t = 0; t < 2; t++)
+        for (int i = 0; i < nl; i++)
+            for (u64 n = 0; n < N; n++) {
+                u64 o = t * S + (u64)i * N + n;
+                out[o] = mul_mod(a[o], k[i], c->primes[i]);
+            }
 }
 
 /*

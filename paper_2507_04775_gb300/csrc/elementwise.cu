@@ -1,0 +1,176 @@
+// Element-wise CKKS operations (Table I): HAdd, HSub, PtAdd, PtMult,
+// ScalarAdd and ScalarMult on ciphertexts in evaluation form, where a
+// polynomial product is the slot-wise product of evaluations and a constant
+// polynomial evaluates to itself everywhere.
+//
+// One kernel covers all six: a grid-stride loop over both polynomials of the
+// ciphertext, two words per thread per step with 16-byte loads and stores
+// (8-byte ones when a buffer is not 16-byte aligned).  The work is bound by
+// HBM: per word it reads one or two operands and writes one result.
+#include "fides_internal.cuh"
+
+namespace {
+
+enum ElemOp { E_HADD, E_HSUB, E_PTADD, E_PTMULT, E_SCALAR_ADD, E_SCALAR_MULT };
+
+struct ElemArgs {
+    const u64 *a;     // [2][nl][N]
+    const u64 *b;     // HADD / HSUB: [2][nl][N]; PTADD / PTMULT: [nl][N]
+    u64 *out;         // [2][nl][N] (may alias a or b: each word is read and written by one thread)
+    int nl, logN;
+    TwPair k[FIDES_MAX_PRIMES];   // scalar ops: residue of the constant per limb, with its Shoup companion
+};
+
+template <int OP>
+__device__ __forceinline__ u64 elem(u64 x, u64 y, int poly, const TwPair &k, const PrimeInfo &p)
+{
+    switch (OP) {
+    case E_HADD: return csub(x + y, p.q);
+    case E_HSUB: return csub(x + p.q - y, p.q);
+    case E_PTADD: return poly == 0 ? csub(x + y, p.q) : x;
+    case E_PTMULT: return mul_mod(x, y, p);
+    case E_SCALAR_ADD: return poly == 0 ? csub(x + k.w, p.q) : x;
+    default: return csub(mul_shoup(x, k, p.q), p.q);
+    }
+}
+
+// b's word for word w (polynomial poly, offset wi within it)
+template <int OP>
+__device__ __forceinline__ size_t b_index(size_t w, size_t wi)
+{
+    return (OP == E_HADD || OP == E_HSUB) ? w : wi;
+}
+
+template <int OP, bool VEC>
+__global__ void __launch_bounds__(256) k_elem(ElemArgs A, const PrimeInfo *__restrict__ P)
+{
+    pdl_enter();
+    const size_t S = (size_t)A.nl << A.logN;     // words of one polynomial
+    const size_t pairs = S;                      // 2 S words, two per step
+    const bool reads_b = OP == E_HADD || OP == E_HSUB || OP == E_PTADD || OP == E_PTMULT;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < pairs; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = 2 * v;
+        const int poly = w >= S;
+        const size_t wi = w - (poly ? S : 0);
+        const int z = (int)(wi >> A.logN);
+        const PrimeInfo p = P[z];
+        const TwPair k = (OP == E_SCALAR_ADD || OP == E_SCALAR_MULT) ? A.k[z] : TwPair{0, 0};
+        u64 x0, x1, y0 = 0, y1 = 0;
+        if (VEC) {
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.a + w);
+            x0 = x.x; x1 = x.y;
+            if (reads_b && !(OP == E_PTADD && poly)) {
+                const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(A.b + b_index<OP>(w, wi));
+                y0 = y.x; y1 = y.y;
+            }
+        } else {
+            x0 = A.a[w]; x1 = A.a[w + 1];
+            if (reads_b && !(OP == E_PTADD && poly)) {
+                y0 = A.b[b_index<OP>(w, wi)];
+                y1 = A.b[b_index<OP>(w, wi) + 1];
+            }
+        }
+        const u64 r0 = elem<OP>(x0, y0, poly, k, p), r1 = elem<OP>(x1, y1, poly, k, p);
+        if (VEC) {
+            *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
+        } else {
+            A.out[w] = r0;
+            A.out[w + 1] = r1;
+        }
+    }
+}
+
+template <int OP>
+int launch_elem(const fides_ctx *c, const ElemArgs &A, cudaStream_t st)
+{
+    const size_t pairs = (size_t)A.nl << A.logN;
+    const size_t want = (pairs + 255) / 256;
+    const unsigned blocks = (unsigned)std::min<size_t>(want, (size_t)c->sms * 8);
+    const bool vec = (((uintptr_t)A.a | (uintptr_t)A.b | (uintptr_t)A.out) & 15) == 0;
+    if (vec) FIDES_LAUNCH("k_elem", st, (k_elem<OP, true>), dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+    else FIDES_LAUNCH("k_elem", st, (k_elem<OP, false>), dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+    return fides_check_cuda(cudaGetLastError(), "element-wise launch");
+}
+
+int run_elem(fides_ctx *c, int op, const fides_ct *a, const uint64_t *b, const uint64_t *k, fides_ct *out,
+             double out_scale, void *stream, const char *fn)
+{
+    if (!c || !a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    const int nl = a->n_limbs;
+    if (nl < 1 || nl > c->L) return fides_set_error(FIDES_ERR_ARG, "%s: n_limbs=%d outside [1, %d]", fn, nl, c->L);
+    if (out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "%s: out->n_limbs must equal a->n_limbs", fn);
+    ElemArgs A;
+    memset(&A, 0, sizeof(A));
+    A.a = a->data;
+    A.b = b;
+    A.out = out->data;
+    A.nl = nl;
+    A.logN = c->logN;
+    if (op == E_SCALAR_ADD || op == E_SCALAR_MULT) {
+        if (!k) return fides_set_error(FIDES_ERR_ARG, "%s: constant is NULL", fn);
+        for (int i = 0; i < nl; ++i) {
+            const u64 q = c->primes[i];
+            if (k[i] >= q) return fides_set_error(FIDES_ERR_ARG, "%s: constant residue %d not below q_%d", fn, i, i);
+            A.k[i].w = k[i];
+            A.k[i].wp = (u64)(((unsigned __int128)k[i] << 64) / q);
+        }
+    } else if (!b) {
+        return fides_set_error(FIDES_ERR_ARG, "%s: second operand is NULL", fn);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    OpTrace tr(fn, st);
+    int rc;
+    switch (op) {
+    case E_HADD: rc = launch_elem<E_HADD>(c, A, st); break;
+    case E_HSUB: rc = launch_elem<E_HSUB>(c, A, st); break;
+    case E_PTADD: rc = launch_elem<E_PTADD>(c, A, st); break;
+    case E_PTMULT: rc = launch_elem<E_PTMULT>(c, A, st); break;
+    case E_SCALAR_ADD: rc = launch_elem<E_SCALAR_ADD>(c, A, st); break;
+    default: rc = launch_elem<E_SCALAR_MULT>(c, A, st); break;
+    }
+    if (!rc) out->scale = out_scale;
+    return rc;
+}
+
+int check_b(const fides_ct *a, const fides_ct *b, const char *fn)
+{
+    if (!b || !b->data) return fides_set_error(FIDES_ERR_ARG, "%s: b is NULL", fn);
+    if (a && b->n_limbs != a->n_limbs) return fides_set_error(FIDES_ERR_ARG, "%s: a and b at different levels", fn);
+    return FIDES_OK;
+}
+
+}  // namespace
+
+extern "C" int fides_hadd(fides_ctx *c, const fides_ct *a, const fides_ct *b, fides_ct *out, void *stream)
+{
+    if (int rc = check_b(a, b, "fides_hadd")) return rc;
+    return run_elem(c, E_HADD, a, b->data, nullptr, out, a ? a->scale : 0.0, stream, "op_hadd");
+}
+
+extern "C" int fides_hsub(fides_ctx *c, const fides_ct *a, const fides_ct *b, fides_ct *out, void *stream)
+{
+    if (int rc = check_b(a, b, "fides_hsub")) return rc;
+    return run_elem(c, E_HSUB, a, b->data, nullptr, out, a ? a->scale : 0.0, stream, "op_hsub");
+}
+
+extern "C" int fides_ptadd(fides_ctx *c, const fides_ct *a, const uint64_t *pt, fides_ct *out, void *stream)
+{
+    return run_elem(c, E_PTADD, a, pt, nullptr, out, a ? a->scale : 0.0, stream, "op_ptadd");
+}
+
+extern "C" int fides_ptmult(fides_ctx *c, const fides_ct *a, const uint64_t *pt, double pt_scale, fides_ct *out,
+                            void *stream)
+{
+    return run_elem(c, E_PTMULT, a, pt, nullptr, out, a ? a->scale * pt_scale : 0.0, stream, "op_ptmult");
+}
+
+extern "C" int fides_scalar_add(fides_ctx *c, const fides_ct *a, const uint64_t *k, fides_ct *out, void *stream)
+{
+    return run_elem(c, E_SCALAR_ADD, a, nullptr, k, out, a ? a->scale : 0.0, stream, "op_scalar_add");
+}
+
+extern "C" int fides_scalar_mult(fides_ctx *c, const fides_ct *a, const uint64_t *k, double k_scale, fides_ct *out,
+                                 void *stream)
+{
+    return run_elem(c, E_SCALAR_MULT, a, nullptr, k, out, a ? a->scale * k_scale : 0.0, stream, "op_scalar_mult");
+}

@@ -256,6 +256,7 @@ struct IPOp {
     const u64 *evk;     // [dnum][2][L+K][N]
     u64 *acc;           // [2][ne][N]
     int nl, ne, beta, alpha;
+    u64 g;              // 0, or the Galois element through which the digits are read (hoisted rotation)
 };
 
 // One op inline (dop == nullptr; grid.y = its ne limbs) or a device table of
@@ -280,13 +281,21 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const u64 *__restrict__ ext = op.ext;
     const u64 *__restrict__ evk = op.evk;
     const u64 *__restrict__ dsrc = op.dsrc;
+    // hoisted rotation: the digits are read through sigma_g (evaluation form:
+    // slot n takes slot brv(((2 brv(n) + 1) g mod 2N - 1) / 2))
+    size_t sn = n;
+    if (op.g) {
+        const u32 rn = __brev((u32)n) >> (32 - logN);
+        const u64 e2 = ((2 * (u64)rn + 1) * op.g) & ((2ull << logN) - 1);
+        sn = __brev((u32)((e2 - 1) >> 1)) >> (32 - logN);
+    }
     // issue every load before the first product (the kernel is bound by HBM)
     u64 e[MAXB], k0[MAXB], k1[MAXB];
 #pragma unroll
     for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
             const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
-            e[j] = src[n];
+            e[j] = src[sn];
             k0[j] = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
             k1[j] = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
         }

@@ -192,25 +192,91 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     return rc;
 }
 
-extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out,
-                            void *stream)
+// sigma_g of a ciphertext with key switching (HRotate, Conjugate)
+static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_t *rk, fides_ct *out, void *stream,
+                           const char *fn, const char *trace)
 {
-    if (int rc = check_ctx(c, "fides_rotate")) return rc;
-    if (!a || !out || !rk || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "fides_rotate: NULL argument");
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!a || !out || !rk || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
     const int nl = a->n_limbs;
-    if (int rc = check_level(c, nl, "fides_rotate")) return rc;
-    if (out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "fides_rotate: level mismatch");
+    if (int rc = check_level(c, nl, fn)) return rc;
+    if (out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "%s: level mismatch", fn);
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
-    OpTrace op("op_rotate", st);
+    OpTrace op(trace, st);
     KsBuffers B = ks_buffers(c, carve(c).dsrc, nl, rk, out->data, out->data + S, 1, 0, carve(c));
     B.prep = 2;
     B.pa = a->data;
     B.pout = out->data;
-    B.g = fides_galois_elt(c, steps);
+    B.g = g;
     int rc = run_keyswitch(c, B, st);
     if (!rc) out->scale = a->scale;
     return rc;
+}
+
+extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out,
+                            void *stream)
+{
+    if (int rc = check_ctx(c, "fides_rotate")) return rc;
+    return automorph_entry(c, a, fides_galois_elt(c, steps), rk, out, stream, "fides_rotate", "op_rotate");
+}
+
+extern "C" int fides_conjugate(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fides_ct *out, void *stream)
+{
+    if (int rc = check_ctx(c, "fides_conjugate")) return rc;
+    return automorph_entry(c, a, 2 * (u64)c->N - 1, ck, out, stream, "fides_conjugate", "op_conjugate");
+}
+
+extern "C" int fides_hsquare(fides_ctx *c, const fides_ct *a, const uint64_t *rlk, fides_ct *out, void *stream)
+{
+    return fides_hmult(c, a, a, rlk, out, stream);
+}
+
+extern "C" int fides_rotate_hoisted(fides_ctx *c, const fides_ct *a, int n_rot, const int64_t *steps,
+                                    const uint64_t *const *rks, fides_ct *outs, void *stream)
+{
+    const char *fn = "fides_rotate_hoisted";
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!a || !a->data || !steps || !rks || !outs) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    if (n_rot < 1 || n_rot > 64) return fides_set_error(FIDES_ERR_ARG, "%s: n_rot=%d outside [1, 64]", fn, n_rot);
+    const int nl = a->n_limbs;
+    if (int rc = check_level(c, nl, fn)) return rc;
+    for (int k = 0; k < n_rot; ++k) {
+        if (!rks[k] || !outs[k].data) return fides_set_error(FIDES_ERR_ARG, "%s: rotation %d: NULL key or output", fn, k);
+        if (outs[k].n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "%s: rotation %d: level mismatch", fn, k);
+    }
+    const size_t S = (size_t)nl * c->N;
+    cudaStream_t st = as_stream(stream);
+    OpTrace op("op_rotate_hoisted", st);
+    // one ModUp of c1 (the INTT reads c1 itself; the digits' own limbs are c1's)
+    KsBuffers B = ks_buffers(c, a->data + S, nl, nullptr, nullptr, nullptr, 0, 0, carve(c));
+    if (int rc = run_modup(c, B, st)) return rc;
+    for (int k = 0; k < n_rot; ++k) {
+        B.evk = rks[k];
+        B.out0 = outs[k].data;
+        B.out1 = outs[k].data + S;
+        const u64 g = fides_galois_elt(c, steps[k]);
+        IPArgs ip;
+        memset(&ip, 0, sizeof(ip));
+        ip.one = ks_ip_op(c, B);
+        ip.one.g = g;
+        if (int rc = launch_inner(c, ip, nl + c->K, ks_beta(c, nl), st)) return rc;
+        std::vector<Seg> v;
+        std::vector<BConvJob> jb;
+        ks_pinv_segs(c, B, v);
+        if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
+        ks_moddown_jobs(c, B, jb);
+        if (int rc = launch_bconv(c, inline_bconv(jb), st)) return rc;
+        v.clear();
+        ks_final_segs(c, B, v);
+        v[0].mode = 2;                  // out0 = sigma_g(c0) + P^-1 (acc0 - conv0)
+        v[0].side = const_cast<u64 *>(a->data);
+        v[0].g = g;
+        v[1].mode = 0;                  // out1 = P^-1 (acc1 - conv1)
+        if (int rc = ntt_forward(c, inline_set(v), ProSrc{}, EpiSubMulRot{}, st)) return rc;
+        outs[k].scale = a->scale;
+    }
+    return FIDES_OK;
 }
 
 extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)

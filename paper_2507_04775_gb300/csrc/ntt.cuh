@@ -159,6 +159,32 @@ struct EpiSubMul {
     }
 };
 
+// As EpiSubMul, but a segment of mode 2 adds side[sigma_g(j)], the
+// automorphism of another polynomial gathered in evaluation form (the
+// ModDown of a hoisted rotation adds sigma(c0) this way).  A separate functor
+// so that the common epilogue keeps its registers.
+struct EpiSubMulRot {
+    static constexpr bool kRaw = false;
+    int logN;
+    __device__ __forceinline__ void load(const Job &J, u32 j, u64 &a, u64 &o) const
+    {
+        a = J.aux[j];
+        o = 0;
+        if (J.mode == 2) {
+            const u32 rj = __brev(j) >> (32 - logN);
+            const u64 e = ((2 * (u64)rj + 1) * J.g) & ((2ull << logN) - 1);
+            o = J.side[__brev((u32)((e - 1) >> 1)) >> (32 - logN)];
+        }
+    }
+    __device__ __forceinline__ void store(const Job &J, u32 j, u64 v, u64 a, u64 o, const PrimeInfo &p) const
+    {
+        u64 y = csub(v, p.q);
+        u64 r = csub(mul_shoup(a + p.q - y, J.cst[J.prime], p.q), p.q);
+        if (J.mode == 2) r = csub(r + o, p.q);
+        J.out[j] = r;
+    }
+};
+
 // One round of four radix-2 stages on the thread's 16 registers.
 // X: the global-index bits above the round (see the header comment);
 // TWS: twiddles come from shared memory (index < 256) instead of global.
@@ -324,6 +350,7 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
 int ntt_fwd_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProSrc, EpiCanon
 int ntt_fwd_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);          // ProSrc, EpiSubMul
 int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);   // ProSwitchMod, EpiSubMul
+int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &set, cudaStream_t st);      // ProSrc, EpiSubMulRot
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep, EpiCanon
 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
@@ -337,6 +364,10 @@ inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiSubMul, 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSwitchMod, EpiSubMul, cudaStream_t st)
 {
     return ntt_fwd_switch_submul(c, s, st);
+}
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiSubMulRot, cudaStream_t st)
+{
+    return ntt_fwd_submul_rot(c, s, st);
 }
 inline int ntt_inverse(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {

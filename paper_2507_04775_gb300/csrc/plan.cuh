@@ -118,6 +118,7 @@ inline IPOp ks_ip_op(const fides_ctx *c, const KsBuffers &B)
     IPOp o;
     o.ext = B.ext; o.dsrc = B.d; o.evk = B.evk; o.acc = B.acc;
     o.nl = B.nl; o.ne = B.nl + c->K; o.beta = ks_beta(c, B.nl); o.alpha = c->alpha;
+    o.g = 0;
     return o;
 }
 

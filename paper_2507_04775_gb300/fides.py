@@ -33,7 +33,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ctx_ntt_tile", "fides_server_create", "fides_server_destroy", "fides_server_set_relin_key",
            "fides_server_add_rotation_key", "fides_server_submit", "fides_server_poll", "fides_server_release",
            "fides_server_cancel", "fides_server_pause", "fides_server_inject", "fides_server_stats_read",
-           "fides_now_ns"]
+           "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
+           "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -145,6 +146,15 @@ def lib():
         L.fides_server_inject.argtypes = [_vp, _i, ctypes.c_int64]
         L.fides_server_stats_read.argtypes = [_vp, ctypes.POINTER(fides_server_stats)]
         L.fides_now_ns.restype = ctypes.c_int64
+        L.fides_hsquare.argtypes = [_vp, ctp, _vp, ctp, _vp]
+        L.fides_conjugate.argtypes = [_vp, ctp, _vp, ctp, _vp]
+        L.fides_rotate_hoisted.argtypes = [_vp, ctp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp), ctp, _vp]
+        L.fides_hadd.argtypes = [_vp, ctp, ctp, ctp, _vp]
+        L.fides_hsub.argtypes = [_vp, ctp, ctp, ctp, _vp]
+        L.fides_ptadd.argtypes = [_vp, ctp, _vp, ctp, _vp]
+        L.fides_ptmult.argtypes = [_vp, ctp, _vp, ctypes.c_double, ctp, _vp]
+        L.fides_scalar_add.argtypes = [_vp, ctp, _u64p, ctp, _vp]
+        L.fides_scalar_mult.argtypes = [_vp, ctp, _u64p, ctypes.c_double, ctp, _vp]
         _lib = L
     return _lib
 
@@ -311,6 +321,76 @@ class Context:
     def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
         _check(lib().fides_rescale(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def hsquare(self, a, n_limbs: int, rlk, out, scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_hsquare(self._h, ctypes.byref(ca), _ptr(rlk, self.key_words(), "rlk"), ctypes.byref(co),
+                                   _stream(stream)))
+        return co.scale
+
+    def conjugate(self, a, n_limbs: int, ck, out, scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_conjugate(self._h, ctypes.byref(ca), _ptr(ck, self.key_words(), "ck"), ctypes.byref(co),
+                                     _stream(stream)))
+        return co.scale
+
+    def rotate_hoisted(self, a, n_limbs: int, steps, rks, outs, scale: float = 1.0, stream=None):
+        """Rotations of `a` by every steps[k] (key rks[k], output outs[k]) sharing one ModUp."""
+        n = len(steps)
+        if len(rks) != n or len(outs) != n:
+            raise ValueError("steps, rks and outs must have the same length")
+        ca = self._ct(a, n_limbs, scale, "a")
+        st = (ctypes.c_int64 * n)(*steps)
+        keys = (_vp * n)(*[_ptr(k, self.key_words(), "rk").value for k in rks])
+        cts = (fides_ct * n)(*[self._ct(o, n_limbs, 0.0, "out") for o in outs])
+        _check(lib().fides_rotate_hoisted(self._h, ctypes.byref(ca), n, st, keys, cts, _stream(stream)))
+
+    def _ct2(self, fn, a, b, n_limbs, out, scale, stream):
+        ca, cb = self._ct(a, n_limbs, scale, "a"), self._ct(b, n_limbs, scale, "b")
+        co = self._ct(out, n_limbs, 0.0, "out")
+        _check(fn(self._h, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def hadd(self, a, b, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        return self._ct2(lib().fides_hadd, a, b, n_limbs, out, scale, stream)
+
+    def hsub(self, a, b, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        return self._ct2(lib().fides_hsub, a, b, n_limbs, out, scale, stream)
+
+    def ptadd(self, a, pt, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_ptadd(self._h, ctypes.byref(ca), _ptr(pt, n_limbs * self.N, "pt"), ctypes.byref(co),
+                                 _stream(stream)))
+        return co.scale
+
+    def ptmult(self, a, pt, n_limbs: int, out, scale: float = 1.0, pt_scale: float = 1.0, stream=None) -> float:
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_ptmult(self._h, ctypes.byref(ca), _ptr(pt, n_limbs * self.N, "pt"), pt_scale,
+                                  ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def _consts(self, k, n_limbs):
+        if isinstance(k, int):
+            k = [k % q for q in self.q[:n_limbs]]
+        arr = np.ascontiguousarray(k, dtype=np.uint64)
+        if arr.size < n_limbs:
+            raise ValueError("constant needs %d residues" % n_limbs)
+        return arr
+
+    def scalar_add(self, a, k, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+        """k: a Python int (reduced modulo each q_i) or its residues per limb."""
+        arr = self._consts(k, n_limbs)
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_scalar_add(self._h, ctypes.byref(ca), arr.ctypes.data_as(_u64p), ctypes.byref(co),
+                                      _stream(stream)))
+        return co.scale
+
+    def scalar_mult(self, a, k, n_limbs: int, out, scale: float = 1.0, k_scale: float = 1.0, stream=None) -> float:
+        arr = self._consts(k, n_limbs)
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_scalar_mult(self._h, ctypes.byref(ca), arr.ctypes.data_as(_u64p), k_scale,
+                                       ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def rescale_noalloc(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:

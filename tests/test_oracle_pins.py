@@ -412,3 +412,124 @@ def test_lower_level_hmult(mid):
     b = cl.encrypt(z2, 5, 2.0**40)
     out = mid.hmult(a, b, cl.relin_key())
     assert _rel_err(cl.decrypt(out, 2.0**80), z1 * z2) < 2.0**-20
+
+
+# ------------------------------------------- Table I element-wise ops, Conjugate, HSquare
+def _negacyclic(a, b, q):
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            if i + j < N:
+                out[i + j] += a[i] * b[j]
+            else:
+                out[i + j - N] -= a[i] * b[j]
+    return [x % q for x in out]
+
+
+def test_ptmult_is_the_negacyclic_ring_product(tiny):
+    """In evaluation form the slot-wise product is the product in
+    Z_q[X]/(X^N + 1): checked against the schoolbook product of the
+    coefficient forms, in Python integers."""
+    c = tiny
+    st = si.Stream(71)
+    a = np.stack([si.uniform_poly(st, c.q, c.N) for _ in range(2)])
+    pt = si.uniform_poly(st, c.q, c.N)
+    out = c.ptmult(a, pt)
+    idx = list(range(c.nq))
+    cp = c.intt_limbs(pt, idx)
+    for t in range(2):
+        ca, co = c.intt_limbs(a[t], idx), c.intt_limbs(out[t], idx)
+        for i in range(c.nq):
+            assert [int(x) for x in co[i]] == _negacyclic([int(x) for x in ca[i]], [int(x) for x in cp[i]], c.q[i])
+
+
+def test_additive_and_scalar_ops_are_crt_identities(mid):
+    """Each limb is the residue of one big integer modulo Q = prod q_i:
+    HAdd/HSub/PtAdd/ScalarAdd/ScalarMult must act on those integers."""
+    c = mid
+    nl = 7
+    st = si.Stream(72)
+    a = np.stack([si.uniform_poly(st, c.q[:nl], c.N) for _ in range(2)])
+    b = np.stack([si.uniform_poly(st, c.q[:nl], c.N) for _ in range(2)])
+    pt = si.uniform_poly(st, c.q[:nl], c.N)
+    Q = 1
+    for q in c.q[:nl]:
+        Q *= q
+    K = random.Random(5).randrange(Q)
+    k = np.array([K % q for q in c.q[:nl]], dtype=np.uint64)
+    cols = range(0, c.N, 97)
+
+    def big(x):
+        return oracle.crt(x[:, cols], c.q[:nl])
+
+    A0, A1, B0, B1, PT = big(a[0]), big(a[1]), big(b[0]), big(b[1]), big(pt)
+    h, s = c.hadd(a, b), c.hsub(a, b)
+    assert big(h[0]) == [(x + y) % Q for x, y in zip(A0, B0)] and big(h[1]) == [(x + y) % Q for x, y in zip(A1, B1)]
+    assert big(s[0]) == [(x - y) % Q for x, y in zip(A0, B0)] and big(s[1]) == [(x - y) % Q for x, y in zip(A1, B1)]
+    p = c.ptadd(a, pt)
+    assert big(p[0]) == [(x + y) % Q for x, y in zip(A0, PT)] and np.array_equal(p[1], a[1])
+    sa = c.scalar_add(a, k)
+    assert big(sa[0]) == [(x + K) % Q for x in A0] and np.array_equal(sa[1], a[1])
+    sm = c.scalar_mult(a, k)
+    assert big(sm[0]) == [x * K % Q for x in A0] and big(sm[1]) == [x * K % Q for x in A1]
+    pm = c.ptmult(a, pt)
+    assert big(pm[1]) == [x * y % Q for x, y in zip(A1, PT)]
+
+
+def test_elementwise_ops_decrypt_to_slot_arithmetic(small, small_client):
+    cl, D = small_client, 2.0 ** 40
+    nl = small.nq
+    z1, z2 = cl.random_slots(), cl.random_slots()
+    a, b = cl.encrypt(z1, nl, D), cl.encrypt(z2, nl, D)
+    assert _rel_err(cl.decrypt(small.hadd(a, b), D), z1 + z2) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.hsub(a, b), D), z1 - z2) < 2.0 ** -20
+    pt = cl.encode_eval(z2, nl, D)
+    assert _rel_err(cl.decrypt(small.ptadd(a, pt), D), z1 + z2) < 2.0 ** -20
+    pm = small.ptmult(a, pt)
+    assert _rel_err(cl.decrypt(pm, D * D), z1 * z2) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.rescale(pm), D * D / small.q[nl - 1]), z1 * z2) < 2.0 ** -20
+    x = 0.3711
+    assert _rel_err(cl.decrypt(small.scalar_add(a, cl.const_residues(x, nl, D)), D), z1 + x) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.scalar_mult(a, cl.const_residues(3, nl, 1.0)), D), 3 * z1) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.scalar_mult(a, cl.const_residues(x, nl, D)), D * D), x * z1) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.hsquare(a, cl.relin_key()), D * D), z1 * z1) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.conjugate(a, cl.conjugation_key()), D), np.conj(z1)) < 2.0 ** -20
+
+
+# ------------------------------------------------------------- hoisted rotations
+def test_hoisted_rotation_without_automorphism_is_the_key_switch(small, small_client):
+    """steps = 0 (g = 1): one shared ModUp, inner product, ModDown and + c0 are
+    exactly the single rotation's key switch, residue for residue."""
+    cl = small_client
+    z = cl.random_slots()
+    ct = cl.encrypt(z, small.nq, 2.0 ** 40)
+    rk0 = cl.rotation_key(0)
+    (h,) = small.rotate_hoisted(ct, [0], [rk0])
+    assert np.array_equal(h, small.rotate(ct, 0, rk0))
+
+
+def test_hoisted_rotations_decrypt_to_rotations(small, small_client):
+    cl, D = small_client, 2.0 ** 40
+    z = cl.random_slots()
+    ct = cl.encrypt(z, small.nq, D)
+    steps = [1, 2, -1, 5]
+    keys = [cl.rotation_key(k) for k in steps]
+    outs = small.rotate_hoisted(ct, steps, keys)
+    for k, o, rk in zip(steps, outs, keys):
+        assert _rel_err(cl.decrypt(o, D), np.roll(z, -k)) < 2.0 ** -20, k
+        # same message as the unhoisted rotation, different residues
+        plain = small.rotate(ct, k, rk)
+        assert _rel_err(cl.decrypt(o, D), cl.decrypt(plain, D)) < 2.0 ** -20
+
+
+def test_hoisted_rotation_at_ragged_levels(mid):
+    cl = Client(mid, seed=23)
+    D = 2.0 ** 40
+    z = cl.random_slots()
+    for nl in (12, 6, 1):
+        ct = cl.encrypt(z, nl, D)
+        steps = [3, -7]
+        outs = mid.rotate_hoisted(ct, steps, [cl.rotation_key(k) for k in steps])
+        for k, o in zip(steps, outs):
+            assert _rel_err(cl.decrypt(o, D), np.roll(z, -k)) < 2.0 ** -20, (nl, k)
