@@ -53,7 +53,7 @@ extern "C" {
 #define FIDES_ERR_CUDA (-4)         /* a CUDA call failed */
 #define FIDES_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
 #define FIDES_ERR_PRIME (-6)        /* a modulus is not an NTT-friendly prime */
-#define FIDES_ERR_KEY (-7)          /* request server: no key registered for the request */
+#define FIDES_ERR_KEY (-7)          /* no key for a request or a rotation the operation needs */
 #define FIDES_ERR_BUSY (-8)         /* request server: queue full, or request no longer queued */
 #define FIDES_ERR_CANCELLED (-9)    /* request server: the request was cancelled before it ran */
 
@@ -215,6 +215,31 @@ int fides_conjugate(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_ck, f
  */
 int fides_rotate_hoisted(fides_ctx *ctx, const fides_ct *a, int n_rot, const int64_t *steps,
                          const uint64_t *const *dev_rks, fides_ct *outs, void *stream);
+
+/*
+ * Linear transform of the slots (the diagonal method with a baby-step
+ * giant-step split; bootstrapping's CoeffToSlot / SlotToCoeff, Sec. III-F7,
+ * with hoisted baby steps, Sec. III-F6):
+ *   y = sum_i d_i (.) rot_i(z) = sum_g rot_{n1 g}( sum_b pt_{g,b} (.) rot_b(z) ),
+ * i = n1 g + b, 0 <= b < n1, rot_k = rotation left by k slots.
+ *   diag_idx : host [n_diag], the diagonal indices i in use, in [0, N/2), distinct
+ *   pts      : host [n_diag] of device plaintexts [n_limbs][N] (evaluation form):
+ *              pts[k] encodes rot_{-n1 floor(i/n1)}(d_i) for i = diag_idx[k]
+ *              at scale pt_scale (pre-rotated, as the split requires)
+ *   keys     : host arrays [n_keys] of step counts and device rotation keys;
+ *              one is needed for every baby step b != 0 and every giant step
+ *              n1 g != 0 in use (FIDES_ERR_KEY before anything is queued if not)
+ *   work     : device scratch of fides_linear_transform_work_words() words
+ *   out      : result at a's level, scale a->scale * pt_scale; may not alias a
+ * The residues equal those of: hoisted rotations of a by the baby steps, a
+ * plaintext multiply-accumulate per giant step, HRotate by n1 g, HAdd.
+ */
+int fides_linear_transform_work_words(fides_ctx *ctx, int n_limbs, int n_diag, const int *diag_idx, int n1,
+                                      size_t *words);
+int fides_linear_transform(fides_ctx *ctx, const fides_ct *a, int n_diag, const int *diag_idx,
+                           const uint64_t *const *dev_pts, double pt_scale, int n1, int n_keys,
+                           const int64_t *key_steps, const uint64_t *const *dev_keys, uint64_t *dev_work,
+                           size_t work_words, fides_ct *out, void *stream);
 
 /*
  * Element-wise operations (Table I) on ciphertexts in evaluation form; out

@@ -85,6 +85,9 @@ def lib():
         L.or_conjugate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p, _u64p]
         L.or_rotate_hoisted.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _u64p,
                                         _u64p]
+        L.or_linear_transform.restype = ctypes.c_int
+        L.or_linear_transform.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int, _intp, _u64p,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _u64p, _u64p]
         for name in ("or_hadd", "or_hsub", "or_ptadd", "or_ptmult", "or_scalar_add", "or_scalar_mult"):
             getattr(L, name).argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _u64p]
         L.or_from_signed.argtypes = [ctypes.c_void_p, _i64p, _intp, ctypes.c_int, _u64p]
@@ -249,6 +252,21 @@ class Context:
         keys = _u64(np.stack([_u64(k) for k in rks]))
         out = np.empty((len(st), 2, nl, self.N), dtype=np.uint64)
         lib().or_rotate_hoisted(self._h, _p(a), nl, len(st), st.ctypes.data, _p(keys), _p(out)); return out
+
+    def linear_transform(self, a, diag_idx, pts, n1: int, keys: dict) -> np.ndarray:
+        """BSGS diagonal-method linear transform: pts[k] is the plaintext of
+        rot_{-n1 floor(i/n1)}(d_i) for i = diag_idx[k]; keys: {steps: key}."""
+        a = _u64(a); nl = a.shape[1]
+        di = _i32(diag_idx)
+        p = _u64(np.stack([_u64(x) for x in pts]))
+        ks = np.ascontiguousarray(list(keys), dtype=np.int64)
+        kk = _u64(np.stack([_u64(keys[k]) for k in keys])) if keys else np.zeros(1, dtype=np.uint64)
+        out = np.empty_like(a)
+        rc = lib().or_linear_transform(self._h, _p(a), nl, len(di), _p(di), _p(p), n1, len(ks), ks.ctypes.data,
+                                       _p(kk), _p(out))
+        if rc != 0:
+            raise KeyError("a rotation key of the transform is missing")
+        return out
 
     def hsquare(self, a, rlk) -> np.ndarray:
         return self.hmult(a, a, rlk)

@@ -62,6 +62,14 @@ class Client:
         idx = list(range(nl))
         return c.ntt_limbs(c.from_signed(encode(z, c.N, scale), idx), idx)
 
+    def encode_diagonals(self, diags: dict, n1: int, nl: int, scale: float):
+        """Plaintexts of a diagonal-method linear transform with baby step n1:
+        diagonal i (slots d_i, y = sum_i d_i * rot_i(z)) is encoded pre-rotated
+        by -n1 floor(i / n1).  Returns (indices, plaintexts)."""
+        idx = sorted(diags)
+        pts = [self.encode_eval(np.roll(np.asarray(diags[i]), n1 * (i // n1)), nl, scale) for i in idx]
+        return idx, pts
+
     def const_residues(self, x: float, nl: int, scale: float) -> np.ndarray:
         """Residues of round(x * scale) modulo q_0..q_{nl-1}."""
         v = int(round(x * scale))

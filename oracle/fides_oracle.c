@@ -690,6 +690,84 @@ void or_scalar_mult(const or_ctx *c, const u64 *a, const u64 *k, int nl, u64 *ou
 }
 
 /*
+ * Linear transform of the slots with the baby-step giant-step split of the
+ * diagonal method (Sec. III-F7 bootstrapping's CoeffToSlot / SlotToCoeff,
+ * whose baby steps are the hoisted rotations of Sec. III-F6):
+ *   y = sum_i d_i (.) rot_i(z) = sum_g rot_{n1 g}( sum_b pt_{g,b} (.) rot_b(z) ),
+ * i = n1 g + b, 0 <= b < n1, with pt_{g,b} the plaintext of rot_{-n1 g}(d_i)
+ * (the caller encodes it pre-rotated).  The baby-step rotations b != 0 share
+ * one ModUp (or_rotate_hoisted); each giant step g != 0 is one HRotate.
+ *   diag_idx[n_diag]   : diagonal indices i in [0, N/2), distinct
+ *   pts                : [n_diag][nl][N], pts[k] the plaintext of diagonal diag_idx[k]
+ *   key_steps, keys    : n_keys rotation keys [dnum][2][nq + K][N] by step count
+ *   out                : [2][nl][N]
+ * Returns 0, or -1 if a needed rotation key is missing.
+ */
+static const u64 *find_key(const or_ctx *c, int n_keys, const i64 *key_steps, const u64 *keys, i64 steps)
+{
+    i64 half = (i64)(c->N / 2), want = ((steps % half) + half) % half;
+    u64 key_words = (u64)c->dnum * 2 * (c->nq + c->nk) * c->N;
+    for (int k = 0; k < n_keys; k++)
+        if ((((key_steps[k] % half) + half) % half) == want) return keys + (u64)k * key_words;
+    return NULL;
+}
+
+int or_linear_transform(const or_ctx *c, const u64 *a, int nl, int n_diag, const int *diag_idx, const u64 *pts,
+                        int n1, int n_keys, const i64 *key_steps, const u64 *keys, u64 *out)
+{
+    u64 N = c->N, S = (u64)nl * N;
+    int half = (int)(N / 2), n_giant = (half + n1 - 1) / n1;
+    u64 key_words = (u64)c->dnum * 2 * (c->nq + c->nk) * N;
+    /* baby steps in use */
+    int *baby_used = (int *)calloc(n1, sizeof(int));
+    for (int k = 0; k < n_diag; k++) baby_used[diag_idx[k] % n1] = 1;
+    int n_rot = 0;
+    i64 *steps = (i64 *)malloc(sizeof(i64) * n1);
+    u64 *rkeys = (u64 *)malloc(sizeof(u64) * (n1 > 1 ? n1 : 1) * key_words);
+    for (int b = 1; b < n1; b++) {
+        if (!baby_used[b]) continue;
+        const u64 *k = find_key(c, n_keys, key_steps, keys, b);
+        if (!k) { free(baby_used); free(steps); free(rkeys); return -1; }
+        memcpy(rkeys + (u64)n_rot * key_words, k, sizeof(u64) * key_words);
+        steps[n_rot++] = b;
+    }
+    u64 *rot = (u64 *)malloc(sizeof(u64) * (n_rot > 0 ? n_rot : 1) * 2 * S);
+    if (n_rot) or_rotate_hoisted(c, a, nl, n_rot, steps, rkeys, rot);
+    /* rotated copy of b, by baby step */
+    const u64 **baby = (const u64 **)calloc(n1, sizeof(u64 *));
+    baby[0] = a;
+    for (int r = 0; r < n_rot; r++) baby[steps[r]] = rot + (u64)r * 2 * S;
+    u64 *inner = (u64 *)malloc(sizeof(u64) * 2 * S);
+    u64 *term = (u64 *)malloc(sizeof(u64) * 2 * S);
+    u64 *prod = (u64 *)malloc(sizeof(u64) * 2 * S);
+    int have_out = 0, rc = 0;
+    for (int g = 0; g < n_giant && !rc; g++) {
+        int have_inner = 0;
+        for (int k = 0; k < n_diag; k++) {
+            if (diag_idx[k] / n1 != g) continue;
+            or_ptmult(c, baby[diag_idx[k] % n1], pts + (u64)k * S, nl, prod);
+            if (have_inner) or_hadd(c, inner, prod, nl, inner);
+            else memcpy(inner, prod, sizeof(u64) * 2 * S);
+            have_inner = 1;
+        }
+        if (!have_inner) continue;
+        if (g == 0) {
+            memcpy(term, inner, sizeof(u64) * 2 * S);
+        } else {
+            const u64 *k = find_key(c, n_keys, key_steps, keys, (i64)n1 * g);
+            if (!k) { rc = -1; break; }
+            or_rotate(c, inner, nl, (i64)n1 * g, k, term);
+        }
+        if (have_out) or_hadd(c, out, term, nl, out);
+        else memcpy(out, term, sizeof(u64) * 2 * S);
+        have_out = 1;
+    }
+    if (!have_out && !rc) memset(out, 0, sizeof(u64) * 2 * S);
+    free(baby_used); free(steps); free(rkeys); free(rot); free(baby); free(inner); free(term); free(prod);
+    return rc;
+}
+
+/*
  * Rescale (Table I; Sec. III-F5 "Rescale fusion"): with l = nl - 1, INTT limb
  * l, take its canonical [0, q_l) representative modulo each q_i (SwitchModulo),
  * NTT under q_i, and return q_l^-1 (x_i - that) mod q_i for i < l.

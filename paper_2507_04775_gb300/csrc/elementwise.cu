@@ -7,6 +7,9 @@
 // ciphertext, two words per thread per step with 16-byte loads and stores
 // (8-byte ones when a buffer is not 16-byte aligned).  The work is bound by
 // HBM: per word it reads one or two operands and writes one result.
+#include <algorithm>
+#include <cstring>
+
 #include "fides_internal.cuh"
 
 namespace {
@@ -173,4 +176,85 @@ extern "C" int fides_scalar_mult(fides_ctx *c, const fides_ct *a, const uint64_t
                                  void *stream)
 {
     return run_elem(c, E_SCALAR_MULT, a, nullptr, k, out, a ? a->scale * k_scale : 0.0, stream, "op_scalar_mult");
+}
+
+// ---------------------------------------------------------------------------
+// Plaintext multiply-accumulate: out = sum_t ct_t (.) pt_t (+ out), the inner
+// sum of a baby-step giant-step linear transform, with one 128-bit
+// accumulator per word and one reduction at the end.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct MacArgs {
+    const u64 *ct[FIDES_MAC_TERMS];   // [2][nl][N] each
+    const u64 *pt[FIDES_MAC_TERMS];   // [nl][N] each
+    u64 *out;                         // [2][nl][N]
+    int nt, nl, logN, accumulate;
+};
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_ptmac(MacArgs A, const PrimeInfo *__restrict__ P)
+{
+    pdl_enter();
+    const size_t S = (size_t)A.nl << A.logN;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < S; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = 2 * v;
+        const size_t wi = w - (w >= S ? S : 0);
+        const PrimeInfo p = P[(int)(wi >> A.logN)];
+        U128 s0 = {0, 0}, s1 = {0, 0};
+        if (A.accumulate) {
+            s0.lo = A.out[w];
+            s1.lo = A.out[w + 1];
+        }
+        for (int t = 0; t < A.nt; ++t) {
+            u64 x0, x1, y0, y1;
+            if (VEC) {
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.ct[t] + w);
+                const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(A.pt[t] + wi);
+                x0 = x.x; x1 = x.y; y0 = y.x; y1 = y.y;
+            } else {
+                x0 = A.ct[t][w]; x1 = A.ct[t][w + 1];
+                y0 = A.pt[t][wi]; y1 = A.pt[t][wi + 1];
+            }
+            mac128(s0, x0, y0);
+            mac128(s1, x1, y1);
+        }
+        const u64 r0 = reduce128(s0.hi, s0.lo, p), r1 = reduce128(s1.hi, s1.lo, p);
+        if (VEC) {
+            *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
+        } else {
+            A.out[w] = r0;
+            A.out[w + 1] = r1;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_ptmac(const fides_ctx *c, const u64 *const *cts, const u64 *const *pts, int nt, u64 *out, int nl,
+                 bool accumulate, cudaStream_t st)
+{
+    for (int t0 = 0; t0 < nt; t0 += FIDES_MAC_TERMS) {
+        MacArgs A;
+        memset(&A, 0, sizeof(A));
+        A.nt = std::min(FIDES_MAC_TERMS, nt - t0);
+        uintptr_t align = (uintptr_t)out;
+        for (int t = 0; t < A.nt; ++t) {
+            A.ct[t] = cts[t0 + t];
+            A.pt[t] = pts[t0 + t];
+            align |= (uintptr_t)A.ct[t] | (uintptr_t)A.pt[t];
+        }
+        A.out = out;
+        A.nl = nl;
+        A.logN = c->logN;
+        A.accumulate = (accumulate || t0 > 0) ? 1 : 0;
+        const size_t S = (size_t)nl << c->logN;
+        const unsigned blocks = (unsigned)std::min<size_t>((S + 255) / 256, (size_t)c->sms * 8);
+        if ((align & 15) == 0)
+            FIDES_LAUNCH("k_ptmac", st, k_ptmac<true>, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+        else
+            FIDES_LAUNCH("k_ptmac", st, k_ptmac<false>, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+        if (int rc = fides_check_cuda(cudaGetLastError(), "plaintext multiply-accumulate launch")) return rc;
+    }
+    return FIDES_OK;
 }

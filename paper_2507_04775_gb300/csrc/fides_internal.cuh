@@ -29,6 +29,7 @@ typedef uint32_t u32;
 #define FIDES_MAX_DIGITS 8
 #define FIDES_MAX_SRC 32
 #define FIDES_TUNE_MAX 128   // NTT tile variants are kept per limb count up to this
+#define FIDES_MAC_TERMS 32   // products one plaintext multiply-accumulate launch sums (each < 2^122)
 
 // A twiddle or constant with its Shoup companion.
 struct __align__(16) TwPair {
@@ -230,6 +231,11 @@ __device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
 // ---------------------------------------------------------------------------
 int fides_set_error(int code, const char *fmt, ...);
 int fides_check_cuda(cudaError_t e, const char *what);
+
+// out = sum_t cts[t] (.) pts[t] (+ out when accumulate), ciphertexts [2][nl][N]
+// and plaintexts [nl][N] in evaluation form (elementwise.cu)
+int launch_ptmac(const fides_ctx *c, const u64 *const *cts, const u64 *const *pts, int nt, u64 *out, int nl,
+                 bool accumulate, cudaStream_t st);
 
 // tracing (trace.cu)
 int fides_trace_begin(const char *name, cudaStream_t st);

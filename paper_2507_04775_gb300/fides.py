@@ -34,7 +34,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_server_add_rotation_key", "fides_server_submit", "fides_server_poll", "fides_server_release",
            "fides_server_cancel", "fides_server_pause", "fides_server_inject", "fides_server_stats_read",
            "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
-           "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult"]
+           "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
+           "fides_linear_transform_work_words"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -155,6 +156,11 @@ def lib():
         L.fides_ptmult.argtypes = [_vp, ctp, _vp, ctypes.c_double, ctp, _vp]
         L.fides_scalar_add.argtypes = [_vp, ctp, _u64p, ctp, _vp]
         L.fides_scalar_mult.argtypes = [_vp, ctp, _u64p, ctypes.c_double, ctp, _vp]
+        L.fides_linear_transform_work_words.argtypes = [_vp, _i, _i, ctypes.POINTER(_i), _i,
+                                                        ctypes.POINTER(ctypes.c_size_t)]
+        L.fides_linear_transform.argtypes = [_vp, ctp, _i, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.c_double,
+                                             _i, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp), _vp,
+                                             ctypes.c_size_t, ctp, _vp]
         _lib = L
     return _lib
 
@@ -345,6 +351,28 @@ class Context:
         keys = (_vp * n)(*[_ptr(k, self.key_words(), "rk").value for k in rks])
         cts = (fides_ct * n)(*[self._ct(o, n_limbs, 0.0, "out") for o in outs])
         _check(lib().fides_rotate_hoisted(self._h, ctypes.byref(ca), n, st, keys, cts, _stream(stream)))
+
+    def linear_transform(self, a, n_limbs: int, diag_idx, pts, n1: int, keys: dict, out, scale: float = 1.0,
+                         pt_scale: float = 1.0, work=None, stream=None) -> float:
+        """BSGS diagonal-method transform (fides_linear_transform); pts[k] is
+        the device plaintext of diagonal diag_idx[k], pre-rotated; keys maps
+        step counts to device rotation keys."""
+        n = len(diag_idx)
+        di = (_i * n)(*diag_idx)
+        words = ctypes.c_size_t(0)
+        _check(lib().fides_linear_transform_work_words(self._h, n_limbs, n, di, n1, ctypes.byref(words)))
+        if work is None:
+            import torch
+            work = torch.empty(max(1, words.value), dtype=torch.int64, device="cuda")
+        pp = (_vp * n)(*[_ptr(p, n_limbs * self.N, "pt").value for p in pts])
+        ks = list(keys)
+        kst = (ctypes.c_int64 * max(1, len(ks)))(*ks)
+        kp = (_vp * max(1, len(ks)))(*[_ptr(keys[k], self.key_words(), "key").value for k in ks])
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_linear_transform(self._h, ctypes.byref(ca), n, di, pp, pt_scale, n1, len(ks), kst, kp,
+                                            _ptr(work, words.value, "work"), work.numel(), ctypes.byref(co),
+                                            _stream(stream)))
+        return co.scale
 
     def _ct2(self, fn, a, b, n_limbs, out, scale, stream):
         ca, cb = self._ct(a, n_limbs, scale, "a"), self._ct(b, n_limbs, scale, "b")

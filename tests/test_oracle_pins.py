@@ -533,3 +533,38 @@ def test_hoisted_rotation_at_ragged_levels(mid):
         outs = mid.rotate_hoisted(ct, steps, [cl.rotation_key(k) for k in steps])
         for k, o in zip(steps, outs):
             assert _rel_err(cl.decrypt(o, D), np.roll(z, -k)) < 2.0 ** -20, (nl, k)
+
+
+# ------------------------------------------------------- BSGS linear transform
+def _lt_keys(cl, diag_idx, n1):
+    steps = {i % n1 for i in diag_idx if i % n1} | {n1 * (i // n1) for i in diag_idx if i // n1}
+    return {k: cl.rotation_key(k) for k in sorted(steps)}
+
+
+def test_linear_transform_decrypts_to_matrix_product(small, small_client):
+    """y = M z for a matrix given by 8 of its 2048 diagonals, against numpy."""
+    cl, D = small_client, 2.0 ** 40
+    n = small.N // 2
+    st = si.Stream(81)
+    idx = [0, 1, 3, 8, 9, 21, 100, n - 1]
+    diags = {i: st.complex_slots(n) for i in idx}
+    z = cl.random_slots()
+    ct = cl.encrypt(z, small.nq, D)
+    ref = sum(diags[i] * np.roll(z, -i) for i in idx)
+    outs = []
+    for n1 in (8, 1, 4096):
+        di, pts = cl.encode_diagonals(diags, n1, small.nq, D)
+        out = small.linear_transform(ct, di, pts, n1, _lt_keys(cl, idx, n1))
+        got = cl.decrypt(out, D * D)
+        assert _rel_err(got, ref) < 2.0 ** -20, n1
+        outs.append(got)
+    assert _rel_err(outs[0], outs[1]) < 2.0 ** -20
+
+
+def test_linear_transform_needs_its_keys(small, small_client):
+    cl = small_client
+    ct = cl.encrypt(cl.random_slots(), small.nq, 2.0 ** 40)
+    diags = {0: np.ones(small.N // 2), 9: np.ones(small.N // 2)}
+    di, pts = cl.encode_diagonals(diags, 8, small.nq, 2.0 ** 40)
+    with pytest.raises(KeyError):
+        small.linear_transform(ct, di, pts, 8, {1: cl.rotation_key(1)})     # giant step 8 missing
