@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default NTT tile widths")
     ap.add_argument("--batch-ops", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server workload")
+    ap.add_argument("--no-ops", action="store_true", help="skip hoisted rotations, linear transform, element-wise")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -353,6 +354,11 @@ def run_fides(args, world, rank, local):
     if not args.no_serving and not args.small:
         serving = run_serving(args, ctx, dA, dK, P, scale)
 
+    # ---------------- hoisted rotations, linear transform, element-wise ----------------
+    ops_extra = None
+    if not args.no_ops and not args.small:
+        ops_extra = run_ops(args, ctx, dA, dB, dK, P, scale)
+
     # ---------------- end to end through host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -375,6 +381,7 @@ def run_fides(args, world, rank, local):
         "e2e": e2e,
         "batched": batched,
         "serving": serving,
+        "ops": ops_extra,
         "autotune": {"ran": not args.no_autotune, "seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
     }
     if mismatch:
@@ -601,6 +608,88 @@ def run_serving(args, ctx, dA, dK, P, scale):
             "latency": "submit to completion observed by the dispatcher (host CLOCK_MONOTONIC)"}
 
 
+def run_ops(args, ctx, dA, dB, dK, P, scale):
+    """The operations beyond the key-switching step, at 30 limbs: 8 hoisted
+    rotations against 8 single rotations, a 32-diagonal baby-step giant-step
+    linear transform (n1 = 8), and the element-wise kernels against the HBM
+    peak (their roofline: bytes read + written per launch)."""
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+    N, nl = ctx.N, P.nq
+    a, b = dA[0], dB[0]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    steps = [1, 2, 3, 4, 5, 6, 7, 8]
+    keys = [dK[1 + i % (len(dK) - 1)] for i in range(len(steps))]
+    outs = [torch.empty(2 * nl * N, dtype=torch.int64, device="cuda") for _ in steps]
+    t_h = timed(lambda: ctx.rotate_hoisted(a, nl, steps, keys, outs, scale), 10)
+    t_p = timed(lambda: [ctx.rotate(a, nl, k, key, o, scale) for k, key, o in zip(steps, keys, outs)], 10)
+    res["hoisted_rotations"] = {"rotations": len(steps), "limbs": nl, "hoisted_ms": round(t_h, 3),
+                                "single_ms": round(t_p, 3), "speedup": round(t_p / t_h, 3)}
+    # linear transform: 32 diagonals {0..7} x giant steps {0, 8, 16, 24} -> 7 baby + 3 giant rotations
+    idx = list(range(32))
+    n1 = 8
+    st = si.Stream(si.workload_seed(1), 20)
+    pts = [fides.to_device(si.uniform_poly(st, ctx.q, N)) for _ in idx]
+    lt_keys = {k: dK[1 + (k % (len(dK) - 1))] for k in sorted({i % n1 for i in idx if i % n1} |
+                                                                {n1 * (i // n1) for i in idx if i // n1})}
+    out = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    words = (7 + 2) * 2 * nl * N
+    work = torch.empty(words, dtype=torch.int64, device="cuda")
+    t_lt = timed(lambda: ctx.linear_transform(a, nl, idx, pts, n1, lt_keys, out, scale, 1.0, work=work), 5)
+    res["linear_transform"] = {"diagonals": len(idx), "n1": n1, "limbs": nl, "ms": round(t_lt, 3),
+                               "rotations": "7 hoisted baby steps + 3 giant steps"}
+    # element-wise kernels: bytes read + written per launch over the measured HBM peak
+    hbm_peak = peaks()[0]
+    limb = 8 * N
+    pt = pts[0]
+    o = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
+    ew = {}
+    k3 = [3 % q for q in ctx.q[:nl]]
+    flush = torch.empty(256 << 20, dtype=torch.int8, device="cuda")     # larger than L2
+    for name, fn, nbytes in (
+            ("hadd", lambda: ctx.hadd(a, b, nl, o, scale), 6 * nl * limb),
+            ("ptmult", lambda: ctx.ptmult(a, pt, nl, o, scale), 5 * nl * limb),
+            ("scalar_mult", lambda: ctx.scalar_mult(a, k3, nl, o, scale), 4 * nl * limb),
+            ("ptmac_8", lambda: ctx.linear_transform(a, nl, list(range(8)), pts[:8], 8, lt_keys, out, scale, 1.0,
+                                                     work=work), None)):
+        fn()
+        torch.cuda.synchronize()
+        fides.trace_reset()
+        fides.trace_enable(True)
+        for _ in range(20):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        fides.trace_enable(False)
+        tr = fides.trace_read()
+        kname = "k_ptmac" if name.startswith("ptmac") else "k_elem"
+        n_l, ms = tr[kname]
+        t = ms / n_l
+        if nbytes is None:     # 8 baby-step ciphertexts and 8 plaintexts read, one ciphertext written
+            nbytes = (8 * 2 * nl + 8 * nl + 2 * nl) * limb
+        gbs = nbytes / (t / 1e3) / 1e9
+        ew[name] = {"us": round(t * 1e3, 2), "GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 3)}
+    del flush
+    res["elementwise"] = ew
+    res["elementwise_note"] = ("device time of the kernel (CUDA events around each launch), L2 flushed before each "
+                               "launch; 30-limb operands; bytes = operands read + result written once")
+    return res
+
+
 def load_traffic(kernel, bytes_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources; else None."""
@@ -610,19 +699,26 @@ def load_traffic(kernel, bytes_per_launch):
     except (OSError, ValueError):
         return None
     ent = t.get(kernel)
-    if not ent or ent.get("sources_sha") != sources_sha():
+    if not ent or ent.get("sources_sha") != sources_sha(kernel):
         return None
     # the capture ran a smaller case: scale by the units one bench launch processes
     return int(ent["dram_bytes_per_unit"] * bytes_per_launch / ent["algorithmic_bytes_per_unit"])
 
 
-def sources_sha() -> str:
+KERNEL_SOURCES = {"k_ntt": ["ntt.cuh", "ntt.cu", "fides_internal.cuh"],
+                  "k_bconv": ["kernels.cuh", "fides_internal.cuh"],
+                  "k_inner": ["kernels.cuh", "fides_internal.cuh"]}
+
+
+def sources_sha(kernel: str = "k_ntt") -> str:
+    """Hash of the sources a kernel is compiled from (a DRAM-traffic figure
+    measured on other sources is stale)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2507_04775_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    files = next((v for k, v in KERNEL_SOURCES.items() if kernel.startswith(k)), None)
+    for f in sorted(files or [f for f in os.listdir(d) if f.endswith((".cu", ".cuh"))]):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
