@@ -242,6 +242,24 @@ int fides_linear_transform(fides_ctx *ctx, const fides_ct *a, int n_diag, const 
                            size_t work_words, fides_ct *out, void *stream);
 
 /*
+ * ModRaise (bootstrapping, Sec. III-F7): a ciphertext at one limb (modulo
+ * q_0) is lifted to out->n_limbs limbs: each coefficient's centred
+ * representative in (-q_0/2, q_0/2] is reduced modulo q_0 .. q_{n-1} (INTT of
+ * limb 0, centred lift, NTT per limb).  The result decrypts to m + q_0 I for
+ * a small integer polynomial I.  a->n_limbs must be 1; out may not alias a;
+ * out->scale = a->scale.
+ */
+int fides_modraise(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
+
+/*
+ * Multiplication of every slot by i (sign = +1: the monomial X^(N/2)) or by
+ * -i (sign = -1: X^(3N/2)), exactly, without a level: in evaluation form the
+ * monomial X^(N/2) is i_q (-1)^brv(j) at point j, i_q = psi^(N/2) mod q.
+ * out may alias a; out->scale = a->scale.
+ */
+int fides_mul_i(fides_ctx *ctx, const fides_ct *a, int sign, fides_ct *out, void *stream);
+
+/*
  * Element-wise operations (Table I) on ciphertexts in evaluation form; out
  * may alias a (and b).  out->n_limbs must equal a->n_limbs.
  *   fides_hadd / fides_hsub : out = a +/- b (b at a's level); out->scale = a->scale

@@ -88,6 +88,8 @@ def lib():
         L.or_linear_transform.restype = ctypes.c_int
         L.or_linear_transform.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int, _intp, _u64p,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _u64p, _u64p]
+        L.or_modraise.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
+        L.or_mul_monomial.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_uint64, _u64p]
         for name in ("or_hadd", "or_hsub", "or_ptadd", "or_ptmult", "or_scalar_add", "or_scalar_mult"):
             getattr(L, name).argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _u64p]
         L.or_from_signed.argtypes = [ctypes.c_void_p, _i64p, _intp, ctypes.c_int, _u64p]
@@ -267,6 +269,15 @@ class Context:
         if rc != 0:
             raise KeyError("a rotation key of the transform is missing")
         return out
+
+    def modraise(self, a, nl: int) -> np.ndarray:
+        """[2][1][N] modulo q_0 -> [2][nl][N], centred lift."""
+        a = _u64(a); out = np.empty((2, nl, self.N), dtype=np.uint64)
+        lib().or_modraise(self._h, _p(a), nl, _p(out)); return out
+
+    def mul_monomial(self, a, k: int) -> np.ndarray:
+        a = _u64(a); nl = a.shape[1]; out = np.empty_like(a)
+        lib().or_mul_monomial(self._h, _p(a), nl, k, _p(out)); return out
 
     def hsquare(self, a, rlk) -> np.ndarray:
         return self.hmult(a, a, rlk)

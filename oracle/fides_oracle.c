@@ -612,6 +612,59 @@ void or_rotate_hoisted(const or_ctx *c, const u64 *a, int nl, int n_rot, const i
     free(ext); free(rext); free(acc); free(r0);
 }
 
+/*
+ * ModRaise (bootstrapping, Sec. III-F7): a is a ciphertext [2][1][N] modulo
+ * q_0; out [2][nl][N] holds, for every coefficient, its centred
+ * representative in (-q_0/2, q_0/2] reduced modulo q_0 .. q_{nl-1}
+ * (coefficient form after INTT, evaluation form again after NTT).
+ */
+void or_from_signed(const or_ctx *c, const i64 *v, const int *pidx, int n, u64 *out);
+
+void or_modraise(const or_ctx *c, const u64 *a, int nl, u64 *out)
+{
+    u64 N = c->N, q0 = c->primes[0];
+    u64 *coef = (u64 *)malloc(sizeof(u64) * N);
+    i64 *v = (i64 *)malloc(sizeof(i64) * N);
+    int *pidx = (int *)malloc(sizeof(int) * nl);
+    for (int i = 0; i < nl; i++) pidx[i] = i;
+    for (int t = 0; t < 2; t++) {
+        memcpy(coef, a + (u64)t * N, sizeof(u64) * N);
+        or_intt(c, 0, coef);
+        for (u64 n = 0; n < N; n++) v[n] = coef[n] > q0 / 2 ? (i64)coef[n] - (i64)q0 : (i64)coef[n];
+        u64 *o = out + (u64)t * nl * N;
+        or_from_signed(c, v, pidx, nl, o);
+        or_ntt_limbs(c, o, pidx, nl);
+    }
+    free(coef); free(v); free(pidx);
+}
+
+/* Multiplication by the monomial X^k, 0 <= k < 2N, of both polynomials of a
+ * ciphertext [2][nl][N]: in coefficient form a_i X^i -> a_i X^(i+k), negated
+ * once for every wrap past X^N (X^N = -1). */
+void or_mul_monomial(const or_ctx *c, const u64 *a, int nl, u64 k, u64 *out)
+{
+    u64 N = c->N;
+    int *pidx = (int *)malloc(sizeof(int) * nl);
+    for (int i = 0; i < nl; i++) pidx[i] = i;
+    u64 *x = (u64 *)malloc(sizeof(u64) * nl * N);
+    for (int t = 0; t < 2; t++) {
+        memcpy(x, a + (u64)t * nl * N, sizeof(u64) * nl * N);
+        or_intt_limbs(c, x, pidx, nl);
+        u64 *o = out + (u64)t * nl * N;
+        for (int z = 0; z < nl; z++) {
+            u64 q = c->primes[z];
+            for (u64 i = 0; i < N; i++) {
+                u64 e = i + k, val = x[(u64)z * N + i];
+                int neg = 0;
+                while (e >= N) { e -= N; neg ^= 1; }
+                o[(u64)z * N + e] = neg ? neg_mod(val, q) : val;
+            }
+        }
+        or_ntt_limbs(c, o, pidx, nl);
+    }
+    free(x); free(pidx);
+}
+
 /* ------------------------------------------------------------------------
  * Element-wise operations of Table I on ciphertexts [2][nl][N] in evaluation
  * form, where a product of polynomials is the slot-wise product of their

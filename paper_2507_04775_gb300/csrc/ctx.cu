@@ -161,6 +161,7 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_rs_qlinv);
     cudaFree(c->d_mu_nscale);
     cudaFree(c->d_md_nscale);
+    cudaFree(c->d_raise);
     cudaFree(c->scratch);
     free(c);
 }
@@ -305,6 +306,13 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     for (int l = 1; l < L; ++l)
         for (int i = 0; i < l; ++i) rs[(size_t)l * L + i] = pair_of(hinv(primes[l] % primes[i], primes[i]), primes[i]);
 
+    // ModRaise: q_0 mod q_i (the centred lift subtracts q_0 from the upper half)
+    std::vector<TwPair> raise((size_t)L);
+    for (int i = 0; i < L; ++i) raise[i] = pair_of(primes[0] % primes[i], primes[i]);
+    // multiplication by X^(N/2): i_q = psi^(N/2) mod q_i (a square root of -1)
+    std::vector<TwPair> iroot((size_t)L);
+    for (int i = 0; i < L; ++i) iroot[i] = pair_of(hpow(c->psi[i], (u64)N / 2, primes[i]), primes[i]);
+
     // combined N^-1 * qhat^-1 constants of the inverse NTTs feeding a conversion
     std::vector<TwPair> mu_ns((size_t)L * (L + 1) / 2), md_ns((size_t)np);
     for (int nl = 1; nl <= L; ++nl) {
@@ -333,6 +341,8 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     if (!rc) rc = upload(&c->d_rs_qlinv, rs, "rescale tables");
     if (!rc) rc = upload(&c->d_mu_nscale, mu_ns, "modup tables");
     if (!rc) rc = upload(&c->d_md_nscale, md_ns, "moddown tables");
+    if (!rc) rc = upload(&c->d_raise, raise, "modraise tables");
+    for (int i = 0; i < L; ++i) c->iroot[i] = iroot[i];
     if (!rc) {
         c->scratch_words = scratch_words_for(L, K, dnum, alpha, N);
         rc = fides_check_cuda(cudaMalloc((void **)&c->scratch, c->scratch_words * sizeof(u64)), "scratch pool");

@@ -14,14 +14,16 @@
 
 namespace {
 
-enum ElemOp { E_HADD, E_HSUB, E_PTADD, E_PTMULT, E_SCALAR_ADD, E_SCALAR_MULT };
+enum ElemOp { E_HADD, E_HSUB, E_PTADD, E_PTMULT, E_SCALAR_ADD, E_SCALAR_MULT, E_MULI };
 
 struct ElemArgs {
     const u64 *a;     // [2][nl][N]
     const u64 *b;     // HADD / HSUB: [2][nl][N]; PTADD / PTMULT: [nl][N]
     u64 *out;         // [2][nl][N] (may alias a or b: each word is read and written by one thread)
     int nl, logN;
-    TwPair k[FIDES_MAX_PRIMES];   // scalar ops: residue of the constant per limb, with its Shoup companion
+    int neg;                      // E_MULI: 0 multiplies by X^(N/2) (slots by i), 1 by X^(3N/2) (slots by -i)
+    TwPair k[FIDES_MAX_PRIMES];   // scalar ops: residue of the constant per limb, with its Shoup companion;
+                                  // E_MULI: i_q = psi^(N/2) mod q_i
 };
 
 template <int OP>
@@ -33,7 +35,7 @@ __device__ __forceinline__ u64 elem(u64 x, u64 y, int poly, const TwPair &k, con
     case E_PTADD: return poly == 0 ? csub(x + y, p.q) : x;
     case E_PTMULT: return mul_mod(x, y, p);
     case E_SCALAR_ADD: return poly == 0 ? csub(x + k.w, p.q) : x;
-    default: return csub(mul_shoup(x, k, p.q), p.q);
+    default: return csub(mul_shoup(x, k, p.q), p.q);   // E_SCALAR_MULT, E_MULI
     }
 }
 
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(256) k_elem(ElemArgs A, const PrimeInfo *__res
         const size_t wi = w - (poly ? S : 0);
         const int z = (int)(wi >> A.logN);
         const PrimeInfo p = P[z];
-        const TwPair k = (OP == E_SCALAR_ADD || OP == E_SCALAR_MULT) ? A.k[z] : TwPair{0, 0};
+        const TwPair k = (OP == E_SCALAR_ADD || OP == E_SCALAR_MULT || OP == E_MULI) ? A.k[z] : TwPair{0, 0};
         u64 x0, x1, y0 = 0, y1 = 0;
         if (VEC) {
             const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.a + w);
@@ -73,7 +75,15 @@ __global__ void __launch_bounds__(256) k_elem(ElemArgs A, const PrimeInfo *__res
                 y1 = A.b[b_index<OP>(w, wi) + 1];
             }
         }
-        const u64 r0 = elem<OP>(x0, y0, poly, k, p), r1 = elem<OP>(x1, y1, poly, k, p);
+        u64 r0 = elem<OP>(x0, y0, poly, k, p), r1 = elem<OP>(x1, y1, poly, k, p);
+        if (OP == E_MULI) {
+            // X^(N/2) at the point psi^(2 brv(j) + 1) is i_q^(2 brv(j) + 1) = i_q (-1)^brv(j), and brv(j)
+            // is odd exactly in the upper half of the limb
+            if ((int)((wi >> (A.logN - 1)) & 1) != A.neg) {
+                r0 = r0 ? p.q - r0 : 0;
+                r1 = r1 ? p.q - r1 : 0;
+            }
+        }
         if (VEC) {
             *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
         } else {
@@ -96,7 +106,7 @@ int launch_elem(const fides_ctx *c, const ElemArgs &A, cudaStream_t st)
 }
 
 int run_elem(fides_ctx *c, int op, const fides_ct *a, const uint64_t *b, const uint64_t *k, fides_ct *out,
-             double out_scale, void *stream, const char *fn)
+             double out_scale, void *stream, const char *fn, int neg = 0)
 {
     if (!c || !a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
     const int nl = a->n_limbs;
@@ -117,6 +127,9 @@ int run_elem(fides_ctx *c, int op, const fides_ct *a, const uint64_t *b, const u
             A.k[i].w = k[i];
             A.k[i].wp = (u64)(((unsigned __int128)k[i] << 64) / q);
         }
+    } else if (op == E_MULI) {
+        for (int i = 0; i < nl; ++i) A.k[i] = c->iroot[i];
+        A.neg = neg;
     } else if (!b) {
         return fides_set_error(FIDES_ERR_ARG, "%s: second operand is NULL", fn);
     }
@@ -129,6 +142,7 @@ int run_elem(fides_ctx *c, int op, const fides_ct *a, const uint64_t *b, const u
     case E_PTADD: rc = launch_elem<E_PTADD>(c, A, st); break;
     case E_PTMULT: rc = launch_elem<E_PTMULT>(c, A, st); break;
     case E_SCALAR_ADD: rc = launch_elem<E_SCALAR_ADD>(c, A, st); break;
+    case E_MULI: rc = launch_elem<E_MULI>(c, A, st); break;
     default: rc = launch_elem<E_SCALAR_MULT>(c, A, st); break;
     }
     if (!rc) out->scale = out_scale;
@@ -176,6 +190,12 @@ extern "C" int fides_scalar_mult(fides_ctx *c, const fides_ct *a, const uint64_t
                                  void *stream)
 {
     return run_elem(c, E_SCALAR_MULT, a, nullptr, k, out, a ? a->scale * k_scale : 0.0, stream, "op_scalar_mult");
+}
+
+extern "C" int fides_mul_i(fides_ctx *c, const fides_ct *a, int sign, fides_ct *out, void *stream)
+{
+    if (sign != 1 && sign != -1) return fides_set_error(FIDES_ERR_ARG, "fides_mul_i: sign must be +1 or -1");
+    return run_elem(c, E_MULI, a, nullptr, nullptr, out, a ? a->scale : 0.0, stream, "op_mul_i", sign < 0 ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,6 +125,10 @@ struct fides_ctx {
     TwPair *d_mu_nscale;
     TwPair *d_md_nscale;
 
+    // ModRaise: [L] q_0 mod q_i; host copy of i_q = psi_i^(N/2) mod q_i (X^(N/2) in evaluation form)
+    TwPair *d_raise;
+    TwPair iroot[FIDES_MAX_PRIMES];
+
     // Scratch pool for one operation at the top level.
     u64 *scratch;
     size_t scratch_words;

@@ -299,3 +299,30 @@ extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, voi
     if (!rc) out->scale = a->scale / (double)c->primes[nl - 1];
     return rc;
 }
+
+extern "C" int fides_modraise(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
+{
+    const char *fn = "fides_modraise";
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    if (a->n_limbs != 1) return fides_set_error(FIDES_ERR_ARG, "%s: input must have one limb", fn);
+    const int nl = out->n_limbs;
+    if (int rc = check_level(c, nl, fn)) return rc;
+    if (out->data == a->data) return fides_set_error(FIDES_ERR_ARG, "%s: out may not alias a", fn);
+    const size_t N = c->N;
+    cudaStream_t st = as_stream(stream);
+    OpTrace op("op_modraise", st);
+    Scratch s = carve(c);
+    std::vector<Seg> v;
+    for (int t = 0; t < 2; ++t) v.push_back(seg_of(a->data + (size_t)t * N, s.last + (size_t)t * N, 1, 0));
+    if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
+    v.clear();
+    for (int t = 0; t < 2; ++t) {
+        Seg g = seg_of(s.last + (size_t)t * N, out->data + (size_t)t * nl * N, nl, 0, nullptr, nullptr, 0, 0, c->d_raise);
+        g.g = c->primes[0];
+        v.push_back(g);
+    }
+    int rc = ntt_forward(c, inline_set(v), ProRaise{}, EpiCanon{}, st);
+    if (!rc) out->scale = a->scale;
+    return rc;
+}

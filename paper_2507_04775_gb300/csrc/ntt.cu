@@ -110,6 +110,10 @@ int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 {
     return forward(c, s, ProSrc{}, EpiSubMulRot{c->logN}, st);
 }
+int ntt_fwd_raise(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
+{
+    return forward(c, s, ProRaise{}, EpiCanon{}, st);
+}
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 {
     return inverse(c, s, ProPrep{c->logN}, EpiCanon{}, st);

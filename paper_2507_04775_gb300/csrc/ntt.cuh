@@ -82,6 +82,19 @@ struct ProSwitchMod {
     }
 };
 
+// ModRaise (bootstrapping, Sec. III-F7): src is a coefficient of the limb
+// modulo q_0 (canonical); its centred representative in (-q_0/2, q_0/2] is
+// reduced modulo this limb's prime.  g holds q_0, cst[prime].w = q_0 mod q.
+struct ProRaise {
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
+    {
+        const u64 v = J.src[j];
+        const u64 r = reduce64_lazy(v, p);                                  // [0, 2q)
+        if (v > (J.g >> 1)) return csub(r + p.q - J.cst[J.prime].w, p.q2);  // v - q_0 mod q, in [0, 2q)
+        return r;
+    }
+};
+
 // Inverse-NTT prologue with a run-time variant (the segment's mode), which
 // fuses the element-wise step that produces a key-switch input:
 //   0: the input limb as is;
@@ -351,6 +364,7 @@ int ntt_fwd_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);     
 int ntt_fwd_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);          // ProSrc, EpiSubMul
 int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);   // ProSwitchMod, EpiSubMul
 int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &set, cudaStream_t st);      // ProSrc, EpiSubMulRot
+int ntt_fwd_raise(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProRaise, EpiCanon
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep, EpiCanon
 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
@@ -368,6 +382,10 @@ inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSwitchMod, EpiSu
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiSubMulRot, cudaStream_t st)
 {
     return ntt_fwd_submul_rot(c, s, st);
+}
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProRaise, EpiCanon, cudaStream_t st)
+{
+    return ntt_fwd_raise(c, s, st);
 }
 inline int ntt_inverse(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {

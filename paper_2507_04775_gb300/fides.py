@@ -35,7 +35,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_server_cancel", "fides_server_pause", "fides_server_inject", "fides_server_stats_read",
            "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
-           "fides_linear_transform_work_words"]
+           "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -161,6 +161,8 @@ def lib():
         L.fides_linear_transform.argtypes = [_vp, ctp, _i, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.c_double,
                                              _i, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp), _vp,
                                              ctypes.c_size_t, ctp, _vp]
+        L.fides_modraise.argtypes = [_vp, ctp, ctp, _vp]
+        L.fides_mul_i.argtypes = [_vp, ctp, _i, ctp, _vp]
         _lib = L
     return _lib
 
@@ -372,6 +374,18 @@ class Context:
         _check(lib().fides_linear_transform(self._h, ctypes.byref(ca), n, di, pp, pt_scale, n1, len(ks), kst, kp,
                                             _ptr(work, words.value, "work"), work.numel(), ctypes.byref(co),
                                             _stream(stream)))
+        return co.scale
+
+    def modraise(self, a, out, n_limbs: int, scale: float = 1.0, stream=None) -> float:
+        """ModRaise of a one-limb ciphertext to n_limbs limbs."""
+        ca, co = self._ct(a, 1, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_modraise(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def mul_i(self, a, n_limbs: int, out, sign: int = 1, scale: float = 1.0, stream=None) -> float:
+        """Slots times i (sign=+1) or -i (sign=-1), exactly."""
+        ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
+        _check(lib().fides_mul_i(self._h, ctypes.byref(ca), sign, ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def _ct2(self, fn, a, b, n_limbs, out, scale, stream):

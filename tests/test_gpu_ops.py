@@ -146,3 +146,24 @@ def test_hoisted_rotations_match_oracle(pairs, P, nl, steps):
         assert np.array_equal(to_host(outs[i]).reshape(a.shape), ref[i]), steps[i]
     with pytest.raises(FidesError):
         g.rotate_hoisted(da, nl, [], [], [])
+
+
+@pytest.mark.parametrize("P,nl", [(si.SMALL, 3), (si.MID, 12), (si.MID, 4), (si.FULL, 30), (si.FULL, 13)],
+                         ids=["logN12-L3", "logN12-L12", "logN12-L4", "logN16-L30", "logN16-L13"])
+def test_modraise_and_mul_i_match_oracle(pairs, P, nl):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o = pairs(P)
+    st = si.Stream(804, nl)
+    a1 = np.stack([si.uniform_poly(st, o.q[:1], o.N) for _ in range(2)])
+    raised = torch.empty(2 * nl * o.N, dtype=torch.int64, device="cuda")
+    g.modraise(to_device(a1), raised, nl)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(raised).reshape(2, nl, o.N), o.modraise(a1, nl))
+    a = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+    da = to_device(a)
+    for sign, k in ((1, o.N // 2), (-1, 3 * o.N // 2)):
+        out = torch.empty_like(da)
+        g.mul_i(da, nl, out, sign=sign)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(out).reshape(a.shape), o.mul_monomial(a, k)), sign

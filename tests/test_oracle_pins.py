@@ -568,3 +568,51 @@ def test_linear_transform_needs_its_keys(small, small_client):
     di, pts = cl.encode_diagonals(diags, 8, small.nq, 2.0 ** 40)
     with pytest.raises(KeyError):
         small.linear_transform(ct, di, pts, 8, {1: cl.rotation_key(1)})     # giant step 8 missing
+
+
+# ----------------------------------------------------------- bootstrapping steps
+def test_modraise_is_the_centred_lift(mid):
+    """Each coefficient of the raised ciphertext is the centred representative
+    of the one-limb coefficient (big-integer CRT over the raised limbs)."""
+    c = mid
+    st = si.Stream(91)
+    a = np.stack([si.uniform_poly(st, c.q[:1], c.N) for _ in range(2)])
+    nl = 9
+    r = c.modraise(a, nl)
+    idx = list(range(nl))
+    Q = 1
+    for q in c.q[:nl]:
+        Q *= q
+    q0 = c.q[0]
+    for t in range(2):
+        src = c.intt(a[t][0], 0)
+        got = oracle.centered(oracle.crt(c.intt_limbs(r[t], idx), c.q[:nl]), Q)
+        want = [int(v) - q0 if int(v) > q0 // 2 else int(v) for v in src]
+        assert got == want
+
+
+def test_modraise_decrypts_to_m_plus_q0_I(small, small_client):
+    cl = small_client
+    z = cl.random_slots()
+    ct = cl.encrypt(z, 1, 2.0 ** 30)
+    raised = small.modraise(ct, small.nq)
+    d1 = cl.decrypt_coeffs(ct)
+    dr = cl.decrypt_coeffs(raised)
+    q0 = small.q[0]
+    I = [(x - y) // q0 for x, y in zip(dr, d1)]
+    assert all((x - y) % q0 == 0 for x, y in zip(dr, d1))
+    s1 = int(np.sum(np.abs(cl.s_coeff)))
+    assert max(abs(v) for v in I) <= s1 + 1 and any(I)
+
+
+def test_monomial_multiplication_rotates_the_phase(small, small_client):
+    cl, D = small_client, 2.0 ** 40
+    z = cl.random_slots()
+    ct = cl.encrypt(z, small.nq, D)
+    N = small.N
+    assert _rel_err(cl.decrypt(small.mul_monomial(ct, N // 2), D), 1j * z) < 2.0 ** -20
+    assert _rel_err(cl.decrypt(small.mul_monomial(ct, 3 * N // 2), D), -1j * z) < 2.0 ** -20
+    # X^(N/2) twice is X^N = -1, exactly
+    twice = small.mul_monomial(small.mul_monomial(ct, N // 2), N // 2)
+    neg = np.stack([np.stack([(q - x) % q for x, q in zip(ct[t], small.q)]) for t in range(2)]).astype(np.uint64)
+    assert np.array_equal(twice, neg)
