@@ -616,3 +616,85 @@ def test_monomial_multiplication_rotates_the_phase(small, small_client):
     twice = small.mul_monomial(small.mul_monomial(ct, N // 2), N // 2)
     neg = np.stack([np.stack([(q - x) % q for x, q in zip(ct[t], small.q)]) for t in range(2)]).astype(np.uint64)
     assert np.array_equal(twice, neg)
+
+
+# ------------------------------------------------------------- bootstrapping
+def _dense(M, n):
+    A = np.zeros((n, n), dtype=complex)
+    r = np.arange(n)
+    for d, v in M.items():
+        A[r, (r + d) % n] += v
+    return A
+
+
+@pytest.mark.parametrize("n,budget", [(16, 3), (64, 3), (32, 2)])
+def test_slot_dft_factorisation(n, budget):
+    """The grouped butterfly stages times the bit reversal are the slot DFT
+    U[j][i] = zeta^(5^j i) (zeta = exp(i pi / 2n)), and the adjoint of the
+    diagonal form is the conjugate transpose."""
+    from oracle import bootstrap as bt
+    N = 2 * n
+    U = np.exp(1j * np.pi * np.outer([pow(5, j, 2 * N) for j in range(n)], np.arange(n)) / N)
+    bits = n.bit_length() - 1
+    P = np.zeros((n, n))
+    for i in range(n):
+        P[i, brv(i, bits)] = 1
+    F = np.eye(n, dtype=complex)
+    for G in bt.dft_groups(n, budget):
+        assert len(G) <= 2 ** (bits // budget + 2) - 1
+        F = _dense(G, n) @ F
+    assert np.max(np.abs(F @ P - U)) < 1e-12
+    G = bt.dft_groups(n, budget)[0]
+    assert np.max(np.abs(_dense(bt.diag_adjoint(G, n), n) - _dense(G, n).conj().T)) < 1e-14
+
+
+def test_coefficients_to_slots_identity():
+    """With real coefficients t, (1/n) U^H U t = t_lo + i t_hi (the reading
+    CoeffToSlot relies on)."""
+    n = 32
+    N = 2 * n
+    ex = np.array([pow(5, j, 2 * N) for j in range(n)])
+    Ufull = np.exp(1j * np.pi * np.outer(ex, np.arange(N)) / N)
+    t = np.random.default_rng(3).normal(size=N)
+    Ulo = Ufull[:, :n]
+    w = Ulo.conj().T @ (Ufull @ t) / n
+    assert np.max(np.abs(w - (t[:n] + 1j * t[n:]))) < 1e-12
+
+
+def test_chebyshev_interpolation_and_division():
+    from oracle import bootstrap as bt
+    f = lambda u: np.cos(2 * np.pi * (25 * u - 0.25) / 4)
+    c = bt.cheb_interp(f, 119)
+    u = np.linspace(-1, 1, 2001)
+    assert np.max(np.abs(np.polynomial.chebyshev.chebval(u, c) - f(u))) < 1e-12
+    qc, rc = bt.cheb_divide(c, 64)
+    T64 = np.cos(64 * np.arccos(u))
+    lhs = np.polynomial.chebyshev.chebval(u, qc) * T64 + np.polynomial.chebyshev.chebval(u, rc)
+    assert np.max(np.abs(lhs - np.polynomial.chebyshev.chebval(u, c))) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def boot12():
+    """logN=12 bootstrapping context: q_0 of 60 bits, 29 q_i of 54 bits, K=10 x 60 bits, dnum=3, h=192."""
+    from oracle import bootstrap as bt
+    q0 = oracle.find_primes(12, 60, 1)
+    q = q0 + oracle.find_primes(12, 54, 29, exclude=q0)
+    p = oracle.find_primes(12, 60, 10, exclude=q)
+    ctx = oracle.Context(12, q, p, 3)
+    cl = Client(ctx, seed=si.workload_seed(4), hamming=192)
+    prog = bt.plan(cl, q, 2.0 ** 50)
+    keys = (cl.relin_key(), cl.conjugation_key(), {s: cl.rotation_key(s) for s in prog.rot_steps})
+    return ctx, cl, prog, keys
+
+
+def test_bootstrap_refreshes_the_ciphertext(boot12):
+    """ModRaise -> CoeffToSlot -> EvalMod -> SlotToCoeff on a one-limb
+    ciphertext: the result has limbs again and decrypts to the message within
+    2^-12 (sparse ternary secret, h = 192)."""
+    from oracle import bootstrap as bt
+    ctx, cl, prog, (rlk, ck, rks) = boot12
+    z = cl.random_slots()
+    ct = cl.encrypt(z, 1, 2.0 ** 50)
+    out = bt.run(ctx, prog, ct, rlk, ck, rks)
+    assert out.shape[1] >= 12
+    assert _rel_err(cl.decrypt(out, prog.out_scale), z) < 2.0 ** -12
