@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--batch-ops", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server workload")
     ap.add_argument("--no-ops", action="store_true", help="skip hoisted rotations, linear transform, element-wise")
+    ap.add_argument("--no-bootstrap", action="store_true", help="skip the bootstrapping workload")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -359,6 +360,11 @@ def run_fides(args, world, rank, local):
     if not args.no_ops and not args.small:
         ops_extra = run_ops(args, ctx, dA, dB, dK, P, scale)
 
+    # ---------------- bootstrapping ----------------
+    boot = None
+    if not args.no_bootstrap and not args.small:
+        boot = run_bootstrap(args)
+
     # ---------------- end to end through host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -382,6 +388,7 @@ def run_fides(args, world, rank, local):
         "batched": batched,
         "serving": serving,
         "ops": ops_extra,
+        "bootstrap": boot,
         "autotune": {"ran": not args.no_autotune, "seconds": round(t_tune, 2), "ntt_tile_by_limbs": tiles},
     }
     if mismatch:
@@ -687,6 +694,69 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
     res["elementwise"] = ew
     res["elementwise_note"] = ("device time of the kernel (CUDA events around each launch), L2 flushed before each "
                                "launch; 30-limb operands; bytes = operands read + result written once")
+    return res
+
+
+def run_bootstrap(args):
+    """Bootstrapping at logN=16 (2^15 slots): q_0 of 60 bits and 29 q_i of 54
+    bits, K = 10 special 60-bit primes, dnum = 3; the library's planner builds
+    the program (CoeffToSlot / SlotToCoeff with level budget 3/3, EvalMod of
+    Chebyshev degree 119 plus 2 double-angle steps).  A batch of 8 one-limb
+    ciphertexts is bootstrapped one after another.  Keys and ciphertexts are
+    uniform residues of the right shapes (timing only; the decryption check is
+    in the GPU tests)."""
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+    from paper_2507_04775_gb300 import bootstrap as bt
+    logN = 16
+    q0 = fides.find_primes(logN, 60, 1)
+    q = q0 + fides.find_primes(logN, 54, 29, exclude=q0)
+    p = fides.find_primes(logN, 60, 10, exclude=q)
+    ctx = fides.Context(logN, q, p, 3)
+    if not args.no_autotune:
+        ctx.autotune(128)
+    N = ctx.N
+    t0 = time.perf_counter()
+    prog = bt.plan(N, q, 2.0 ** 50)
+    t_plan = time.perf_counter() - t0
+    st = si.Stream(si.workload_seed(4), 30)
+    key = fides.to_device(np.stack([np.stack([si.uniform_poly(st, q + p, N) for _ in range(2)]) for _ in range(3)]))
+    rks = {s: key.clone() for s in prog.rot_steps}
+    rlk, ck = key.clone(), key.clone()
+    t0 = time.perf_counter()
+    dp = bt.DeviceProgram(ctx, prog, rlk, ck, rks)
+    t_load = time.perf_counter() - t0
+    cts = [fides.to_device(np.stack([si.uniform_poly(st, q[:1], N) for _ in range(2)])) for _ in range(8)]
+    outs = [torch.empty(2 * dp.out_limbs * N, dtype=torch.int64, device="cuda") for _ in cts]
+    stream = torch.cuda.current_stream()
+    launches0 = fides.kernel_launches()
+    dp.run(cts[0], outs[0], 2.0 ** 50)
+    torch.cuda.synchronize()
+    per_boot_launches = fides.kernel_launches() - launches0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c, o in zip(cts, outs):
+        dp.run(c, o, 2.0 ** 50)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    counts = {}
+    for ins in prog.instr:
+        counts[ins[0]] = counts.get(ins[0], 0) + 1
+    names = {v: k for k, v in bt.OP.items()}
+    res = {"workload": "bootstrap logN=16, 2^15 slots, L=30 (1 x 60-bit + 29 x 54-bit), K=10, dnum=3, "
+                       "CtS/StC level budget 3/3, EvalMod Chebyshev degree 119 + 2 double angles, batch of 8",
+           "ms_per_ciphertext": round(ms / len(cts), 2), "ms_per_batch": round(ms, 2), "batch": len(cts),
+           "limbs_out": dp.out_limbs, "rotation_keys": len(prog.rot_steps),
+           "plaintexts": sum(len(t["coeffs"]) for t in prog.lts), "instructions": len(prog.instr),
+           "instruction_mix": {names[k]: v for k, v in sorted(counts.items())},
+           "kernels_per_bootstrap": int(per_boot_launches), "device_buffers": dp.buffers,
+           "work_gib": round(dp.work_words * 8 / 2 ** 30, 2), "plan_s": round(t_plan, 1), "load_s": round(t_load, 1)}
+    dp.close()
+    del rks, cts, outs, key
+    ctx.close()
+    torch.cuda.empty_cache()
     return res
 
 

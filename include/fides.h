@@ -448,6 +448,85 @@ int fides_server_stats_read(fides_server *srv, fides_server_stats *out);
 int64_t fides_now_ns(void);
 
 /*
+ * Homomorphic programs (bootstrapping, Sec. III-F7).  A program is a list of
+ * instructions over virtual ciphertext registers, each written once, with the
+ * tables they use: linear transforms (diagonal indices, device plaintexts in
+ * evaluation form pre-rotated for the baby-step giant-step split, n1,
+ * plaintext scale; see fides_linear_transform), scalar constants (host
+ * residues, one per q-limb; entries beyond an instruction's level unused) and
+ * keys.  Bootstrapping is the program ModRaise -> three linear transforms
+ * (CoeffToSlot) -> conjugation split -> EvalMod polynomial and double-angle
+ * steps -> three linear transforms (SlotToCoeff); its tables are the
+ * precomputation the paper takes from OpenFHE (Sec. III-B).
+ *
+ * Instructions (dst <- ...):
+ *   MODRAISE a to `arg` limbs (a has one limb)     LT #arg of a
+ *   RESCALE a                                      DROP a to its first `arg` limbs
+ *   HADD / HSUB / HMULT a, b (same level; HMULT relinearises with the relin key)
+ *   CONJ a (conjugation key)                       MULI a by i (arg = 1) or -i (arg = -1)
+ *   CMULT a by constant #arg (scale times const_scale[arg])
+ *   CADD constant #arg to a                        COPY a
+ * fides_program_create checks the program (operands defined before use,
+ * levels consistent, keys present; FIDES_ERR_ARG naming the instruction),
+ * copies every host table (device plaintexts and keys are referenced and must
+ * outlive the program) and maps the virtual registers onto as few
+ * ciphertext-sized buffers as their lifetimes allow.
+ * fides_program_info reports the device work buffer the program needs (words),
+ * the buffer count and the output's limb count.
+ * fides_program_run executes it on `stream` from `in` (in_limbs limbs) into
+ * `out` (the output register's limbs; out->scale = desc->out_scale); it uses
+ * the context's scratch like the single-operation entry points.
+ */
+#define FIDES_I_MODRAISE 1
+#define FIDES_I_LT 2
+#define FIDES_I_RESCALE 3
+#define FIDES_I_DROP 4
+#define FIDES_I_HADD 5
+#define FIDES_I_HSUB 6
+#define FIDES_I_HMULT 7
+#define FIDES_I_CONJ 8
+#define FIDES_I_MULI 9
+#define FIDES_I_CMULT 10
+#define FIDES_I_CADD 11
+#define FIDES_I_COPY 12
+
+typedef struct {
+    int op, dst, a, b, arg;
+} fides_instr;
+
+typedef struct {
+    int n_diag;
+    const int *diag_idx;
+    const uint64_t *const *dev_pts;
+    int n1;
+    double pt_scale;
+} fides_lt;
+
+typedef struct {
+    int n_instr;
+    const fides_instr *instr;
+    int n_regs, in_reg, out_reg, in_limbs;
+    double out_scale;
+    int n_lt;
+    const fides_lt *lt;
+    int n_const;
+    const uint64_t *const *consts;   /* host [n_const] arrays of L residues */
+    const double *const_scale;
+    const uint64_t *dev_relin_key, *dev_conj_key;
+    int n_rot_keys;
+    const int64_t *rot_steps;
+    const uint64_t *const *dev_rot_keys;
+} fides_program_desc;
+
+typedef struct fides_program fides_program;
+
+int fides_program_create(fides_ctx *ctx, const fides_program_desc *desc, fides_program **out);
+int fides_program_info(const fides_program *prog, size_t *work_words, int *buffers, int *out_limbs);
+int fides_program_run(fides_program *prog, const fides_ct *in, fides_ct *out, uint64_t *dev_work, size_t work_words,
+                      void *stream);
+void fides_program_destroy(fides_program *prog);
+
+/*
  * Rescale that allocates nothing.  The paper has no counterpart: this entry
  * point serves callers that cannot allocate device memory when they call it
  * (a host application that owns every device allocation and hands the library

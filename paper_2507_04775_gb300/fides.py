@@ -35,7 +35,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_server_cancel", "fides_server_pause", "fides_server_inject", "fides_server_stats_read",
            "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
-           "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i"]
+           "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
+           "fides_program_info", "fides_program_run", "fides_program_destroy"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -84,6 +85,26 @@ class fides_server_stats(ctypes.Structure):
         "submitted", "rejected", "cancelled", "completed", "failed", "timed_out", "groups", "grouped_ops",
         "max_group", "pending", "in_flight", "held", "arena_bytes", "arena_used", "arena_peak",
         "admission_stalls", "kernel_launches")] + [("device_ms", ctypes.c_double), ("max_lanes_busy", ctypes.c_int)]
+
+
+class fides_instr(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("dst", ctypes.c_int), ("a", ctypes.c_int), ("b", ctypes.c_int),
+                ("arg", ctypes.c_int)]
+
+
+class fides_lt(ctypes.Structure):
+    _fields_ = [("n_diag", ctypes.c_int), ("diag_idx", ctypes.POINTER(ctypes.c_int)),
+                ("dev_pts", ctypes.POINTER(ctypes.c_void_p)), ("n1", ctypes.c_int), ("pt_scale", ctypes.c_double)]
+
+
+class fides_program_desc(ctypes.Structure):
+    _fields_ = [("n_instr", ctypes.c_int), ("instr", ctypes.POINTER(fides_instr)), ("n_regs", ctypes.c_int),
+                ("in_reg", ctypes.c_int), ("out_reg", ctypes.c_int), ("in_limbs", ctypes.c_int),
+                ("out_scale", ctypes.c_double), ("n_lt", ctypes.c_int), ("lt", ctypes.POINTER(fides_lt)),
+                ("n_const", ctypes.c_int), ("consts", ctypes.POINTER(ctypes.c_void_p)),
+                ("const_scale", ctypes.POINTER(ctypes.c_double)), ("dev_relin_key", ctypes.c_void_p),
+                ("dev_conj_key", ctypes.c_void_p), ("n_rot_keys", ctypes.c_int),
+                ("rot_steps", ctypes.POINTER(ctypes.c_int64)), ("dev_rot_keys", ctypes.POINTER(ctypes.c_void_p))]
 
 
 _lib = None
@@ -163,6 +184,11 @@ def lib():
                                              ctypes.c_size_t, ctp, _vp]
         L.fides_modraise.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_mul_i.argtypes = [_vp, ctp, _i, ctp, _vp]
+        L.fides_program_create.argtypes = [_vp, ctypes.POINTER(fides_program_desc), ctypes.POINTER(_vp)]
+        L.fides_program_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i), ctypes.POINTER(_i)]
+        L.fides_program_run.argtypes = [_vp, ctp, ctp, _vp, ctypes.c_size_t, _vp]
+        L.fides_program_destroy.argtypes = [_vp]
+        L.fides_program_destroy.restype = None
         _lib = L
     return _lib
 
