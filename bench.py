@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server workload")
     ap.add_argument("--no-ops", action="store_true", help="skip hoisted rotations, linear transform, element-wise")
     ap.add_argument("--no-bootstrap", action="store_true", help="skip the bootstrapping workload")
+    ap.add_argument("--clocks-dir", default=None, help="where the sampled nvidia-smi clock log is written")
+    ap.add_argument("--bootstrap-only", action="store_true",
+                    help="run only the bootstrapping workload and print its JSON (for profiler launch lists)")
+    ap.add_argument("--bootstrap-batch", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -116,10 +120,11 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, directory: str | None = None):
+        import tempfile
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        self.path = os.path.join(directory or tempfile.gettempdir(), "clocks_rank%d.csv" % gpu_index)
 
     def start(self):
         try:
@@ -271,7 +276,7 @@ def run_fides(args, world, rank, local):
         ctx.rescale(out_m, nl, out_s, s)
         ctx.rotate(a, nl, 1 << (k % N_ROT), rks[k % N_ROT], out_r, scale)
 
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_dir)
     clocks.start()             # sampling runs through the warm-up and the timed region
     for k in range(args.warmup):
         step(k)
@@ -727,7 +732,8 @@ def run_bootstrap(args):
     t0 = time.perf_counter()
     dp = bt.DeviceProgram(ctx, prog, rlk, ck, rks)
     t_load = time.perf_counter() - t0
-    cts = [fides.to_device(np.stack([si.uniform_poly(st, q[:1], N) for _ in range(2)])) for _ in range(8)]
+    cts = [fides.to_device(np.stack([si.uniform_poly(st, q[:1], N) for _ in range(2)]))
+           for _ in range(args.bootstrap_batch)]
     outs = [torch.empty(2 * dp.out_limbs * N, dtype=torch.int64, device="cuda") for _ in cts]
     stream = torch.cuda.current_stream()
     launches0 = fides.kernel_launches()
@@ -741,18 +747,31 @@ def run_bootstrap(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # one more bootstrap with every operation and kernel bracketed by events
+    fides.trace_reset()
+    fides.trace_enable(True)
+    dp.run(cts[0], outs[0], 2.0 ** 50)
+    torch.cuda.synchronize()
+    fides.trace_enable(False)
+    tr = fides.trace_read()
+    fides.trace_reset()
+    top_ops = {k[3:]: [v[0], round(v[1], 2)] for k, v in sorted(tr.items(), key=lambda x: -x[1][1])
+               if k.startswith("op_") and k != "op_program"}
+    kern = {k: [v[0], round(v[1], 2)] for k, v in sorted(tr.items(), key=lambda x: -x[1][1]) if k.startswith("k_")}
     counts = {}
     for ins in prog.instr:
         counts[ins[0]] = counts.get(ins[0], 0) + 1
     names = {v: k for k, v in bt.OP.items()}
     res = {"workload": "bootstrap logN=16, 2^15 slots, L=30 (1 x 60-bit + 29 x 54-bit), K=10, dnum=3, "
-                       "CtS/StC level budget 3/3, EvalMod Chebyshev degree 119 + 2 double angles, batch of 8",
+                       "CtS/StC level budget 3/3, EvalMod Chebyshev degree 119 + 2 double angles, batch of %d" % len(cts),
            "ms_per_ciphertext": round(ms / len(cts), 2), "ms_per_batch": round(ms, 2), "batch": len(cts),
            "limbs_out": dp.out_limbs, "rotation_keys": len(prog.rot_steps),
            "plaintexts": sum(len(t["coeffs"]) for t in prog.lts), "instructions": len(prog.instr),
            "instruction_mix": {names[k]: v for k, v in sorted(counts.items())},
            "kernels_per_bootstrap": int(per_boot_launches), "device_buffers": dp.buffers,
-           "work_gib": round(dp.work_words * 8 / 2 ** 30, 2), "plan_s": round(t_plan, 1), "load_s": round(t_load, 1)}
+           "work_gib": round(dp.work_words * 8 / 2 ** 30, 2), "plan_s": round(t_plan, 1), "load_s": round(t_load, 1),
+           "traced_ops_calls_ms": top_ops, "traced_kernels_launches_ms": kern,
+           "traced_note": "one traced bootstrap; nested operations (a linear transform's rotations) count in both"}
     dp.close()
     del rks, cts, outs, key
     ctx.close()
@@ -910,7 +929,11 @@ def run_reference(args, world, rank):
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.bootstrap_only:
+        import torch
+        torch.cuda.set_device(local)
+        res = run_bootstrap(args)
+    elif args.impl == "reference":
         res = run_reference(args, world, rank)
     else:
         res = run_fides(args, world, rank, local)
