@@ -114,6 +114,15 @@ void fides_ctx_destroy(fides_ctx *ctx);
 int fides_ctx_autotune(fides_ctx *ctx, int max_limbs, void *stream);
 int fides_ctx_ntt_tile(const fides_ctx *ctx, int pass, int n_limbs);
 
+/*
+ * The tuned table itself, for an autotuner cache: FIDES_TUNE_ENTRIES bytes,
+ * the variant index per pass kind (4) and limb count (0..128).  set = 0
+ * copies the context's table out; set = 1 installs `table` (FIDES_ERR_ARG,
+ * nothing changed, if an entry is not a variant index).
+ */
+#define FIDES_TUNE_ENTRIES (4 * 129)
+int fides_ctx_tune_table(fides_ctx *ctx, unsigned char *table, int set);
+
 /* Number of digits in use at n_limbs limbs: ceil(n_limbs / alpha). */
 int fides_ctx_beta(const fides_ctx *ctx, int n_limbs);
 /* psi of prime index i (0..L+K-1), or 0 for a bad index. */

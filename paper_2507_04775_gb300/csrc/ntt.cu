@@ -192,3 +192,17 @@ extern "C" int fides_ctx_ntt_tile(const fides_ctx *c, int pass, int n_limbs)
     const int v = variant_of(c, pass, n_limbs);
     return (VAR_CT[v] << 8) | VAR_MINB[v];
 }
+
+extern "C" int fides_ctx_tune_table(fides_ctx *c, unsigned char *table, int set)
+{
+    if (!c || !table) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_tune_table: NULL argument");
+    const size_t n = sizeof(c->ntt_var);
+    if (!set) {
+        memcpy(table, c->ntt_var, n);
+        return FIDES_OK;
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (table[i] >= NVAR) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_tune_table: variant %d out of range", table[i]);
+    memcpy(c->ntt_var, table, n);
+    return FIDES_OK;
+}

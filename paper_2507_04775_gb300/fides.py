@@ -36,7 +36,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
-           "fides_program_info", "fides_program_run", "fides_program_destroy"]
+           "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -189,6 +189,7 @@ def lib():
         L.fides_program_run.argtypes = [_vp, ctp, ctp, _vp, ctypes.c_size_t, _vp]
         L.fides_program_destroy.argtypes = [_vp]
         L.fides_program_destroy.restype = None
+        L.fides_ctx_tune_table.argtypes = [_vp, ctypes.c_char_p, _i]
         _lib = L
     return _lib
 
@@ -301,9 +302,40 @@ class Context:
     def galois_elt(self, steps: int) -> int:
         return int(lib().fides_galois_elt(self._h, steps))
 
-    def autotune(self, max_limbs: int = 128, stream=None):
-        """Time the NTT tile variants per pass and limb count; keep the fastest."""
+    def autotune(self, max_limbs: int = 128, stream=None, cache: str | None = None):
+        """Time the NTT tile variants per pass and limb count; keep the fastest.
+        With `cache`, a table tuned earlier for the same device and parameters
+        is loaded from that JSON file instead, and a new one is saved there."""
+        key = None
+        if cache:
+            import json
+            import torch
+            key = {"device": torch.cuda.get_device_name(), "logN": self.logN, "L": self.L, "K": self.K,
+                   "library": version()}
+            try:
+                entry = json.load(open(cache))
+                if entry.get("key") == key:
+                    self.set_tune_table(bytes(entry["table"]))
+                    return
+            except (OSError, ValueError, KeyError, TypeError, FidesError):
+                pass
         _check(lib().fides_ctx_autotune(self._h, max_limbs, _stream(stream)))
+        if cache:
+            import json
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump({"key": key, "table": list(self.tune_table())}, f)
+            os.replace(tmp, cache)
+
+    def tune_table(self) -> bytes:
+        buf = ctypes.create_string_buffer(4 * 129)
+        _check(lib().fides_ctx_tune_table(self._h, buf, 0))
+        return buf.raw
+
+    def set_tune_table(self, table: bytes):
+        if len(table) != 4 * 129:
+            raise ValueError("a tune table has %d entries" % (4 * 129))
+        _check(lib().fides_ctx_tune_table(self._h, ctypes.create_string_buffer(bytes(table), 4 * 129), 1))
 
     def ntt_tile(self, pass_kind: int, n_limbs: int) -> int:
         """Tile width chosen for pass 0..3 (fwd cols, fwd rows, inv rows, inv cols)."""

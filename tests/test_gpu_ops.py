@@ -167,3 +167,19 @@ def test_modraise_and_mul_i_match_oracle(pairs, P, nl):
         g.mul_i(da, nl, out, sign=sign)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(out).reshape(a.shape), o.mul_monomial(a, k)), sign
+
+
+def test_autotune_cache_round_trip(pairs, tmp_path):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o = pairs(si.FULL)
+    path = str(tmp_path / "tune.json")
+    g.autotune(16, cache=path)
+    first = g.tune_table()
+    g.set_tune_table(bytes(len(first)))           # all variant 0
+    assert g.tune_table() == bytes(len(first))
+    g.autotune(16, cache=path)                    # loaded from the cache, not re-timed
+    assert g.tune_table() == first
+    with pytest.raises(FidesError):
+        g.set_tune_table(bytes([9]) * len(first))
+    assert g.tune_table() == first
