@@ -475,6 +475,10 @@ int64_t fides_now_ns(void);
  *   CONJ a (conjugation key)                       MULI a by i (arg = 1) or -i (arg = -1)
  *   CMULT a by constant #arg (scale times const_scale[arg])
  *   CADD constant #arg to a                        COPY a
+ *   CMAC: dst <- sum_t const[c_t] * reg[r_t] at `b` limbs, over term list #arg
+ *         (terms r_t, c_t: lin_reg / lin_const[lin_start[arg] .. lin_start[arg+1]),
+ *         1..32 terms, each register with at least b limbs, read in place;
+ *         scale = scale(r_0) * const_scale[c_0])
  * fides_program_create checks the program (operands defined before use,
  * levels consistent, keys present; FIDES_ERR_ARG naming the instruction),
  * copies every host table (device plaintexts and keys are referenced and must
@@ -498,6 +502,7 @@ int64_t fides_now_ns(void);
 #define FIDES_I_CMULT 10
 #define FIDES_I_CADD 11
 #define FIDES_I_COPY 12
+#define FIDES_I_CMAC 13
 
 typedef struct {
     int op, dst, a, b, arg;
@@ -525,6 +530,9 @@ typedef struct {
     int n_rot_keys;
     const int64_t *rot_steps;
     const uint64_t *const *dev_rot_keys;
+    int n_lin;                       /* CMAC term lists */
+    const int *lin_start;            /* [n_lin + 1] offsets */
+    const int *lin_reg, *lin_const;  /* [lin_start[n_lin]] */
 } fides_program_desc;
 
 typedef struct fides_program fides_program;

@@ -42,7 +42,7 @@ import numpy as np
 from oracle import encode
 
 # instruction codes (shared program format)
-MODRAISE, LT, RESCALE, DROP, HADD, HSUB, HMULT, CONJ, MULI, CMULT, CADD, COPY = range(1, 13)
+MODRAISE, LT, RESCALE, DROP, HADD, HSUB, HMULT, CONJ, MULI, CMULT, CADD, COPY, CMAC = range(1, 14)
 
 
 @dataclass
@@ -56,6 +56,7 @@ class Program:
     out_reg: int = 0
     rot_steps: list = field(default_factory=list)
     out_scale: float = 0.0
+    lins: list = field(default_factory=list)        # CMAC term lists: [(register, constant index)]
 
 
 # ---------------------------------------------------------------------------
@@ -184,9 +185,15 @@ class _Builder:
         return self.emit(DROP, a, arg=nl, level=nl, scale=self.scale[a])
 
     def adjust(self, a, nl):
-        """a at nl limbs with scale sigma[nl]."""
+        """a at nl limbs with scale sigma[nl] (computed once per register and level)."""
         if self.level[a] == nl:
             return a
+        memo = self.__dict__.setdefault("_adjusted", {})
+        if (a, nl) not in memo:
+            memo[(a, nl)] = self._adjust(a, nl)
+        return memo[(a, nl)]
+
+    def _adjust(self, a, nl):
         a = self.drop(a, nl + 1)
         cs = self.q[nl] * self.sigma[nl] / self.scale[a]
         k = self.const(self.residues(cs, nl + 1), cs)
@@ -306,16 +313,19 @@ def _evalmod(B: _Builder, u: int, coeffs, m: int, double_angle: int) -> int:
         G.append(B.cadd(B.add(g, g), -1.0))
 
     def leaf(c):
-        """sum_b c_b T_b at one level below the lowest T_b used, with scale sigma there."""
+        """sum_b c_b T_b at one level below the lowest T_b used, with scale sigma
+        there: one multiply-accumulate over the T_b (each read at its own level)
+        with constants c_b q sigma / scale(T_b), then a rescale."""
         terms = [b for b in range(1, len(c)) if c[b] != 0.0] or [1]
         out_nl = min(B.level[T[b]] for b in terms) - 1
-        acc = None
+        lin = []
         for b in terms:
-            tb = B.drop(T[b], out_nl + 1)
-            cs = B.q[out_nl] * B.sigma[out_nl] / B.scale[tb]
-            k = B.const(B.residues(c[b] * cs if b < len(c) else 0.0, out_nl + 1), cs)
-            p = B.emit(CMULT, tb, arg=k, level=out_nl + 1, scale=B.scale[tb] * cs)
-            acc = p if acc is None else B.emit(HADD, acc, p, level=out_nl + 1, scale=B.scale[acc])
+            cs = B.q[out_nl] * B.sigma[out_nl] / B.scale[T[b]]
+            lin.append((T[b], B.const(B.residues((c[b] if b < len(c) else 0.0) * cs, out_nl + 1), cs)))
+        B.prog.lins.append(lin)
+        k0 = lin[0][1]
+        acc = B.emit(CMAC, lin[0][0], out_nl + 1, len(B.prog.lins) - 1, level=out_nl + 1,
+                     scale=B.scale[lin[0][0]] * B.prog.const_scale[k0])
         acc = B.rescale(acc)
         return B.cadd(acc, c[0]) if c[0] else acc
 
@@ -344,7 +354,7 @@ def run(ctx, prog: Program, ct, relin_key, conj_key, rot_keys: dict, registers: 
     N = ctx.N
     R = {prog.in_reg: np.asarray(ct, dtype=np.uint64)}
     for op, dst, a, b, arg in prog.instr:
-        x = R[a]
+        x = R[a] if op != CMAC else None
         if op == MODRAISE:
             y = ctx.modraise(x, arg)
         elif op == LT:
@@ -371,6 +381,11 @@ def run(ctx, prog: Program, ct, relin_key, conj_key, rot_keys: dict, registers: 
             y = ctx.scalar_add(x, prog.consts[arg][:x.shape[1]])
         elif op == COPY:
             y = x.copy()
+        elif op == CMAC:
+            y = None
+            for r, k in prog.lins[arg]:
+                t = ctx.scalar_mult(np.ascontiguousarray(R[r][:, :b]), prog.consts[k][:b])
+                y = t if y is None else ctx.hadd(y, t)
         else:
             raise ValueError("unknown instruction %d" % op)
         R[dst] = y

@@ -38,7 +38,7 @@ import numpy as np
 from . import fides as F
 
 OP = {"MODRAISE": 1, "LT": 2, "RESCALE": 3, "DROP": 4, "HADD": 5, "HSUB": 6, "HMULT": 7, "CONJ": 8, "MULI": 9,
-      "CMULT": 10, "CADD": 11, "COPY": 12}
+      "CMULT": 10, "CADD": 11, "COPY": 12, "CMAC": 13}
 
 
 class BootProgram:
@@ -47,6 +47,7 @@ class BootProgram:
 
     def __init__(self):
         self.instr, self.lts, self.consts, self.const_scale, self.rot_steps = [], [], [], [], []
+        self.lins = []          # CMAC term lists [(register, constant index)]
         self.n_regs = self.in_reg = self.out_reg = 0
         self.out_scale = 0.0
 
@@ -161,6 +162,7 @@ class _Plan:
         self.p = BootProgram()
         self.lv, self.sc = [], []
         self.sigma = {}
+        self.lowered = {}
 
     def new(self, lv, sc):
         self.lv.append(lv)
@@ -185,9 +187,15 @@ class _Plan:
 
     def to_level(self, a, l):
         """a at l limbs with scale sigma[l] (one constant product and a rescale
-        when a has more limbs)."""
+        when a has more limbs; made once per register and level)."""
         if self.lv[a] == l:
             return a
+        key = (a, l)
+        if key not in self.lowered:
+            self.lowered[key] = self._lower(a, l)
+        return self.lowered[key]
+
+    def _lower(self, a, l):
         if self.lv[a] > l + 1:
             a = self.op("DROP", a, arg=l + 1, lv=l + 1)
         cs = self.q[l] * self.sigma[l] / self.sc[a]
@@ -281,15 +289,18 @@ def _evalmod(P: _Plan, u: int, coeffs, m: int, double_angle: int) -> int:
         giants.append(double(giants[-1]))
 
     def linear(c):
+        """sum_b c_b T_b: one multiply-accumulate reading every T_b at its own
+        level, constants chosen so the rescaled sum has scale sigma."""
         used = [b for b in range(1, len(c)) if c[b] != 0.0] or [1]
         l = min(P.lv[T[b]] for b in used) - 1
-        acc = None
+        terms = []
         for b in used:
-            tb = T[b] if P.lv[T[b]] == l + 1 else P.op("DROP", T[b], arg=l + 1, lv=l + 1)
-            cs = P.q[l] * P.sigma[l] / P.sc[tb]
-            k = P.constant((c[b] if b < len(c) else 0.0) * cs, l + 1, cs)
-            term = P.op("CMULT", tb, arg=k, sc=P.sc[tb] * cs)
-            acc = term if acc is None else P.op("HADD", acc, term)
+            cs = P.q[l] * P.sigma[l] / P.sc[T[b]]
+            terms.append((T[b], P.constant((c[b] if b < len(c) else 0.0) * cs, l + 1, cs)))
+        P.p.lins.append(terms)
+        first_reg, first_k = terms[0]
+        acc = P.op("CMAC", first_reg, b=l + 1, arg=len(P.p.lins) - 1, lv=l + 1,
+                   sc=P.sc[first_reg] * P.p.const_scale[first_k])
         acc = P.rescale(acc)
         return P.add_const(acc, c[0]) if c[0] != 0.0 else acc
 
@@ -370,7 +381,18 @@ class DeviceProgram:
         d.n_rot_keys = len(steps)
         d.rot_steps = ctypes.cast(st, ctypes.POINTER(ctypes.c_int64))
         d.dev_rot_keys = ctypes.cast(kp, ctypes.POINTER(ctypes.c_void_p))
-        self._refs = (ins, lt_arr, cptr, cscale, st, kp)
+        lins = getattr(prog, "lins", [])
+        starts = [0]
+        for lin in lins:
+            starts.append(starts[-1] + len(lin))
+        ls = (ctypes.c_int * len(starts))(*starts)
+        lr = (ctypes.c_int * max(1, starts[-1]))(*[r for lin in lins for r, _ in lin])
+        lc = (ctypes.c_int * max(1, starts[-1]))(*[k for lin in lins for _, k in lin])
+        d.n_lin = len(lins)
+        d.lin_start = ctypes.cast(ls, ctypes.POINTER(ctypes.c_int))
+        d.lin_reg = ctypes.cast(lr, ctypes.POINTER(ctypes.c_int))
+        d.lin_const = ctypes.cast(lc, ctypes.POINTER(ctypes.c_int))
+        self._refs = (ins, lt_arr, cptr, cscale, st, kp, ls, lr, lc)
         h = ctypes.c_void_p()
         F._check(F.lib().fides_program_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
         self._h = h

@@ -278,3 +278,68 @@ int launch_ptmac(const fides_ctx *c, const u64 *const *cts, const u64 *const *pt
     }
     return FIDES_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Multiply-accumulate of ciphertexts by scalar constants:
+//   out = sum_t k_t (.) x_t   at nl limbs,
+// where x_t may have more limbs than nl (its first nl limbs of each polynomial
+// are read in place, with its own polynomial stride) and k_t is row cidx[t]
+// of a device table of per-limb residues.  One 128-bit accumulator per word,
+// one reduction.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CmacArgs {
+    const u64 *x[FIDES_MAC_TERMS];
+    int xl[FIDES_MAC_TERMS];        // limbs of x_t (its polynomial stride in limbs)
+    int cidx[FIDES_MAC_TERMS];      // row of k_t in the constant table
+    const u64 *k;                   // [rows][kld] residues
+    int kld;
+    u64 *out;                       // [2][nl][N]
+    int nt, nl, logN;
+};
+
+__global__ void __launch_bounds__(256) k_cmac(const CmacArgs A, const PrimeInfo *__restrict__ P)
+{
+    pdl_enter();
+    const size_t S = (size_t)A.nl << A.logN;
+    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * S; w += (size_t)gridDim.x * blockDim.x) {
+        const int poly = w >= S;
+        const size_t wi = w - (poly ? S : 0);
+        const int z = (int)(wi >> A.logN);
+        const PrimeInfo p = P[z];
+        U128 s = {0, 0};
+        for (int t = 0; t < A.nt; ++t) {
+            const size_t off = poly ? ((size_t)A.xl[t] << A.logN) + wi : wi;
+            mac128(s, A.x[t][off], __ldg(A.k + (size_t)A.cidx[t] * A.kld + z));
+        }
+        A.out[w] = reduce128(s.hi, s.lo, p);
+    }
+}
+
+}  // namespace
+
+int launch_cmac(const fides_ctx *c, const u64 *const *x, const int *xl, const int *cidx, int nt, const u64 *k,
+                int kld, u64 *out, int nl, cudaStream_t st)
+{
+    if (nt < 1 || nt > FIDES_MAC_TERMS)
+        return fides_set_error(FIDES_ERR_ARG, "constant multiply-accumulate: %d terms outside [1, %d]", nt,
+                               FIDES_MAC_TERMS);
+    CmacArgs A;
+    memset(&A, 0, sizeof(A));
+    for (int t = 0; t < nt; ++t) {
+        A.x[t] = x[t];
+        A.xl[t] = xl[t];
+        A.cidx[t] = cidx[t];
+    }
+    A.k = k;
+    A.kld = kld;
+    A.out = out;
+    A.nt = nt;
+    A.nl = nl;
+    A.logN = c->logN;
+    const size_t words = 2 * ((size_t)nl << c->logN);
+    const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, (size_t)c->sms * 8);
+    FIDES_LAUNCH("k_cmac", st, k_cmac, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+    return fides_check_cuda(cudaGetLastError(), "constant multiply-accumulate launch");
+}

@@ -241,6 +241,12 @@ int fides_check_cuda(cudaError_t e, const char *what);
 int launch_ptmac(const fides_ctx *c, const u64 *const *cts, const u64 *const *pts, int nt, u64 *out, int nl,
                  bool accumulate, cudaStream_t st);
 
+// out = sum_t k[cidx[t]] (.) x[t] at nl limbs; x[t] has xl[t] >= nl limbs and is
+// read in place; k is a device table of rows of kld per-limb residues
+// (elementwise.cu)
+int launch_cmac(const fides_ctx *c, const u64 *const *x, const int *xl, const int *cidx, int nt, const u64 *k,
+                int kld, u64 *out, int nl, cudaStream_t st);
+
 // tracing (trace.cu)
 int fides_trace_begin(const char *name, cudaStream_t st);
 void fides_trace_end(int id, cudaStream_t st);

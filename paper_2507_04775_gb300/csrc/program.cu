@@ -32,6 +32,8 @@ struct fides_program {
     std::vector<Lt> lt;
     std::vector<std::vector<uint64_t>> consts;
     std::vector<double> const_scale;
+    u64 *dconst = nullptr;                      // device copy of the constants, [n_const][L]
+    std::vector<int> lin_start, lin_reg, lin_const;   // CMAC term lists
     const uint64_t *relin, *conj;
     std::vector<int64_t> rot_steps;
     std::vector<const uint64_t *> rot_keys;
@@ -46,6 +48,16 @@ namespace {
 
 bool reads_b(int op) { return op == FIDES_I_HADD || op == FIDES_I_HSUB || op == FIDES_I_HMULT; }
 
+// registers an instruction reads
+std::vector<int> operands(const fides_program *p, const fides_instr &I)
+{
+    if (I.op == FIDES_I_CMAC)
+        return std::vector<int>(p->lin_reg.begin() + p->lin_start[I.arg], p->lin_reg.begin() + p->lin_start[I.arg + 1]);
+    std::vector<int> r(1, I.a);
+    if (reads_b(I.op) && I.b != I.a) r.push_back(I.b);
+    return r;
+}
+
 int analyse(fides_program *p)
 {
     const fides_ctx *c = p->ctx;
@@ -59,6 +71,23 @@ int analyse(fides_program *p)
         auto bad = [&](const char *why) {
             return fides_set_error(FIDES_ERR_ARG, "fides_program_create: instruction %d (op %d): %s", i, I.op, why);
         };
+        if (I.op == FIDES_I_CMAC) {
+            if (I.arg < 0 || I.arg + 1 >= (int)p->lin_start.size()) return bad("no such term list");
+            const int t0 = p->lin_start[I.arg], t1 = p->lin_start[I.arg + 1];
+            if (t1 - t0 < 1 || t1 - t0 > FIDES_MAC_TERMS) return bad("a term list holds 1..32 terms");
+            if (I.dst < 0 || I.dst >= p->n_regs || def[I.dst] != -1) return bad("bad or reused destination");
+            if (I.b < 1 || I.b > c->L) return bad("bad target level");
+            for (int t = t0; t < t1; ++t) {
+                const int r = p->lin_reg[t], k = p->lin_const[t];
+                if (r < 0 || r >= p->n_regs || def[r] == -1) return bad("term register not defined");
+                if (p->level[r] < I.b) return bad("term below the target level");
+                if (k < 0 || k >= (int)p->consts.size()) return bad("no such constant");
+                last[r] = i;
+            }
+            p->level[I.dst] = I.b;
+            def[I.dst] = i;
+            continue;
+        }
         if (I.dst < 0 || I.dst >= p->n_regs || I.a < 0 || I.a >= p->n_regs) return bad("register out of range");
         if (def[I.a] == -1) return bad("operand a is not defined yet");
         if (reads_b(I.op) && (I.b < 0 || I.b >= p->n_regs || def[I.b] == -1)) return bad("operand b is not defined");
@@ -120,10 +149,11 @@ int analyse(fides_program *p)
         if (!free_list.empty()) { b = free_list.back(); free_list.pop_back(); }
         else b = count++;
         p->phys[I.dst] = b;
-        const int ops[2] = {I.a, reads_b(I.op) ? I.b : -1};
-        for (int k = 0; k < 2; ++k) {
-            const int r = ops[k];
-            if (r < 0 || r == p->in_reg || (k == 1 && r == I.a)) continue;
+        std::vector<int> ops = operands(p, I);
+        std::sort(ops.begin(), ops.end());
+        ops.erase(std::unique(ops.begin(), ops.end()), ops.end());
+        for (int r : ops) {
+            if (r == p->in_reg) continue;
             if (last[r] == i) free_list.push_back(p->phys[r]);
         }
         if (last[I.dst] < 0) free_list.push_back(b);   // never read
@@ -179,6 +209,27 @@ extern "C" int fides_program_create(fides_ctx *c, const fides_program_desc *d, f
         p->consts.emplace_back(d->consts[k], d->consts[k] + c->L);
         p->const_scale.push_back(d->const_scale[k]);
     }
+    if (d->n_lin > 0) {
+        if (!d->lin_start || !d->lin_reg || !d->lin_const) {
+            delete p;
+            return fides_set_error(FIDES_ERR_ARG, "fides_program_create: NULL term lists");
+        }
+        p->lin_start.assign(d->lin_start, d->lin_start + d->n_lin + 1);
+        const int nt = p->lin_start.back();
+        if (p->lin_start[0] != 0 || nt < 0) {
+            delete p;
+            return fides_set_error(FIDES_ERR_ARG, "fides_program_create: bad term list offsets");
+        }
+        for (int k = 0; k < d->n_lin; ++k)
+            if (p->lin_start[k + 1] < p->lin_start[k]) {
+                delete p;
+                return fides_set_error(FIDES_ERR_ARG, "fides_program_create: bad term list offsets");
+            }
+        p->lin_reg.assign(d->lin_reg, d->lin_reg + nt);
+        p->lin_const.assign(d->lin_const, d->lin_const + nt);
+    } else {
+        p->lin_start.assign(1, 0);
+    }
     p->relin = d->dev_relin_key;
     p->conj = d->dev_conj_key;
     p->rot_steps.assign(d->rot_steps, d->rot_steps + d->n_rot_keys);
@@ -187,11 +238,27 @@ extern "C" int fides_program_create(fides_ctx *c, const fides_program_desc *d, f
         delete p;
         return rc;
     }
+    if (!p->consts.empty()) {
+        std::vector<uint64_t> flat;
+        for (const auto &k : p->consts) flat.insert(flat.end(), k.begin(), k.end());
+        int rc = fides_check_cuda(cudaMalloc((void **)&p->dconst, flat.size() * sizeof(u64)), "fides_program_create");
+        if (!rc) rc = fides_check_cuda(cudaMemcpy(p->dconst, flat.data(), flat.size() * sizeof(u64), cudaMemcpyHostToDevice),
+                                       "fides_program_create");
+        if (rc) {
+            fides_program_destroy(p);
+            return rc;
+        }
+    }
     *out = p;
     return FIDES_OK;
 }
 
-extern "C" void fides_program_destroy(fides_program *p) { delete p; }
+extern "C" void fides_program_destroy(fides_program *p)
+{
+    if (!p) return;
+    cudaFree(p->dconst);
+    delete p;
+}
 
 extern "C" int fides_program_info(const fides_program *p, size_t *work_words, int *buffers, int *out_limbs)
 {
@@ -231,10 +298,27 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
     };
     for (size_t i = 0; i < p->instr.size(); ++i) {
         const fides_instr &I = p->instr[i];
-        fides_ct a = reg(I.a), d = reg(I.dst), b;
+        fides_ct d = reg(I.dst), a, b;
+        if (I.op != FIDES_I_CMAC) a = reg(I.a);
         if (reads_b(I.op)) b = reg(I.b);
         int rc = FIDES_OK;
         switch (I.op) {
+        case FIDES_I_CMAC: {
+            const int t0 = p->lin_start[I.arg], nt = p->lin_start[I.arg + 1] - t0;
+            std::vector<const u64 *> x(nt);
+            std::vector<int> xl(nt), ci(nt);
+            double sc = 0.0;
+            for (int t = 0; t < nt; ++t) {
+                const fides_ct r = reg(p->lin_reg[t0 + t]);
+                x[t] = r.data;
+                xl[t] = r.n_limbs;
+                ci[t] = p->lin_const[t0 + t];
+                if (t == 0) sc = r.scale * p->const_scale[ci[t]];
+            }
+            rc = launch_cmac(c, x.data(), xl.data(), ci.data(), nt, p->dconst, c->L, d.data, d.n_limbs, st);
+            d.scale = sc;
+            break;
+        }
         case FIDES_I_MODRAISE: rc = fides_modraise(c, &a, &d, stream); break;
         case FIDES_I_LT: {
             const fides_program::Lt &t = p->lt[I.arg];

@@ -104,7 +104,9 @@ class fides_program_desc(ctypes.Structure):
                 ("n_const", ctypes.c_int), ("consts", ctypes.POINTER(ctypes.c_void_p)),
                 ("const_scale", ctypes.POINTER(ctypes.c_double)), ("dev_relin_key", ctypes.c_void_p),
                 ("dev_conj_key", ctypes.c_void_p), ("n_rot_keys", ctypes.c_int),
-                ("rot_steps", ctypes.POINTER(ctypes.c_int64)), ("dev_rot_keys", ctypes.POINTER(ctypes.c_void_p))]
+                ("rot_steps", ctypes.POINTER(ctypes.c_int64)), ("dev_rot_keys", ctypes.POINTER(ctypes.c_void_p)),
+                ("n_lin", ctypes.c_int), ("lin_start", ctypes.POINTER(ctypes.c_int)),
+                ("lin_reg", ctypes.POINTER(ctypes.c_int)), ("lin_const", ctypes.POINTER(ctypes.c_int))]
 
 
 _lib = None

@@ -63,7 +63,7 @@ def as_eval_form(ctx, prog):
     evaluation-form residues (the oracle interpreter's format)."""
     out = obt.Program(instr=list(prog.instr), consts=list(prog.consts), const_scale=list(prog.const_scale),
                       n_regs=prog.n_regs, in_reg=prog.in_reg, out_reg=prog.out_reg, rot_steps=list(prog.rot_steps),
-                      out_scale=prog.out_scale)
+                      out_scale=prog.out_scale, lins=list(prog.lins))
     for t in prog.lts:
         lvl = t["level"]
         idx = list(range(lvl))
