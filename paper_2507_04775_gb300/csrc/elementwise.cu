@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(256) k_ptmac(MacArgs A, const PrimeInfo *__res
             s0.lo = A.out[w];
             s1.lo = A.out[w + 1];
         }
+#pragma unroll 4
         for (int t = 0; t < A.nt; ++t) {
             u64 x0, x1, y0, y1;
             if (VEC) {
@@ -299,21 +300,40 @@ struct CmacArgs {
     int nt, nl, logN;
 };
 
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_cmac(const CmacArgs A, const PrimeInfo *__restrict__ P)
 {
     pdl_enter();
     const size_t S = (size_t)A.nl << A.logN;
-    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * S; w += (size_t)gridDim.x * blockDim.x) {
+    // two words per thread and step (both in one limb: N is even)
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < S; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = 2 * v;
         const int poly = w >= S;
         const size_t wi = w - (poly ? S : 0);
         const int z = (int)(wi >> A.logN);
         const PrimeInfo p = P[z];
-        U128 s = {0, 0};
+        U128 s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll 4
         for (int t = 0; t < A.nt; ++t) {
-            const size_t off = poly ? ((size_t)A.xl[t] << A.logN) + wi : wi;
-            mac128(s, A.x[t][off], __ldg(A.k + (size_t)A.cidx[t] * A.kld + z));
+            const u64 *src = A.x[t] + (poly ? ((size_t)A.xl[t] << A.logN) + wi : wi);
+            const u64 k = __ldg(A.k + (size_t)A.cidx[t] * A.kld + z);
+            u64 x0, x1;
+            if (VEC) {
+                const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(src);
+                x0 = xv.x; x1 = xv.y;
+            } else {
+                x0 = src[0]; x1 = src[1];
+            }
+            mac128(s0, x0, k);
+            mac128(s1, x1, k);
         }
-        A.out[w] = reduce128(s.hi, s.lo, p);
+        const u64 r0 = reduce128(s0.hi, s0.lo, p), r1 = reduce128(s1.hi, s1.lo, p);
+        if (VEC) {
+            *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
+        } else {
+            A.out[w] = r0;
+            A.out[w + 1] = r1;
+        }
     }
 }
 
@@ -338,8 +358,13 @@ int launch_cmac(const fides_ctx *c, const u64 *const *x, const int *xl, const in
     A.nt = nt;
     A.nl = nl;
     A.logN = c->logN;
-    const size_t words = 2 * ((size_t)nl << c->logN);
-    const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, (size_t)c->sms * 8);
-    FIDES_LAUNCH("k_cmac", st, k_cmac, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+    const size_t pairs = (size_t)nl << c->logN;
+    const unsigned blocks = (unsigned)std::min<size_t>((pairs + 255) / 256, (size_t)c->sms * 8);
+    uintptr_t align = (uintptr_t)out;
+    for (int t = 0; t < nt; ++t) align |= (uintptr_t)x[t];
+    if ((align & 15) == 0)
+        FIDES_LAUNCH("k_cmac", st, k_cmac<true>, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
+    else
+        FIDES_LAUNCH("k_cmac", st, k_cmac<false>, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
     return fides_check_cuda(cudaGetLastError(), "constant multiply-accumulate launch");
 }
