@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--bootstrap-only", action="store_true",
                     help="run only the bootstrapping workload and print its JSON (for profiler launch lists)")
     ap.add_argument("--bootstrap-batch", type=int, default=8)
+    ap.add_argument("--ops-only", action="store_true",
+                    help="run only the hoisted-rotation / linear-transform / element-wise legs (profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -779,6 +781,22 @@ def run_bootstrap(args):
     return res
 
 
+def run_ops_only(args, local):
+    import torch
+
+    import paper_2507_04775_gb300 as fides
+    torch.cuda.set_device(local)
+    P = si.FULL
+    q = fides.find_primes(P.logN, P.q_bits, P.nq)
+    p = fides.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    ctx = fides.Context(P.logN, q, p, P.dnum)
+    A, B, keys = workload_inputs(P, q, p, si.workload_seed(1))
+    dA = [fides.to_device(x) for x in A]
+    dB = [fides.to_device(x) for x in B]
+    dK = [fides.to_device(x) for x in keys]
+    return {"ops": run_ops(args, ctx, dA, dB, dK, P, 2.0 ** P.log_scale)}
+
+
 def load_traffic(kernel, bytes_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources; else None."""
@@ -929,7 +947,9 @@ def run_reference(args, world, rank):
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.bootstrap_only:
+    if args.ops_only:
+        res = run_ops_only(args, local)
+    elif args.bootstrap_only:
         import torch
         torch.cuda.set_device(local)
         res = run_bootstrap(args)
