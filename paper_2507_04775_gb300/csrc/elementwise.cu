@@ -39,64 +39,72 @@ __device__ __forceinline__ u64 elem(u64 x, u64 y, int poly, const TwPair &k, con
     }
 }
 
-// b's word for word w (polynomial poly, offset wi within it)
-template <int OP>
-__device__ __forceinline__ size_t b_index(size_t w, size_t wi)
+template <bool VEC>
+__device__ __forceinline__ void load2(const u64 *p, u64 &x0, u64 &x1)
 {
-    return (OP == E_HADD || OP == E_HSUB) ? w : wi;
+    if (VEC) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        x0 = v.x; x1 = v.y;
+    } else {
+        x0 = p[0]; x1 = p[1];
+    }
 }
 
+template <bool VEC>
+__device__ __forceinline__ void store2(u64 *p, u64 x0, u64 x1)
+{
+    if (VEC) {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x0, x1);
+    } else {
+        p[0] = x0; p[1] = x1;
+    }
+}
+
+// Each thread step handles two consecutive words at the same position of both
+// polynomials, so a plaintext operand is read once for both.
 template <int OP, bool VEC>
 __global__ void __launch_bounds__(256) k_elem(ElemArgs A, const PrimeInfo *__restrict__ P)
 {
     pdl_enter();
     const size_t S = (size_t)A.nl << A.logN;     // words of one polynomial
-    const size_t pairs = S;                      // 2 S words, two per step
-    const bool reads_b = OP == E_HADD || OP == E_HSUB || OP == E_PTADD || OP == E_PTMULT;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < pairs; v += (size_t)gridDim.x * blockDim.x) {
-        const size_t w = 2 * v;
-        const int poly = w >= S;
-        const size_t wi = w - (poly ? S : 0);
+    const bool two_b = OP == E_HADD || OP == E_HSUB;
+    const bool pt_b = OP == E_PTADD || OP == E_PTMULT;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < S / 2; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t wi = 2 * v;
         const int z = (int)(wi >> A.logN);
         const PrimeInfo p = P[z];
         const TwPair k = (OP == E_SCALAR_ADD || OP == E_SCALAR_MULT || OP == E_MULI) ? A.k[z] : TwPair{0, 0};
-        u64 x0, x1, y0 = 0, y1 = 0;
-        if (VEC) {
-            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.a + w);
-            x0 = x.x; x1 = x.y;
-            if (reads_b && !(OP == E_PTADD && poly)) {
-                const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(A.b + b_index<OP>(w, wi));
-                y0 = y.x; y1 = y.y;
-            }
-        } else {
-            x0 = A.a[w]; x1 = A.a[w + 1];
-            if (reads_b && !(OP == E_PTADD && poly)) {
-                y0 = A.b[b_index<OP>(w, wi)];
-                y1 = A.b[b_index<OP>(w, wi) + 1];
-            }
+        u64 x[4], y[4] = {0, 0, 0, 0};
+        load2<VEC>(A.a + wi, x[0], x[1]);
+        load2<VEC>(A.a + S + wi, x[2], x[3]);
+        if (two_b) {
+            load2<VEC>(A.b + wi, y[0], y[1]);
+            load2<VEC>(A.b + S + wi, y[2], y[3]);
+        } else if (pt_b) {
+            load2<VEC>(A.b + wi, y[0], y[1]);
+            y[2] = y[0];
+            y[3] = y[1];
         }
-        u64 r0 = elem<OP>(x0, y0, poly, k, p), r1 = elem<OP>(x1, y1, poly, k, p);
+        u64 r[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r[i] = elem<OP>(x[i], y[i], i >> 1, k, p);
         if (OP == E_MULI) {
             // X^(N/2) at the point psi^(2 brv(j) + 1) is i_q^(2 brv(j) + 1) = i_q (-1)^brv(j), and brv(j)
             // is odd exactly in the upper half of the limb
             if ((int)((wi >> (A.logN - 1)) & 1) != A.neg) {
-                r0 = r0 ? p.q - r0 : 0;
-                r1 = r1 ? p.q - r1 : 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) r[i] = r[i] ? p.q - r[i] : 0;
             }
         }
-        if (VEC) {
-            *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
-        } else {
-            A.out[w] = r0;
-            A.out[w + 1] = r1;
-        }
+        store2<VEC>(A.out + wi, r[0], r[1]);
+        store2<VEC>(A.out + S + wi, r[2], r[3]);
     }
 }
 
 template <int OP>
 int launch_elem(const fides_ctx *c, const ElemArgs &A, cudaStream_t st)
 {
-    const size_t pairs = (size_t)A.nl << A.logN;
+    const size_t pairs = ((size_t)A.nl << A.logN) / 2;
     const size_t want = (pairs + 255) / 256;
     const unsigned blocks = (unsigned)std::min<size_t>(want, (size_t)c->sms * 8);
     const bool vec = (((uintptr_t)A.a | (uintptr_t)A.b | (uintptr_t)A.out) & 15) == 0;
@@ -217,36 +225,29 @@ __global__ void __launch_bounds__(256) k_ptmac(MacArgs A, const PrimeInfo *__res
 {
     pdl_enter();
     const size_t S = (size_t)A.nl << A.logN;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < S; v += (size_t)gridDim.x * blockDim.x) {
-        const size_t w = 2 * v;
-        const size_t wi = w - (w >= S ? S : 0);
+    // two consecutive words at the same position of both polynomials per
+    // step: each plaintext word is read once
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < S / 2; v += (size_t)gridDim.x * blockDim.x) {
+        const size_t wi = 2 * v;
         const PrimeInfo p = P[(int)(wi >> A.logN)];
-        U128 s0 = {0, 0}, s1 = {0, 0};
+        U128 s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
         if (A.accumulate) {
-            s0.lo = A.out[w];
-            s1.lo = A.out[w + 1];
+            load2<VEC>(A.out + wi, s[0].lo, s[1].lo);
+            load2<VEC>(A.out + S + wi, s[2].lo, s[3].lo);
         }
-#pragma unroll 4
+#pragma unroll 2
         for (int t = 0; t < A.nt; ++t) {
-            u64 x0, x1, y0, y1;
-            if (VEC) {
-                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.ct[t] + w);
-                const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(A.pt[t] + wi);
-                x0 = x.x; x1 = x.y; y0 = y.x; y1 = y.y;
-            } else {
-                x0 = A.ct[t][w]; x1 = A.ct[t][w + 1];
-                y0 = A.pt[t][wi]; y1 = A.pt[t][wi + 1];
-            }
-            mac128(s0, x0, y0);
-            mac128(s1, x1, y1);
+            u64 x[4], y0, y1;
+            load2<VEC>(A.ct[t] + wi, x[0], x[1]);
+            load2<VEC>(A.ct[t] + S + wi, x[2], x[3]);
+            load2<VEC>(A.pt[t] + wi, y0, y1);
+            mac128(s[0], x[0], y0);
+            mac128(s[1], x[1], y1);
+            mac128(s[2], x[2], y0);
+            mac128(s[3], x[3], y1);
         }
-        const u64 r0 = reduce128(s0.hi, s0.lo, p), r1 = reduce128(s1.hi, s1.lo, p);
-        if (VEC) {
-            *reinterpret_cast<ulonglong2 *>(A.out + w) = make_ulonglong2(r0, r1);
-        } else {
-            A.out[w] = r0;
-            A.out[w + 1] = r1;
-        }
+        store2<VEC>(A.out + wi, reduce128(s[0].hi, s[0].lo, p), reduce128(s[1].hi, s[1].lo, p));
+        store2<VEC>(A.out + S + wi, reduce128(s[2].hi, s[2].lo, p), reduce128(s[3].hi, s[3].lo, p));
     }
 }
 
@@ -269,8 +270,8 @@ int launch_ptmac(const fides_ctx *c, const u64 *const *cts, const u64 *const *pt
         A.nl = nl;
         A.logN = c->logN;
         A.accumulate = (accumulate || t0 > 0) ? 1 : 0;
-        const size_t S = (size_t)nl << c->logN;
-        const unsigned blocks = (unsigned)std::min<size_t>((S + 255) / 256, (size_t)c->sms * 8);
+        const size_t pairs = ((size_t)nl << c->logN) / 2;
+        const unsigned blocks = (unsigned)std::min<size_t>((pairs + 255) / 256, (size_t)c->sms * 8);
         if ((align & 15) == 0)
             FIDES_LAUNCH("k_ptmac", st, k_ptmac<true>, dim3(blocks), dim3(256), A, (const PrimeInfo *)c->d_prime);
         else
