@@ -699,6 +699,21 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
         ew[name] = {"us": round(t * 1e3, 2), "GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 3)}
     del flush
     res["elementwise"] = ew
+    # the logN=12 set (3 x 40-bit q, 1 x 50-bit p, dnum 3): latency of one HMult+relin
+    S = si.SMALL
+    sq = fides.find_primes(S.logN, S.q_bits, S.nq)
+    sp = fides.find_primes(S.logN, S.p_bits, S.nk, exclude=sq)
+    sctx = fides.Context(S.logN, sq, sp, S.dnum)
+    st2 = si.Stream(si.workload_seed(0), 21)
+    sa = fides.to_device(np.stack([si.uniform_poly(st2, sq, sctx.N) for _ in range(2)]))
+    sb = fides.to_device(np.stack([si.uniform_poly(st2, sq, sctx.N) for _ in range(2)]))
+    skey = fides.to_device(np.stack([np.stack([si.uniform_poly(st2, sq + sp, sctx.N) for _ in range(2)])
+                                     for _ in range(S.dnum)]))
+    so = torch.empty_like(sa)
+    t_small = timed(lambda: sctx.hmult(sa, sb, S.nq, skey, so), 200)
+    res["hmult_logN12_L3"] = {"us": round(t_small * 1e3, 2), "launches": 11,
+                              "note": "one call at a time; latency bound (each launch covers 3 to 4 limbs of 32 KiB)"}
+    sctx.close()
     res["elementwise_note"] = ("device time of the kernel (CUDA events around each launch), L2 flushed before each "
                                "launch; 30-limb operands; bytes = operands read + result written once")
     return res
