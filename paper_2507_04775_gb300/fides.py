@@ -611,6 +611,7 @@ class Server:
         self._h = h
         self._keep = {}     # request id -> input tensors, until completion
         self._keys = []     # registered key tensors
+        self._poll_buf = {}
 
     @staticmethod
     def _addr(t, words, name):
@@ -640,7 +641,9 @@ class Server:
         return rid.value
 
     def poll(self, max_n: int = 256, timeout_us: int = 0) -> list:
-        buf = (fides_completion * max_n)()
+        buf = self._poll_buf.get(max_n)
+        if buf is None:
+            buf = self._poll_buf[max_n] = (fides_completion * max_n)()
         n = ctypes.c_int(0)
         _check(lib().fides_server_poll(self._h, buf, max_n, timeout_us, ctypes.byref(n)))
         out = [Completion(buf[i], self.N) for i in range(n.value)]
