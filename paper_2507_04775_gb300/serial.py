@@ -31,9 +31,13 @@ def primes_digest(ctx) -> bytes:
 
 
 def _as_host(x) -> np.ndarray:
+    """The residues as a host uint64 array (int64 input keeps its bits)."""
     if hasattr(x, "detach"):                       # a torch tensor (device or host)
         x = x.detach().cpu().contiguous().numpy()
-    return np.ascontiguousarray(x).view(np.uint64) if np.asarray(x).dtype == np.int64 else np.ascontiguousarray(x, dtype=np.uint64)
+    x = np.ascontiguousarray(x)
+    if x.dtype == np.int64:
+        return x.view(np.uint64)
+    return x.astype(np.uint64, copy=False)
 
 
 def _write(path, magic, ctx, data, n_limbs, n_polys, scale):
