@@ -268,7 +268,9 @@ struct IPArgs {
     IPOp one;
 };
 
-template <int MAXB>
+// V2: two consecutive coefficients per thread with 16-byte loads and stores
+// (only without an automorphism and with 16-byte-aligned buffers).
+template <int MAXB, bool V2>
 __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfull, const PrimeInfo *__restrict__ P,
                                            int logN)
 {
@@ -277,10 +279,39 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const int pz = z < nl ? z : L + (z - nl);
     const int own = z < nl ? z / op.alpha : -1;
     const PrimeInfo pr = P[pz];
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * (V2 ? 2 : 1);
     const u64 *__restrict__ ext = op.ext;
     const u64 *__restrict__ evk = op.evk;
     const u64 *__restrict__ dsrc = op.dsrc;
+    u64 *acc = op.acc;
+    if (V2) {
+        // issue every load before the first product (the kernel is bound by HBM)
+        ulonglong2 e[MAXB], k0[MAXB], k1[MAXB];
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+            if (j < beta) {
+                const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
+                e[j] = *reinterpret_cast<const ulonglong2 *>(src + n);
+                k0[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 0) * nfull + pz) * N + n);
+                k1[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 1) * nfull + pz) * N + n);
+            }
+        }
+        U128 a0 = {0, 0}, a1 = {0, 0}, b0 = {0, 0}, b1 = {0, 0};
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+            if (j < beta) {
+                mac128(a0, e[j].x, k0[j].x);
+                mac128(b0, e[j].y, k0[j].y);
+                mac128(a1, e[j].x, k1[j].x);
+                mac128(b1, e[j].y, k1[j].y);
+            }
+        }
+        *reinterpret_cast<ulonglong2 *>(acc + (size_t)z * N + n) =
+            make_ulonglong2(reduce128(a0.hi, a0.lo, pr), reduce128(b0.hi, b0.lo, pr));
+        *reinterpret_cast<ulonglong2 *>(acc + ((size_t)ne + z) * N + n) =
+            make_ulonglong2(reduce128(a1.hi, a1.lo, pr), reduce128(b1.hi, b1.lo, pr));
+        return;
+    }
     // hoisted rotation: the digits are read through sigma_g (evaluation form:
     // slot n takes slot brv(((2 brv(n) + 1) g mod 2N - 1) / 2))
     size_t sn = n;
@@ -308,9 +339,14 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
             mac128(a1, e[j], k1[j]);
         }
     }
-    u64 *acc = op.acc;
     acc[(size_t)z * N + n] = reduce128(a0.hi, a0.lo, pr);
     acc[((size_t)ne + z) * N + n] = reduce128(a1.hi, a1.lo, pr);
+}
+
+// whether an op can take the paired path
+inline bool ip_pairs_ok(const IPOp &o)
+{
+    return o.g == 0 && ((((uintptr_t)o.ext | (uintptr_t)o.dsrc | (uintptr_t)o.evk | (uintptr_t)o.acc) & 15) == 0);
 }
 
 // index of the op holding row z in a table with exclusive prefix sums
@@ -326,35 +362,45 @@ __device__ __forceinline__ int find_op(const int *__restrict__ pre, int nop, int
 
 // MAXB: the largest digit count of the ops in the launch (loads for digits
 // >= an op's own count are predicated off).
-template <int MAXB>
+template <int MAXB, bool V2>
 __global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
 {
     pdl_enter();
     const int z = blockIdx.y;
     if (A.dop) {
         const int k = find_op(A.dpre, A.nop, z);
-        inner_body<MAXB>(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
+        inner_body<MAXB, V2>(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
     } else {
-        inner_body<MAXB>(A.one, z, L, nfull, P, logN);
+        inner_body<MAXB, V2>(A.one, z, L, nfull, P, logN);
     }
 }
 
 template <int MAXB>
-void launch_inner_b(const fides_ctx *c, const IPArgs &A, int total_limbs, cudaStream_t st)
+void launch_inner_b(const fides_ctx *c, const IPArgs &A, int total_limbs, bool pairs, cudaStream_t st)
 {
-    dim3 grid(c->N / 256, total_limbs);
-    FIDES_LAUNCH("k_inner", st, k_inner<MAXB>, grid, dim3(256), A, c->L, c->L + c->K, (const PrimeInfo *)c->d_prime,
-                 c->logN);
+    if (pairs) {
+        dim3 grid(c->N / 512, total_limbs);
+        FIDES_LAUNCH("k_inner", st, (k_inner<MAXB, true>), grid, dim3(256), A, c->L, c->L + c->K,
+                     (const PrimeInfo *)c->d_prime, c->logN);
+    } else {
+        dim3 grid(c->N / 256, total_limbs);
+        FIDES_LAUNCH("k_inner", st, (k_inner<MAXB, false>), grid, dim3(256), A, c->L, c->L + c->K,
+                     (const PrimeInfo *)c->d_prime, c->logN);
+    }
 }
 
-inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, int max_beta, cudaStream_t st)
+// pairs: < 0 decides from the inline op; the batched path passes what it
+// found for all ops of the table
+inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, int max_beta, cudaStream_t st,
+                        int pairs = -1)
 {
+    const bool p2 = pairs < 0 ? (!A.dop && ip_pairs_ok(A.one)) : pairs != 0;
     switch (max_beta) {
-    case 1: launch_inner_b<1>(c, A, total_limbs, st); break;
-    case 2: launch_inner_b<2>(c, A, total_limbs, st); break;
-    case 3: launch_inner_b<3>(c, A, total_limbs, st); break;
-    case 4: launch_inner_b<4>(c, A, total_limbs, st); break;
-    default: launch_inner_b<FIDES_MAX_DIGITS>(c, A, total_limbs, st); break;
+    case 1: launch_inner_b<1>(c, A, total_limbs, p2, st); break;
+    case 2: launch_inner_b<2>(c, A, total_limbs, p2, st); break;
+    case 3: launch_inner_b<3>(c, A, total_limbs, p2, st); break;
+    case 4: launch_inner_b<4>(c, A, total_limbs, p2, st); break;
+    default: launch_inner_b<FIDES_MAX_DIGITS>(c, A, total_limbs, p2, st); break;
     }
     return fides_check_cuda(cudaGetLastError(), "inner product launch");
 }

@@ -23,6 +23,7 @@ struct Launch {
     int ns, max_dst;
     IPArgs ip;         // L_INNER
     int max_beta;      // L_INNER
+    int ip_pairs;      // L_INNER: every op can take the paired path
     int total;         // grid.y of L_INNER
 };
 
@@ -101,7 +102,11 @@ void plan_inner(Plan &P, const std::vector<IPOp> &ops, const std::vector<int> &r
     for (size_t i = 0; i < ops.size(); ++i) { pre[i] = tot; tot += rows[i]; }
     l.total = tot;
     l.ip.nop = (int)ops.size();
-    for (const IPOp &o : ops) l.max_beta = std::max(l.max_beta, o.beta);
+    l.ip_pairs = 1;
+    for (const IPOp &o : ops) {
+        l.max_beta = std::max(l.max_beta, o.beta);
+        if (!ip_pairs_ok(o)) l.ip_pairs = 0;
+    }
     P.launches.push_back(l);
     const int id = (int)P.launches.size() - 1;
     P.pend.push_back(Pending{id, 3, P.add(ops.data(), sizeof(IPOp) * ops.size())});
@@ -222,7 +227,7 @@ int plan_run(const fides_ctx *c, const std::vector<Launch> &launches, cudaStream
         case L_NTT_SUBMUL: rc = ntt_forward(c, l.set, ProSrc{}, EpiSubMul{}, st); break;
         case L_NTT_SWITCH_SUBMUL: rc = ntt_forward(c, l.set, ProSwitchMod{}, EpiSubMul{}, st); break;
         case L_BCONV: rc = launch_bconv_group(c, l.bc, l.ns, l.max_dst, st); break;
-        case L_INNER: rc = launch_inner(c, l.ip, l.total, l.max_beta, st); break;
+        case L_INNER: rc = launch_inner(c, l.ip, l.total, l.max_beta, st, l.ip_pairs); break;
         }
         if (rc) return rc;
     }

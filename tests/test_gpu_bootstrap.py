@@ -78,6 +78,7 @@ def test_planned_program_matches_oracle_and_decrypts_logN12():
     ref = obt.run(o, as_eval_form(o, prog), ct, *hkeys)
     assert np.array_equal(got, ref)
     err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
+    print("bootstrap logN=12 relative slot error 2^%.2f" % np.log2(err))
     assert err < 2.0 ** -12, err
     g.close()
 
@@ -93,6 +94,7 @@ def test_bootstrap_logN16_decrypts():
     ct = cl.encrypt(z, 1, 2.0 ** 50)
     got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)
     err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
+    print("bootstrap logN=16 relative slot error 2^%.2f" % np.log2(err))
     assert err < 2.0 ** -12, err
     g.close()
 
