@@ -202,3 +202,5 @@ SMALL = ParamSet("logN12-L3-K1-dnum3", 12, 3, 40, 1, 50, 3, 40)
 FULL = ParamSet("logN16-L30-K10-dnum3", 16, 30, 54, 10, 60, 3, 40)
 # a mid-size set for fast checks that still spans several digits and tiles
 MID = ParamSet("logN12-L12-K4-dnum3", 12, 12, 54, 4, 60, 3, 40)
+# the most primes a context takes (L + K = 64): digits of 16 limbs and 16 special primes
+WIDE = ParamSet("logN12-L48-K16-dnum3", 12, 48, 54, 16, 60, 3, 40)

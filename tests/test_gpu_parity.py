@@ -4,7 +4,9 @@ for residue (bit-exact), on seeded inputs.
 Sizes: the logN=12 workload (3 limbs, K=1, dnum=3) and a logN=12 set with 12
 limbs (K=4, alpha=4: several digits, a ragged last digit) run in full; the
 logN=16 workload (30 limbs, K=10, dnum=3) runs in full at the top level and
-at ragged levels.  Keys are uniform residues (parity does not depend on key
+at ragged levels; a logN=12 set with the most primes a context takes (48 q +
+16 special = 64; digits of 16 limbs, beyond the unrolled conversion sizes)
+covers the generic paths.  Keys are uniform residues (parity does not depend on key
 structure); decryption through real keys is checked separately.
 """
 import numpy as np
@@ -26,7 +28,7 @@ def make_pair(P):
     return Context(P.logN, q, p, P.dnum), oracle.Context(P.logN, q, p, P.dnum)
 
 
-@pytest.fixture(scope="module", params=["SMALL", "MID", "FULL"])
+@pytest.fixture(scope="module", params=["SMALL", "MID", "FULL", "WIDE"])
 def pair(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
