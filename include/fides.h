@@ -85,7 +85,8 @@ int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, in
 /*
  * Creates a context on the current CUDA device (Sec. III-E "Precomputation":
  * per-prime constants are computed once at context creation).
- *   logN   : ring degree N = 2^logN; this build supports logN in {12, 16}.
+ *   logN   : ring degree N = 2^logN, 12 <= logN <= 17 (one tile per limb at
+ *            12; two-pass NTTs above).
  *   L      : number of q-primes (maximum ciphertext limbs), 1 <= L.
  *   K      : number of special primes, 1 <= K, L + K <= 64.
  *   dnum   : number of key-switching digits, 1 <= dnum <= L.

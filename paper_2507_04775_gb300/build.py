@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfides.so")
-SOURCES = ["ctx.cu", "ntt.cu", "keyswitch.cu", "batch.cu", "server.cu", "elementwise.cu", "lintrans.cu", "program.cu", "trace.cu", "noalloc.cu", "peak.cu"]
+SOURCES = ["ctx.cu", "ntt.cu", "ntt_l12.cu", "ntt_l13.cu", "ntt_l14.cu", "ntt_l15.cu", "ntt_l16.cu", "ntt_l17.cu", "keyswitch.cu", "batch.cu", "server.cu", "elementwise.cu", "lintrans.cu", "program.cu", "trace.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

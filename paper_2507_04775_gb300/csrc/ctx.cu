@@ -203,8 +203,8 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     *out = nullptr;
     if (!primes || L < 1 || K < 1 || L + K > FIDES_MAX_PRIMES || dnum < 1 || dnum > L)
         return fides_set_error(FIDES_ERR_ARG, "fides_ctx_create: bad sizes (L=%d K=%d dnum=%d)", L, K, dnum);
-    if (logN != 12 && logN != 16)
-        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: logN=%d (supported: 12, 16)", logN);
+    if (logN < 12 || logN > 17)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: logN=%d (supported: 12..17)", logN);
     int alpha = (L + dnum - 1) / dnum;
     if (alpha > FIDES_MAX_SRC || K > FIDES_MAX_SRC)
         return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_create: digit size %d or K=%d above %d",

@@ -241,7 +241,7 @@ int plan_kernel_count(const fides_ctx *c, const std::vector<Launch> &launches)
     for (const Launch &l : launches) {
         const bool ntt = l.kind == L_INTT || l.kind == L_NTT || l.kind == L_NTT_SUBMUL ||
                          l.kind == L_NTT_SWITCH_SUBMUL;
-        n += ntt ? (c->logN == 16 ? 2 : 1) : 1;
+        n += ntt ? (c->logN == 12 ? 1 : 2) : 1;
     }
     return n;
 }

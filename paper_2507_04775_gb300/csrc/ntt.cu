@@ -4,120 +4,50 @@
 // context parameter (Sec. III-F1) whose best value depends on the GPU
 // (Sec. IV).  Here one launch always covers every limb of a step; what is left
 // to tune is the tile width of each pass, which decides how many CTAs a launch
-// has and so how much of its last wave is empty.  Three variants of each
-// logN=16 pass are compiled -- 16, 8 or 4 columns/rows per CTA (256, 128 or 64
-// threads) with up to 80 registers (3, 6 or 12 resident CTAs per SM), and 4
-// or 8 per CTA with up to 64 registers (16 or 8 per SM) -- and the context keeps, per pass
-// kind and limb count, the variant to launch: a fixed default, or the fastest
-// measured one after fides_ctx_autotune.
+// has and so how much of its last wave is empty.  Five variants of each pass
+// of a two-pass transform (logN 13..17) are compiled -- at logN=16, 16, 8 or
+// 4 columns/rows per CTA (256, 128 or 64 threads) with up to 80 registers (3,
+// 6 or 12 resident CTAs per SM), and 4 or 8 per CTA with up to 64 registers
+// (16 or 8 per SM); other sizes scale the resident-CTA target to the same
+// register budget (ntt_impl.cuh) -- and the context keeps, per pass kind and
+// limb count, the variant to launch: a fixed default, or the fastest measured
+// one after fides_ctx_autotune.  The launchers of each ring degree live in
+// ntt_l12.cu .. ntt_l17.cu; this file dispatches on the context's logN.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
-#include "fides_internal.cuh"
-#include "ntt.cuh"
+#include "ntt_impl.cuh"
 
-namespace {
-
-constexpr int NVAR = 5;
-constexpr int VAR_CT[NVAR] = {16, 8, 4, 4, 8};
-constexpr int VAR_MINB[NVAR] = {3, 6, 12, 16, 8};   // 3/6/12: up to 80 registers; 16/8: up to 64
-
-enum PassKind { FWD_COLS = 0, FWD_ROWS = 1, INV_ROWS = 2, INV_COLS = 3 };
-
-int variant_of(const fides_ctx *c, int kind, int total)
-{
-    return c->ntt_var[kind][total > FIDES_TUNE_MAX ? FIDES_TUNE_MAX : total];
-}
-
-template <int V, int KIND, bool INV, bool NINV, class Pro, class Epi>
-void launch_pass(const fides_ctx *c, const LimbSet &set, const TwPair *tw, Pro pro, Epi epi, cudaStream_t st,
-                 const char *name)
-{
-    constexpr int CT = VAR_CT[V], MINB = VAR_MINB[V];
-    auto k = k_ntt<16, 8, KIND, INV, NINV, CT, MINB, Pro, Epi>;
-    dim3 grid(256 / CT, set.total), block(16 * CT);
-    FIDES_LAUNCH(name, st, k, grid, block, set, (const PrimeInfo *)c->d_prime, tw, pro, epi);
-}
-
-template <int KIND, bool INV, bool NINV, class Pro, class Epi>
-void launch_pass_v(int v, const fides_ctx *c, const LimbSet &set, const TwPair *tw, Pro pro, Epi epi,
-                   cudaStream_t st, const char *name)
-{
-    switch (v) {
-    case 0: launch_pass<0, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
-    case 1: launch_pass<1, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
-    case 2: launch_pass<2, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
-    case 3: launch_pass<3, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
-    default: launch_pass<4, KIND, INV, NINV>(c, set, tw, pro, epi, st, name); break;
+#define FIDES_NTT_DISPATCH(fn, ...)                                  \
+    switch (c->logN) {                                               \
+    case 12: return fn##_12(__VA_ARGS__);                            \
+    case 13: return fn##_13(__VA_ARGS__);                            \
+    case 14: return fn##_14(__VA_ARGS__);                            \
+    case 15: return fn##_15(__VA_ARGS__);                            \
+    case 16: return fn##_16(__VA_ARGS__);                            \
+    default: return fn##_17(__VA_ARGS__);                            \
     }
-}
 
-template <class Pro, class Epi>
-int forward(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaStream_t st)
-{
-    if (set.total == 0) return FIDES_OK;
-    if (c->logN == 16) {
-        launch_pass_v<0, false, false>(variant_of(c, FWD_COLS, set.total), c, set, c->d_tw, pro, EpiLazy{}, st,
-                                       "k_ntt_fwd_cols");
-        launch_pass_v<1, false, false>(variant_of(c, FWD_ROWS, set.total), c, set, c->d_tw, ProDst{}, epi, st,
-                                       "k_ntt_fwd_rows");
-    } else {
-        auto k = k_ntt<12, 12, 2, false, false, 16, 3, Pro, Epi>;
-        FIDES_LAUNCH("k_ntt_fwd_limb", st, k, dim3(1, set.total), dim3(256), set, (const PrimeInfo *)c->d_prime,
-                     (const TwPair *)c->d_tw, pro, epi);
-    }
-    return fides_check_cuda(cudaGetLastError(), "ntt forward launch");
-}
-
-template <class Pro, class Epi>
-int inverse(const fides_ctx *c, const LimbSet &set, Pro pro, Epi epi, cudaStream_t st)
-{
-    if (set.total == 0) return FIDES_OK;
-    if (c->logN == 16) {
-        launch_pass_v<1, true, false>(variant_of(c, INV_ROWS, set.total), c, set, c->d_itw, pro, EpiLazy{}, st,
-                                      "k_ntt_inv_rows");
-        launch_pass_v<0, true, true>(variant_of(c, INV_COLS, set.total), c, set, c->d_itw, ProDst{}, epi, st,
-                                     "k_ntt_inv_cols");
-    } else {
-        auto k = k_ntt<12, 12, 2, true, true, 16, 3, Pro, Epi>;
-        FIDES_LAUNCH("k_ntt_inv_limb", st, k, dim3(1, set.total), dim3(256), set, (const PrimeInfo *)c->d_prime,
-                     (const TwPair *)c->d_itw, pro, epi);
-    }
-    return fides_check_cuda(cudaGetLastError(), "ntt inverse launch");
-}
-
-// one pass of kind `kind` with variant v (for the autotuner)
-void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStream_t st)
-{
-    switch (kind) {
-    case FWD_COLS: launch_pass_v<0, false, false>(v, c, set, c->d_tw, ProSrc{}, EpiLazy{}, st, "k_ntt_tune"); break;
-    case FWD_ROWS: launch_pass_v<1, false, false>(v, c, set, c->d_tw, ProDst{}, EpiCanon{}, st, "k_ntt_tune"); break;
-    case INV_ROWS: launch_pass_v<1, true, false>(v, c, set, c->d_itw, ProPrep{16}, EpiLazy{}, st, "k_ntt_tune"); break;
-    default: launch_pass_v<0, true, true>(v, c, set, c->d_itw, ProDst{}, EpiCanon{}, st, "k_ntt_tune"); break;
-    }
-}
-
-}  // namespace
-
-int ntt_fwd_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { return forward(c, s, ProSrc{}, EpiCanon{}, st); }
-int ntt_fwd_submul(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { return forward(c, s, ProSrc{}, EpiSubMul{}, st); }
+int ntt_fwd_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_fwd_canon, c, s, st) }
+int ntt_fwd_submul(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_fwd_submul, c, s, st) }
 int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 {
-    return forward(c, s, ProSwitchMod{}, EpiSubMul{}, st);
+    FIDES_NTT_DISPATCH(ntt_fwd_switch_submul, c, s, st)
 }
 int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
 {
-    return forward(c, s, ProSrc{}, EpiSubMulRot{c->logN}, st);
+    FIDES_NTT_DISPATCH(ntt_fwd_submul_rot, c, s, st)
 }
-int ntt_fwd_raise(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
+int ntt_fwd_raise(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_fwd_raise, c, s, st) }
+int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_inv_canon, c, s, st) }
+
+namespace {
+void tune_one(const fides_ctx *c, int kind, int v, const LimbSet &s, cudaStream_t st)
 {
-    return forward(c, s, ProRaise{}, EpiCanon{}, st);
+    FIDES_NTT_DISPATCH(ntt_tune_one, c, kind, v, s, st)
 }
-int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
-{
-    return inverse(c, s, ProPrep{c->logN}, EpiCanon{}, st);
-}
+}  // namespace
 
 // Default variants before autotuning: 8 columns per CTA for column passes and
 // 4 rows per CTA for row passes (the choice the autotuner makes on GB300 for
@@ -135,7 +65,7 @@ void ntt_default_variants(fides_ctx *c)
 extern "C" int fides_ctx_autotune(fides_ctx *c, int max_limbs, void *stream)
 {
     if (!c) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_autotune: ctx is NULL");
-    if (c->logN != 16) return FIDES_OK;   // one variant only
+    if (c->logN == 12) return FIDES_OK;   // one variant only
     const int np = c->L + c->K;
     const size_t limbs_avail = c->scratch_words / c->N;
     int maxn = std::min(std::min(max_limbs, FIDES_TUNE_MAX), (int)limbs_avail);
@@ -163,7 +93,7 @@ extern "C" int fides_ctx_autotune(fides_ctx *c, int max_limbs, void *stream)
                 float tmin = 0.f;
                 for (int r = 0; r < 4; ++r) {
                     cudaEventRecord(e0, st);
-                    launch_one(c, kind, v, S, st);
+                    tune_one(c, kind, v, S, st);
                     cudaEventRecord(e1, st);
                     rc = fides_check_cuda(cudaEventSynchronize(e1), "fides_ctx_autotune");
                     if (rc) break;
@@ -188,7 +118,7 @@ extern "C" int fides_ctx_autotune(fides_ctx *c, int max_limbs, void *stream)
 extern "C" int fides_ctx_ntt_tile(const fides_ctx *c, int pass, int n_limbs)
 {
     if (!c || pass < 0 || pass > 3 || n_limbs < 0) return 0;
-    if (c->logN != 16) return (1 << 8) | 3;
+    if (c->logN == 12) return (1 << 8) | 3;
     const int v = variant_of(c, pass, n_limbs);
     return (VAR_CT[v] << 8) | VAR_MINB[v];
 }

@@ -9,16 +9,18 @@
 // Decomposition.  A CTA transforms a tile held in registers (16 elements per
 // thread) and shared memory:
 //   * logN = 12: the whole limb is one tile of 256 threads (KIND 2, one pass);
-//   * logN = 16: two passes as in the paper's hierarchical 2-D NTT -- a column
-//     pass (KIND 0) runs stages 0..7 on CT columns of stride 256, a row pass
-//     (KIND 1) runs stages 8..15 on CT contiguous rows of 256, with 16*CT
-//     threads.  Four global accesses per element, as in the paper.  CT is 16,
-//     8 or 4; narrower tiles split a small launch into more CTAs so its last
-//     wave costs less (the choice per pass and limb count is autotuned, see
+//   * logN = 13..17: two passes as in the paper's hierarchical 2-D NTT -- a
+//     column pass (KIND 0) runs the first S_col stages on CT columns of stride
+//     2^(logN - S_col), a row pass (KIND 1) runs the other S_row stages on CT
+//     contiguous rows (S_col, S_row = 7+6, 7+7, 8+7, 8+8, 9+8 for logN 13..17).
+//     Four global accesses per element, as in the paper.  CT is 16, 8 or 4;
+//     narrower tiles split a small launch into more CTAs so its last wave
+//     costs less (the choice per pass and limb count is autotuned, see
 //     ntt.cu).
 // Inside a pass, stages are grouped four at a time ("rounds"): in a round every
 // thread owns 16 elements whose local indices differ only in the round's four
-// bits, so four radix-2 stages run in registers; rounds exchange data through
+// bits, so four radix-2 stages run in registers (a pass whose stage count is
+// not a multiple of four ends with a partial round, see ntt_round); rounds exchange data through
 // shared memory (k-major for columns, XOR-swizzled rows otherwise, both free
 // of bank conflicts).  Loads and stores are coalesced: where the thread-to-
 // element map of the first/last round is strided, the tile is staged through
@@ -198,16 +200,21 @@ struct EpiSubMulRot {
     }
 };
 
-// One round of four radix-2 stages on the thread's 16 registers.
-// X: the global-index bits above the round (see the header comment);
-// TWS: twiddles come from shared memory (index < 256) instead of global.
-template <bool INV, int S0, int S, int RHO, bool TWS>
+// One round of up to four radix-2 stages on the thread's 16 registers, whose
+// local indices differ in the four bits [B, B+3] (the round's window).  A full
+// round runs the four stages of the window; the last round of a pass whose
+// stage count is not a multiple of four runs only the stages a = A0..3 (its
+// window is the lowest four bits for a forward pass, the highest four for an
+// inverse one, and the window bits an earlier round transformed act as
+// independent lanes).  X: the global-index bits above the window; TWS:
+// twiddles come from shared memory instead of global.
+template <bool INV, int S0, int S, int B, int A0, bool TWS>
 __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__restrict__ tw,
                                           const TwPair *stw, u64 q, u64 q2)
 {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int s = INV ? S0 + S - 1 - 4 * RHO - a : S0 + 4 * RHO + a;
+    for (int a = A0; a < 4; ++a) {
+        const int s = INV ? S0 + S - 1 - B - a : S0 + (S - 4 - B) + a;
         const int h = INV ? (1 << a) : (8 >> a);
         const int base = (1 << s) + (INV ? (X << (3 - a)) : (X << a));
 #pragma unroll
@@ -221,25 +228,44 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__r
     }
 }
 
-// KIND: 0 = column pass (CT strided columns, S = 8, stages 0..7 of logN=16),
-//       1 = row pass (CT rows, S = 8, stages 8..15 of logN=16),
+// Window and first stage of round rho of a pass of S stages (see ntt_round).
+template <int S, bool INV>
+__host__ __device__ constexpr int round_window(int rho)
+{
+    return (rho == (S + 3) / 4 - 1 && S % 4 != 0) ? (INV ? S - 4 : 0) : (INV ? 4 * rho : S - 4 - 4 * rho);
+}
+template <int S>
+__host__ __device__ constexpr int round_first(int rho)
+{
+    return (rho == (S + 3) / 4 - 1 && S % 4 != 0) ? 4 - S % 4 : 0;
+}
+
+// Threads of a tile: 16 elements each.
+template <int S, int KIND, int CT>
+__host__ __device__ constexpr int ntt_threads()
+{
+    return ((KIND == 2 ? 1 : CT) << S) / 16;
+}
+
+// KIND: 0 = column pass (CT strided columns of 2^S elements, stages 0..S-1),
+//       1 = row pass (CT contiguous rows of 2^S elements, stages LOGN-S..LOGN-1),
 //       2 = whole limb (S == LOGN == 12, 256 threads; CT ignored).
 // INV selects Gentleman-Sande stages in reverse order; NINV multiplies by
 // N^-1 before the epilogue.  MINB is the resident-CTA target per SM.
 template <int LOGN, int S, int KIND, bool INV, bool NINV, int CT, int MINB, class Pro, class Epi>
-__global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
+__global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     k_ntt(LimbSet set, const PrimeInfo *__restrict__ P, const TwPair *__restrict__ TW, Pro pro, Epi epi)
 {
     constexpr int C = (KIND == 2) ? 1 : CT;            // sub-transforms per tile
-    constexpr int THREADS = (C << S) / 16;             // 16 elements per thread
-    constexpr int R = S / 4;                           // rounds of four stages
+    constexpr int THREADS = ntt_threads<S, KIND, CT>();
+    constexpr int RT = (1 << S) / 16;                  // threads per sub-transform
+    constexpr int R = (S + 3) / 4;                     // rounds (the last one may be partial)
     constexpr int S0 = (KIND == 1) ? (LOGN - S) : 0;
     constexpr int SH = LOGN - S;                       // column stride shift
     constexpr bool TWS = (KIND == 0);                  // column twiddles staged in shared memory
-    static_assert(S % 4 == 0, "tile shape");
-    static_assert(KIND != 1 || S == 8, "row pass handles rows of 256");
+    static_assert(S >= 5 && R <= 3, "tile shape");
     __shared__ u64 sm[C << S];
-    __shared__ TwPair stw[TWS ? 256 : 1];
+    __shared__ TwPair stw[TWS ? (1 << S) : 1];
 
     pdl_enter();
     const int t = threadIdx.x;
@@ -248,12 +274,12 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
     const TwPair *__restrict__ tw = TW + ((size_t)J.prime << LOGN);
     const u64 q = pr.q, q2 = pr.q2;
     if (TWS) {
-        for (int i = t; i < 256; i += THREADS) stw[i] = tw[i];
+        for (int i = t; i < (1 << S); i += THREADS) stw[i] = tw[i];
     }
 
     int c, u;
     if (KIND == 0) { c = t % C; u = t / C; }
-    else if (KIND == 1) { u = t & 15; c = t >> 4; }
+    else if (KIND == 1) { u = t % RT; c = t / RT; }
     else { u = t; c = 0; }
     const int cbase = (KIND == 2) ? 0 : (int)blockIdx.x * C + c;   // column (KIND 0) or row (KIND 1)
 
@@ -266,8 +292,8 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
         if (KIND == 0) return k * C + cc;
         return cc * (1 << S) + (k ^ ((k >> 4) & 15));
     };
-    // the global-index bits above round rho's four bits
-    auto Xof = [&](int b) -> int { return (KIND == 1 ? (cbase << (4 - b)) : 0) | (u >> b); };
+    // the global-index bits above a round's window of four bits starting at b
+    auto Xof = [&](int b) -> int { return (KIND == 1 ? (cbase << (S - 4 - b)) : 0) | (u >> b); };
 
     u64 x[16];
 
@@ -293,11 +319,11 @@ __global__ void __launch_bounds__(KIND == 2 ? 256 : 16 * CT, MINB)
     // ---------------- rounds ----------------
 #define FIDES_NTT_ROUND(RHO)                                                                 \
     if (RHO < R) {                                                                           \
-        const int b = INV ? 4 * RHO : S - 4 - 4 * RHO;                                       \
+        constexpr int b = round_window<S, INV>(RHO < R ? RHO : 0);                          \
         if (RHO > 0) {                                                                       \
             _Pragma("unroll") for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, b))]; \
         }                                                                                    \
-        ntt_round<INV, S0, S, (RHO < R ? RHO : 0), TWS>(x, Xof(b), tw, stw, q, q2);          \
+        ntt_round<INV, S0, S, b, round_first<S>(RHO < R ? RHO : 0), TWS>(x, Xof(b), tw, stw, q, q2); \
         if (RHO < R - 1) {                                                                   \
             _Pragma("unroll") for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, b))] = x[r]; \
             __syncthreads();                                                                 \

@@ -1,0 +1,4 @@
+// NTT launchers and kernels for logN = 17 (see ntt_impl.cuh).
+#include "ntt_impl.cuh"
+
+FIDES_NTT_DEGREE(17)

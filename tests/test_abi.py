@@ -59,8 +59,9 @@ def _create(L, logN, q, p, dnum):
 def test_ctx_create_rejects_bad_parameters_before_device_work(L):
     q = fides.find_primes(12, 40, 3)
     p = fides.find_primes(12, 50, 1, exclude=q)
-    rc, h = _create(L, 13, q, p, 3)
-    assert rc == -2 and not h.value and b"logN" in L.fides_last_error()
+    for logN in (11, 18):                                         # ring degrees outside 2^12..2^17
+        rc, h = _create(L, logN, q, p, 3)
+        assert rc == -2 and not h.value and b"logN" in L.fides_last_error()
     rc, h = _create(L, 12, q[:2] + [q[2] + 2], p, 3)          # not prime
     assert rc == -6 and not h.value
     rc, h = _create(L, 12, q, [q[0]], 3)                        # repeated prime
