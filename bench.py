@@ -717,6 +717,22 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
     res["hmult_logN12_L3"] = {"us": round(t_small * 1e3, 2), "launches": int(fides.kernel_launches() - l0),
                               "note": "one call at a time; latency bound (each launch covers 3 to 4 limbs of 32 KiB)"}
     sctx.close()
+    # forward + inverse NTT of 32 limbs at every ring degree (butterflies per second)
+    by_degree = {}
+    for logN in range(12, 18):
+        dq = fides.find_primes(logN, 54, 30)
+        dp = fides.find_primes(logN, 60, 2, exclude=dq)
+        dctx = fides.Context(logN, dq, dp, 3)
+        if not args.no_autotune:
+            dctx.autotune(32)
+        n = 32
+        x = fides.to_device(np.concatenate([si.uniform_poly(st2, dq + dp, dctx.N)]))
+        t = timed(lambda: (dctx.ntt(x, 0, n), dctx.intt(x, 0, n)), 20)
+        bfly = 2 * n * (dctx.N // 2) * logN
+        by_degree[logN] = {"us_fwd_inv_32_limbs": round(t * 1e3, 1),
+                           "gbutterfly_per_s": round(bfly / (t / 1e3) / 1e9, 1)}
+        dctx.close()
+    res["ntt_by_degree"] = by_degree
     res["elementwise_note"] = ("device time of the kernel (CUDA events around each launch), L2 flushed before each "
                                "launch; 30-limb operands; bytes = operands read + result written once")
     return res
@@ -830,7 +846,7 @@ def load_traffic(kernel, bytes_per_launch):
     return int(ent["dram_bytes_per_unit"] * bytes_per_launch / ent["algorithmic_bytes_per_unit"])
 
 
-KERNEL_SOURCES = {"k_ntt": ["ntt.cuh", "ntt.cu", "fides_internal.cuh"],
+KERNEL_SOURCES = {"k_ntt": ["ntt.cuh", "ntt_impl.cuh", "ntt_l16.cu", "fides_internal.cuh"],
                   "k_bconv": ["kernels.cuh", "fides_internal.cuh"],
                   "k_inner": ["kernels.cuh", "fides_internal.cuh"]}
 

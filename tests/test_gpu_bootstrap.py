@@ -1,7 +1,7 @@
 """GPU bootstrapping through the program executor: the oracle's program run on
 the device equals the oracle's own run residue for residue (logN=12); the
 library's planned program equals the oracle's execution of the same program
-and refreshes a ciphertext within 2^-12 (logN=12 and logN=16, h = 192)."""
+and refreshes a ciphertext within 2^-12 (logN=12, 15 and 16, h = 192)."""
 import numpy as np
 import pytest
 
@@ -83,18 +83,20 @@ def test_planned_program_matches_oracle_and_decrypts_logN12():
     g.close()
 
 
-def test_bootstrap_logN16_decrypts():
-    """logN=16, 2^15 slots, L=30 (q_0 60-bit, 29 x 54-bit), K=10, dnum=3, h=192."""
+@pytest.mark.parametrize("logN", [15, 16])
+def test_bootstrap_decrypts_at_full_size(logN):
+    """logN=16 (2^15 slots) and logN=15 (2^14 slots), L=30 (q_0 60-bit, 29 x
+    54-bit), K=10, dnum=3, h=192."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    g, o, cl, q = setup(16, si.workload_seed(4) + 3)
+    g, o, cl, q = setup(logN, si.workload_seed(4) + 3)
     prog = bt.plan(g.N, q, 2.0 ** 50)
     hkeys, dkeys = dev_keys(cl, prog.rot_steps)
     z = cl.random_slots()
     ct = cl.encrypt(z, 1, 2.0 ** 50)
     got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)
     err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
-    print("bootstrap logN=16 relative slot error 2^%.2f" % np.log2(err))
+    print("bootstrap logN=%d relative slot error 2^%.2f" % (logN, np.log2(err)))
     assert err < 2.0 ** -12, err
     g.close()
 
