@@ -181,7 +181,7 @@ def workload_inputs(P, q, p, seed):
     return A, B, keys
 
 
-def launch_model(nl, K, alpha, N):
+def launch_model(nl, K, alpha, N, bconv="k_bconv_tc"):
     """Per-step launches of the library's kernels with their algorithmic work.
 
     Unit of an NTT pass: one limb (N u64 read + N written = 16 N bytes,
@@ -208,11 +208,11 @@ def launch_model(nl, K, alpha, N):
         fb, fm = (6 * W * nl, 4 * N * nl) if prep == "tensor" else (3 * W * nl, 0)
         ntt("inv", nl, ninv=True, first_bytes=fb, first_mm=fm)
         ntgt = beta * ne - nl
-        L.append(("k_bconv", W * (nl + ntgt), N * sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta))))
+        L.append((bconv, W * (nl + ntgt), N * sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta))))
         ntt("fwd", ntgt)
         L.append(("k_inner", W * (beta * ne + 2 * beta * ne + 2 * ne), N * 2 * beta * ne))
         ntt("inv", 2 * K, ninv=True)                                 # ModDown: P-limbs to coefficients
-        L.append(("k_bconv", W * (2 * K + 2 * nl), N * 2 * K * nl))
+        L.append((bconv, W * (2 * K + 2 * nl), N * 2 * K * nl))
         extra = W * nl * (2 + mode0 + mode1)                         # aux reads (+ out reads when accumulating)
         ntt("fwd", 2 * nl, extra_bytes=extra, extra_mm=2 * N * nl)
 
@@ -319,7 +319,7 @@ def run_fides(args, world, rank, local):
     # ---------------- roofline of the dominant kernel ----------------
     kern = {k: v for k, v in trace.items() if k.startswith("k_")}
     top = max(kern, key=lambda k: kern[k][1])
-    model = launch_model(nl, P.nk, ctx.alpha, N)
+    model = launch_model(nl, P.nk, ctx.alpha, N, "k_bconv_tc" if ctx.tensor_bconv else "k_bconv")
     per_kernel = {}
     for name, by, mm in model:
         d = per_kernel.setdefault(name, [0, 0, 0])
@@ -847,6 +847,7 @@ def load_traffic(kernel, bytes_per_launch):
 
 
 KERNEL_SOURCES = {"k_ntt": ["ntt.cuh", "ntt_impl.cuh", "ntt_l16.cu", "fides_internal.cuh"],
+                  "k_bconv_tc": ["bconv_tc.cuh", "kernels.cuh", "fides_internal.cuh"],
                   "k_bconv": ["kernels.cuh", "fides_internal.cuh"],
                   "k_inner": ["kernels.cuh", "fides_internal.cuh"]}
 

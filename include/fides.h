@@ -124,6 +124,24 @@ int fides_ctx_ntt_tile(const fides_ctx *ctx, int pass, int n_limbs);
 #define FIDES_TUNE_ENTRIES (4 * 129)
 int fides_ctx_tune_table(fides_ctx *ctx, unsigned char *table, int set);
 
+/*
+ * Device status of the context: kernels never spin without a limit.  A
+ * tensor-core base conversion whose wait for its operand copy or for its
+ * matrix products runs out (about 2 s) sets FIDES_STATUS_WAIT_TIMEOUT, skips
+ * its outputs, frees its tensor memory and returns.  Writes the bits seen
+ * since the last call to *flags (0: none) and clears them.  Synchronises the
+ * device.  Returns FIDES_OK or FIDES_ERR_CUDA.
+ */
+#define FIDES_STATUS_WAIT_TIMEOUT 1
+int fides_ctx_status(fides_ctx *ctx, int *flags);
+
+/*
+ * Whether base conversions of this context run on the tensor cores (1: every
+ * digit and K have at most 16 primes) or on the integer pipes (0).  Results
+ * are identical.
+ */
+int fides_ctx_tensor_bconv(const fides_ctx *ctx);
+
 /* Number of digits in use at n_limbs limbs: ceil(n_limbs / alpha). */
 int fides_ctx_beta(const fides_ctx *ctx, int n_limbs);
 /* psi of prime index i (0..L+K-1), or 0 for a bad index. */

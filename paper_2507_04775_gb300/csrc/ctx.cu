@@ -162,8 +162,26 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_mu_nscale);
     cudaFree(c->d_md_nscale);
     cudaFree(c->d_raise);
+    cudaFree(c->d_tc);
+    cudaFree(c->d_c32);
+    cudaFree(c->d_status);
     cudaFree(c->scratch);
     free(c);
+}
+
+extern "C" int fides_ctx_status(fides_ctx *c, int *flags)
+{
+    if (!c || !flags) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_status: NULL argument");
+    *flags = 0;
+    int rc = fides_check_cuda(cudaDeviceSynchronize(), "fides_ctx_status");
+    if (!rc) rc = fides_check_cuda(cudaMemcpy(flags, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "fides_ctx_status");
+    if (!rc) rc = fides_check_cuda(cudaMemset(c->d_status, 0, sizeof(int)), "fides_ctx_status");
+    return rc;
+}
+
+extern "C" int fides_ctx_tensor_bconv(const fides_ctx *c)
+{
+    return c && c->tc_on == 3 ? 1 : 0;
 }
 
 extern "C" int fides_ctx_beta(const fides_ctx *c, int n_limbs)
@@ -184,6 +202,43 @@ extern "C" uint64_t fides_galois_elt(const fides_ctx *c, int64_t steps)
     int64_t half = c->N / 2;
     int64_t k = ((steps % half) + half) % half;
     return hpow(5, (u64)k, 2 * (u64)c->N);
+}
+
+// fp16 bits of an integer 0 <= k < 256 (exact: at most 8 significant bits).
+static uint16_t f16_of_byte(unsigned k)
+{
+    if (k == 0) return 0;
+    int e = 7;
+    while (!(k >> e)) --e;
+    return (uint16_t)(((e + 15) << 10) | ((k << (10 - e)) & 0x3FF));
+}
+
+// Appends the tensor-core image of one conversion matrix to img (bconv_tc.cuh):
+// for target t (prime targets[t]) and source s (constant cst(s, z)), one 8 x 8
+// core matrix of fp16 values in 16-byte rows, row b, column a = byte b of
+// (cst(s, z) * 2^(8a) mod p_z).  Targets and sources are padded to even counts
+// with zero blocks.  Returns the image's byte offset.
+template <class F>
+static size_t tc_image(const u64 *primes, const std::vector<int> &targets, int ns, F cst,
+                       std::vector<uint16_t> &img)
+{
+    const size_t off = img.size() * 2;
+    const int nd = (int)targets.size(), ndp = (nd + 1) & ~1, nsp = (ns + 1) & ~1;
+    img.resize(img.size() + (size_t)ndp * nsp * 64, 0);
+    uint16_t *base = img.data() + off / 2;
+    for (int t = 0; t < nd; ++t) {
+        const int z = targets[t];
+        const u64 p = primes[z];
+        for (int src = 0; src < ns; ++src) {
+            uint16_t *blk = base + ((size_t)t * nsp + src) * 64;
+            u64 v = cst(src, z) % p;
+            for (int a = 0; a < 8; ++a) {
+                for (int b = 0; b < 8; ++b) blk[b * 8 + a] = f16_of_byte((unsigned)((v >> (8 * b)) & 255));
+                v = (u64)(((u128)v << 8) % p);
+            }
+        }
+    }
+    return off;
 }
 
 // Scratch words one top-level operation needs (layout: keyswitch.cu, plan.cuh).
@@ -301,6 +356,39 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
         md_pinv[i] = pair_of(hinv(P, qi), qi);
     }
 
+    // Tensor-core conversion images: ModUp per (nl, j) with targets in the
+    // order of the job's runs ([0, lo), [hi, nl), P), ModDown with targets
+    // [0, L) (a level nl uses the first nl).
+    std::vector<uint16_t> tc_img;
+    c->tc_on = (alpha <= FIDES_TC_MAX_SRC ? 1 : 0) | (K <= FIDES_TC_MAX_SRC ? 2 : 0);
+    c->tc_big = 1;
+    for (int z = 0; z < np; ++z)
+        if (primes[z] < ((u64)1 << 48)) c->tc_big = 0;
+    if (c->tc_on & 1) {
+        for (int nl = 1; nl <= L; ++nl) {
+            int beta = (nl + alpha - 1) / alpha;
+            for (int j = 0; j < beta; ++j) {
+                int lo = j * alpha, hi = std::min(lo + alpha, nl);
+                size_t off = ((size_t)(nl - 1) * dnum + j) * alpha;
+                std::vector<int> tg;
+                for (int z = 0; z < lo; ++z) tg.push_back(z);
+                for (int z = hi; z < nl; ++z) tg.push_back(z);
+                for (int z = L; z < np; ++z) tg.push_back(z);
+                c->tc_mu_off[nl - 1][j] = tc_image(primes, tg, hi - lo,
+                                                   [&](int src, int z) { return mu_mat[(off + src) * np + z]; },
+                                                   tc_img);
+            }
+        }
+    }
+    if (c->tc_on & 2) {
+        std::vector<int> tg;
+        for (int z = 0; z < L; ++z) tg.push_back(z);
+        c->tc_md_off = tc_image(primes, tg, K, [&](int src, int z) { return md_mat[(size_t)src * np + z]; }, tc_img);
+    }
+    if (tc_img.empty()) tc_img.resize(64, 0);
+    std::vector<TwPair> c32((size_t)np);
+    for (int z = 0; z < np; ++z) c32[z] = pair_of((u64)(((u128)1 << 32) % primes[z]), primes[z]);
+
     // Rescale tables
     std::vector<TwPair> rs((size_t)L * L);
     for (int l = 1; l < L; ++l)
@@ -342,6 +430,12 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     if (!rc) rc = upload(&c->d_mu_nscale, mu_ns, "modup tables");
     if (!rc) rc = upload(&c->d_md_nscale, md_ns, "moddown tables");
     if (!rc) rc = upload(&c->d_raise, raise, "modraise tables");
+    if (!rc) rc = upload(&c->d_tc, tc_img, "tensor-core conversion tables");
+    if (!rc) rc = upload(&c->d_c32, c32, "tensor-core conversion tables");
+    if (!rc) {
+        std::vector<int> zero(1, 0);
+        rc = upload(&c->d_status, zero, "status word");
+    }
     for (int i = 0; i < L; ++i) c->iroot[i] = iroot[i];
     if (!rc) {
         c->scratch_words = scratch_words_for(L, K, dnum, alpha, N);

@@ -30,6 +30,7 @@ typedef uint32_t u32;
 #define FIDES_MAX_SRC 32
 #define FIDES_TUNE_MAX 128   // NTT tile variants are kept per limb count up to this
 #define FIDES_MAC_TERMS 32   // products one plaintext multiply-accumulate launch sums (each < 2^122)
+#define FIDES_TC_MAX_SRC 16  // source primes of a tensor-core base conversion (K extent 8 x 16 = 128)
 
 // A twiddle or constant with its Shoup companion.
 struct __align__(16) TwPair {
@@ -128,6 +129,24 @@ struct fides_ctx {
     // ModRaise: [L] q_0 mod q_i; host copy of i_q = psi_i^(N/2) mod q_i (X^(N/2) in evaluation form)
     TwPair *d_raise;
     TwPair iroot[FIDES_MAX_PRIMES];
+
+    // Base conversion on the tensor cores (bconv_tc.cuh): the conversion
+    // matrix of every ModUp job (nl, digit j) and of ModDown, as fp16 bytes
+    // in the tensor cores' shared-memory operand layout, at byte offsets
+    // tc_mu_off[nl-1][j] and tc_md_off of d_tc.  tc_on bit 0: ModUp images
+    // exist (alpha <= FIDES_TC_MAX_SRC), bit 1: the ModDown image exists
+    // (K <= FIDES_TC_MAX_SRC); without one the integer kernel converts.
+    // d_c32[z] = 2^32 mod prime z with its Shoup companion.
+    uint16_t *d_tc;
+    size_t tc_mu_off[FIDES_MAX_PRIMES][FIDES_MAX_DIGITS];
+    size_t tc_md_off;
+    int tc_on;
+    int tc_big;           // every prime >= 2^48 (the conversion's short epilogue)
+    TwPair *d_c32;
+
+    // Device status word: bits set by kernels whose bounded waits ran out
+    // (FIDES_STATUS_*), read and cleared by fides_ctx_status.
+    int *d_status;
 
     // Scratch pool for one operation at the top level.
     u64 *scratch;
@@ -281,6 +300,23 @@ inline cudaError_t fides_launch_kernel(void (*kern)(Params...), dim3 grid, dim3 
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+template <typename... Params, typename... Args>
+inline cudaError_t fides_launch_kernel_smem(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem,
+                                            cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // Launch a kernel (with programmatic dependent launch): count it and, when
 // tracing is on, bracket it with events.
 #define FIDES_LAUNCH(name, st, kern, grid, block, ...)                  \
@@ -289,6 +325,14 @@ inline cudaError_t fides_launch_kernel(void (*kern)(Params...), dim3 grid, dim3 
         fides_launch_kernel(kern, grid, block, st, __VA_ARGS__);        \
         fides_trace_end(fides_trace_id_, st);                           \
         fides_count_launch();                                           \
+    } while (0)
+
+#define FIDES_LAUNCH_SMEM(name, st, kern, grid, block, smem, ...)            \
+    do {                                                                    \
+        int fides_trace_id_ = fides_trace_begin(name, st);                  \
+        fides_launch_kernel_smem(kern, grid, block, smem, st, __VA_ARGS__); \
+        fides_trace_end(fides_trace_id_, st);                               \
+        fides_count_launch();                                               \
     } while (0)
 
 // Bracket a whole public operation with events when tracing is on.

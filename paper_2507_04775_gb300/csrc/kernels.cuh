@@ -42,11 +42,13 @@ struct BConvJob {
     int ld;
     int nrun;
     BConvRun run[3];
+    const void *tc;          // tensor-core image of the conversion matrix (bconv_tc.cuh), or null
 };
 
 // Jobs inline (djob == nullptr) or in device memory (djob[0..njob)).
 struct BConvArgs {
     int njob;
+    int tc;                  // 1: every job has a tensor-core image (k_bconv_tc)
     const BConvJob *djob;
     BConvJob job[FIDES_MAX_DIGITS];
 };
@@ -193,9 +195,17 @@ void launch_bconv_ns(const fides_ctx *c, const BConvArgs &A, int max_dst, cudaSt
     FIDES_LAUNCH("k_bconv", st, k_bconv<NS>, grid, block, A, c->d_prime, c->logN, tg);
 }
 
-// One launch for jobs that all have `ns` source limbs (inline or device jobs).
+}  // namespace
+
+#include "bconv_tc.cuh"
+
+namespace {
+
+// One launch for jobs that all have `ns` source limbs (inline or device jobs);
+// tensor-core jobs (G.tc) may mix source counts up to ns.
 inline int launch_bconv_group(const fides_ctx *c, const BConvArgs &G, int ns, int max_dst, cudaStream_t st)
 {
+    if (G.tc) return launch_bconv_tc(c, G, ns, max_dst, st);
     switch (ns) {
     case 1: launch_bconv_ns<1>(c, G, max_dst, st); break;
     case 2: launch_bconv_ns<2>(c, G, max_dst, st); break;
@@ -221,23 +231,29 @@ inline int bconv_targets(const BConvJob &j)
     return nd;
 }
 
-// Launches one conversion per distinct source count of inline jobs (a ragged
-// last digit gets its own launch, so every launch runs fully unrolled loops).
+// Launch group of a job: every job with a tensor-core image goes to one
+// k_bconv_tc launch (-1); the integer kernel gets one launch per distinct
+// source count (a ragged last digit gets its own, so every launch runs fully
+// unrolled loops).
+inline int bconv_group_key(const BConvJob &j) { return j.tc ? -1 : j.n_src; }
+
 inline int launch_bconv(const fides_ctx *c, const BConvArgs &A, cudaStream_t st)
 {
     if (A.njob == 0) return FIDES_OK;
     bool done[FIDES_MAX_DIGITS] = {false};
     for (int j = 0; j < A.njob; ++j) {
         if (done[j]) continue;
-        const int ns = A.job[j].n_src;
+        const int key = bconv_group_key(A.job[j]);
         BConvArgs G;
         memset(&G, 0, sizeof(G));
-        int max_dst = 0;
+        G.tc = key < 0;
+        int max_dst = 0, ns = 0;
         for (int k = j; k < A.njob; ++k) {
-            if (done[k] || A.job[k].n_src != ns) continue;
+            if (done[k] || bconv_group_key(A.job[k]) != key) continue;
             done[k] = true;
             G.job[G.njob++] = A.job[k];
             max_dst = std::max(max_dst, bconv_targets(A.job[k]));
+            ns = std::max(ns, A.job[k].n_src);
         }
         if (int rc = launch_bconv_group(c, G, ns, max_dst, st)) return rc;
     }

@@ -66,25 +66,29 @@ void plan_ntt(Plan &P, LaunchKind kind, const std::vector<Seg> &segs)
     P.pend.push_back(Pending{id, 1, P.add(pre.data(), sizeof(int) * pre.size())});
 }
 
-// One launch per distinct source count (the conversion kernel is templated on it).
+// One launch for the tensor-core jobs, one per distinct source count of the
+// others (the integer conversion kernel is templated on it).
 void plan_bconv(Plan &P, const std::vector<BConvJob> &jobs)
 {
     std::vector<bool> done(jobs.size(), false);
     for (size_t j = 0; j < jobs.size(); ++j) {
         if (done[j]) continue;
+        const int key = bconv_group_key(jobs[j]);
         std::vector<BConvJob> g;
-        int max_dst = 0;
+        int max_dst = 0, ns = 0;
         for (size_t k = j; k < jobs.size(); ++k) {
-            if (done[k] || jobs[k].n_src != jobs[j].n_src) continue;
+            if (done[k] || bconv_group_key(jobs[k]) != key) continue;
             done[k] = true;
             g.push_back(jobs[k]);
             max_dst = std::max(max_dst, bconv_targets(jobs[k]));
+            ns = std::max(ns, jobs[k].n_src);
         }
         Launch l;
         memset(&l, 0, sizeof(l));
         l.kind = L_BCONV;
         l.bc.njob = (int)g.size();
-        l.ns = jobs[j].n_src;
+        l.bc.tc = key < 0;
+        l.ns = ns;
         l.max_dst = max_dst;
         P.launches.push_back(l);
         P.pend.push_back(Pending{(int)P.launches.size() - 1, 2, P.add(g.data(), sizeof(BConvJob) * g.size())});

@@ -92,6 +92,7 @@ inline void ks_modup_jobs(const fides_ctx *c, const KsBuffers &B, std::vector<BC
         J.scale = c->d_mu_scale + off;
         J.mat = c->d_mu_mat + off * (L + K);
         J.ld = L + K;
+        if (c->tc_on & 1) J.tc = (const unsigned char *)c->d_tc + c->tc_mu_off[nl - 1][j];
         if (lo > 0) J.run[J.nrun++] = BConvRun{e, lo, 0};
         if (hi < nl) J.run[J.nrun++] = BConvRun{e + (size_t)hi * N, nl - hi, hi};
         J.run[J.nrun++] = BConvRun{e + (size_t)nl * N, K, L};
@@ -147,6 +148,7 @@ inline void ks_moddown_jobs(const fides_ctx *c, const KsBuffers &B, std::vector<
         J.ld = c->L + c->K;
         J.nrun = 1;
         J.run[0] = BConvRun{B.conv + (size_t)t * B.nl * N, B.nl, 0};
+        if (c->tc_on & 2) J.tc = (const unsigned char *)c->d_tc + c->tc_md_off;
         v.push_back(J);
     }
 }

@@ -36,10 +36,12 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_now_ns", "fides_hsquare", "fides_conjugate", "fides_rotate_hoisted", "fides_hadd", "fides_hsub",
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
-           "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table"]
+           "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
+           "fides_ctx_status", "fides_ctx_tensor_bconv"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
+STATUS_WAIT_TIMEOUT = 1      # fides_ctx_status bit: a bounded device wait ran out
 
 
 class FidesError(RuntimeError):
@@ -148,6 +150,8 @@ def lib():
         L.fides_trace_read.argtypes = [ctypes.POINTER(fides_trace_stat), _i, ctypes.POINTER(_i)]
         L.fides_kernel_launches.restype = ctypes.c_uint64
         L.fides_ctx_autotune.argtypes = [_vp, _i, _vp]
+        L.fides_ctx_status.argtypes = [_vp, ctypes.POINTER(_i)]
+        L.fides_ctx_tensor_bconv.argtypes = [_vp]
         L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
         L.fides_batch_create.argtypes = [_vp, ctypes.POINTER(fides_op), _i, ctypes.POINTER(_vp)]
         L.fides_batch_run.argtypes = [_vp, _vp]
@@ -297,6 +301,18 @@ class Context:
     # -- structure ---------------------------------------------------------
     def beta(self, n_limbs: int) -> int:
         return lib().fides_ctx_beta(self._h, n_limbs)
+
+    def status(self) -> int:
+        """Device status bits since the last call (STATUS_WAIT_TIMEOUT: a
+        bounded wait of a tensor-core conversion ran out); clears them."""
+        f = _i(0)
+        _check(lib().fides_ctx_status(self._h, ctypes.byref(f)))
+        return f.value
+
+    @property
+    def tensor_bconv(self) -> bool:
+        """Whether base conversions run on the tensor cores."""
+        return bool(lib().fides_ctx_tensor_bconv(self._h))
 
     def psi(self, i: int) -> int:
         return int(lib().fides_ctx_psi(self._h, i))

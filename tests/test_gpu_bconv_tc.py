@@ -1,0 +1,117 @@
+"""Base conversion on the tensor cores (Eq. 1 as an exact byte-matrix product,
+bf16 x bf16 -> fp32): residue for residue against the oracle on extreme
+inputs, on contexts where only one of ModUp / ModDown has tensor-core images
+(the other converts on the integer kernel), and with the device status word
+left clear.  The standard parameter sets (SMALL, MID, FULL, WIDE) run every
+conversion on the tensor cores; their ModUp / ModDown / key-switching parity
+at every level is in test_gpu_parity."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2507_04775_gb300 import Context, find_primes, to_device, to_host  # noqa: E402
+
+
+def contexts(logN, nq, nk, dnum, q_bits=54, p_bits=60):
+    q = find_primes(logN, q_bits, nq)
+    p = find_primes(logN, p_bits, nk, exclude=q)
+    return Context(logN, q, p, dnum), oracle.Context(logN, q, p, dnum)
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def check_modup_moddown(g, o, d_host, x_host, nl, what):
+    beta = g.beta(nl)
+    ext = torch.zeros(beta * (nl + o.nk) * o.N, dtype=torch.int64, device="cuda")
+    g.modup(to_device(d_host), nl, ext)
+    out = torch.zeros(nl * o.N, dtype=torch.int64, device="cuda")
+    g.moddown(to_device(x_host), nl, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(ext).reshape(beta, nl + o.nk, o.N), o.modup(d_host)), "modup, %s, nl=%d" % (what, nl)
+    assert np.array_equal(to_host(out).reshape(nl, o.N), o.moddown(x_host)), "moddown, %s, nl=%d" % (what, nl)
+
+
+@pytest.mark.parametrize("name", ["SMALL", "MID", "FULL", "WIDE"])
+def test_standard_sets_convert_on_tensor_cores(name):
+    need_gpu()
+    P = getattr(si, name)
+    q = find_primes(P.logN, P.q_bits, P.nq)
+    p = find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    g = Context(P.logN, q, p, P.dnum)
+    assert g.tensor_bconv
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["SMALL", "MID", "WIDE"])
+def test_extreme_residues(name):
+    """Every residue q_i - 1 (the largest bytes a residue has), every residue
+    0, and alternating rows: the largest partial sums of the byte product."""
+    need_gpu()
+    P = getattr(si, name)
+    g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
+    for nl in sorted({P.nq, max(1, P.nq - 1)}):
+        top = np.stack([np.full(o.N, qi - 1, dtype=np.uint64) for qi in o.q[:nl]])
+        topx = np.stack([np.full(o.N, qi - 1, dtype=np.uint64) for qi in o.q[:nl] + o.p])
+        check_modup_moddown(g, o, top, topx, nl, "q - 1")
+        check_modup_moddown(g, o, np.zeros_like(top), np.zeros_like(topx), nl, "zero")
+        alt = top.copy()
+        alt[:, 1::2] = 0
+        altx = topx.copy()
+        altx[:, ::2] = 0
+        check_modup_moddown(g, o, alt, altx, nl, "alternating")
+    assert g.status() == 0
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(34, 3, 2), (20, 17, 2)], ids=["modup-integer", "moddown-integer"])
+def test_one_conversion_on_the_integer_kernel(shape):
+    """(L, K, dnum) = (34, 3, 2): digits of 17 primes, ModUp on the integer
+    kernel, ModDown (K = 3) on the tensor cores; (20, 17, 2): the reverse."""
+    need_gpu()
+    nq, nk, dnum = shape
+    g, o = contexts(12, nq, nk, dnum)
+    assert not g.tensor_bconv
+    st = si.Stream(1500 + nq, 1)
+    rlk = np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
+    drlk = to_device(rlk)
+    for nl in (nq, nq - 5):
+        d = si.uniform_poly(st, o.q[:nl], o.N)
+        x = si.uniform_poly(st, o.q[:nl] + o.p, o.N)
+        check_modup_moddown(g, o, d, x, nl, "random")
+        a = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+        b = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+        m = torch.empty(2 * nl * o.N, dtype=torch.int64, device="cuda")
+        g.hmult(to_device(a), to_device(b), nl, drlk, m)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(m).reshape(a.shape), o.hmult(a, b, rlk)), nl
+    assert g.status() == 0
+    g.close()
+
+
+def test_full_size_ragged_levels_and_status():
+    """logN=16, 30 limbs, K=10, dnum=3: HMult at a level whose last digit has
+    one prime (nl = 21) and at one with an odd target count (nl = 28), then
+    the status word."""
+    need_gpu()
+    P = si.FULL
+    g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
+    st = si.Stream(1510, 2)
+    rlk = np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
+    drlk = to_device(rlk)
+    for nl in (21, 28):
+        a = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+        b = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
+        m = torch.empty(2 * nl * o.N, dtype=torch.int64, device="cuda")
+        g.hmult(to_device(a), to_device(b), nl, drlk, m)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(m).reshape(a.shape), o.hmult(a, b, rlk)), nl
+    assert g.status() == 0
+    g.close()
