@@ -9,8 +9,8 @@
 //   D[n][8t + b] = sum_{s,a} x_{s,a}[n] e_{s,t,a,b},
 // the product of a [coefficients x 8 ns] byte matrix with a [8 ns x 8 nd] byte
 // matrix.  Bytes are exact in fp16 and every partial sum is an integer below
-// 8 * 16 * 255^2 < 2^23, exact in the fp32 accumulator whatever the order of
-// the additions, so the MMA gives D exactly.  The epilogue folds the eight
+// 8 * 16 * 255^2 < 2^23 (2^24 with the offset below), exact in the fp32
+// accumulator whatever the order of the additions, so the MMA gives D exactly.  The epilogue folds the eight
 // sums of a target into a value below 2^80 and reduces it mod p_t.  The
 // result equals the integer kernel's (both are canonical residues).
 //
@@ -29,7 +29,10 @@
 // Operand layout (K-major, no swizzle): 8-row x 16-byte core matrices, row r
 // of a core matrix at +16 r; core matrices adjacent along K (one source: its
 // eight bytes) 128 bytes apart (leading byte offset), adjacent 8-row groups
-// 128 nsp bytes apart (stride byte offset), nsp = ns rounded up to even.
+// 128 nsp bytes apart (stride byte offset); nsp = ns + 1 rounded up to even:
+// after the sources, an offset column (A = 256, B = 2^15 for every output byte,
+// both exact) starts every accumulator at 2^23, so that its fp32 bits read
+// 0x4B000000 + D with no conversion.
 //
 // Every wait is bounded (about 2 s of %globaltimer): on a timeout the CTA sets
 // FIDES_STATUS_WAIT_TIMEOUT in the context's status word, skips its outputs,
@@ -178,8 +181,8 @@ struct TcTarget {
 };
 
 // sum_b 2^(8b) D_b mod p, in [0, 4p) (the forward NTT's input range), from
-// the fp32 bits of D_0..D_7 (integers < 2^23).  With f = bits(D + 2^23) =
-// 0x4B000000 + D, w'_k = 2^8 f_2k+1 + f_2k = D_2k + 2^8 D_2k+1 + 0x4B000000
+// the accumulators f_b = bits(2^23 + D_b) = 0x4B000000 + D_b (the offset
+// column adds 2^23 to every sum; D_b < 2^23).  w'_k = 2^8 f_2k+1 + f_2k = D_2k + 2^8 D_2k+1 + 0x4B000000
 // (mod 2^32; the exponent bits of f_2k+1 shift out of the word, and the sum
 // stays below 2^32); value = lo + 2^32 hi with lo, hi < 2^47.01.
 // BIG (every target prime >= 2^48): 2^32 mod p = 2^32, and the Shoup quotient
@@ -192,11 +195,7 @@ __device__ __forceinline__ u64 tc_reduce(const u32 *r, const TcTarget &T, const 
 {
     u32 w[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const u32 f0 = __float_as_uint(__uint_as_float(r[2 * k]) + 8388608.0f);
-        const u32 f1 = __float_as_uint(__uint_as_float(r[2 * k + 1]) + 8388608.0f);
-        w[k] = f1 * 256u + f0;
-    }
+    for (int k = 0; k < 4; ++k) w[k] = r[2 * k + 1] * 256u + r[2 * k];
     constexpr u64 OFF = 0x4B000000ull * (1 + (1ull << 16));
     const u64 lo = (u64)w[0] + ((u64)w[1] << 16) - OFF;
     const u64 hi = (u64)w[2] + ((u64)w[3] << 16) - OFF;
@@ -224,12 +223,13 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) u64 bar[2];
     __shared__ u32 tslot;
+    __shared__ int sok;
     __shared__ TcTarget stg[FIDES_MAX_PRIMES];
     __shared__ PrimeInfo sp[BIG ? 1 : FIDES_MAX_PRIMES];
 
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int N = 1 << logN, ntiles = N / TC_M;
-    const int ns = B.n_src, nsp = (ns + 1) & ~1;
+    const int ns = B.n_src, nsp = (ns + 2) & ~1;   // sources and the offset column, even
     int nd = 0;
     for (int r = 0; r < B.nrun; ++r) nd += B.run[r].count;
     const int ndp = (nd + 1) & ~1;
@@ -275,14 +275,25 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
             xr[k] = s < ns ? B.src[(size_t)s * N + (size_t)tile * TC_M + m] : 0;
         }
     }
-    tc_fence_before();
-    bool ok = __syncthreads_and(mbar_wait(bar0, 0));
-    tc_fence_after();
-    const u32 tm = tslot;
-    if (!ok) {
-        if (t == 0) atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
-        mbar_wait(bar0, 0);   // the copy may still be in flight
+    // constant columns of A: the offset column (fp16 256 in element 0 of row
+    // m; the image holds 2^15 there for every output byte) and a zero column
+    if (t < TC_M) {
+        *(uint4 *)(arow + ns * 128) = make_uint4(0x5C00u, 0, 0, 0);
+        if (ns + 1 < nsp) *(uint4 *)(arow + (ns + 1) * 128) = make_uint4(0, 0, 0, 0);
     }
+    // one thread polls each mbarrier; the others wait at the CTA barrier
+    if (t == 0) {
+        sok = mbar_wait(bar0, 0);
+        if (!sok) {
+            atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
+            mbar_wait(bar0, 0);   // the copy may still be in flight
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    bool ok = sok != 0;
+    const u32 tm = tslot;
 
     const u32 a0 = smem_addr(sA), b0 = smem_addr(sB), sbo = (u32)nsp * 128;
     const int q4 = w & 3, grp = w >> 2;
@@ -291,7 +302,7 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             const int s = s0 + k * (TC_THREADS / TC_M);
-            if (s < nsp) *(uint4 *)(arow + s * 128) = s < ns ? bytes_f16(xr[k]) : make_uint4(0, 0, 0, 0);
+            if (s < ns) *(uint4 *)(arow + s * 128) = bytes_f16(xr[k]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
@@ -313,12 +324,15 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
                 xr[k] = s < ns ? B.src[(size_t)s * N + (size_t)next * TC_M + m] : 0;
             }
         }
-        ok = __syncthreads_and(mbar_wait(bar1, phase));
-        tc_fence_after();
-        if (!ok) {
-            if (t == 0) atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
-            break;
+        if (t == 0) {
+            sok = mbar_wait(bar1, phase);
+            if (!sok) atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
         }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        ok = sok != 0;
+        if (!ok) break;
         const size_t n = (size_t)tile * TC_M + 32 * q4 + lane;
         const u32 lanes = (u32)(32 * q4) << 16;
         for (int pr = grp; 2 * pr < nd; pr += GROUPS) {   // targets 2 pr, 2 pr + 1
@@ -360,6 +374,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_bconv_tc(BConvArgs A, const P
 // dynamic shared memory is raised so that no more fit: a CTA beyond that would
 // wait in its allocation) and two by registers.  The CTAs of a job take its
 // N / 128 tiles round robin.
+// Dynamic shared memory of one job: A operand and matrix image.
+inline int bconv_tc_smem(const BConvJob &j)
+{
+    int nd = 0;
+    for (int r = 0; r < j.nrun; ++r) nd += j.run[r].count;
+    const int nsp = (j.n_src + 2) & ~1, ndp = (nd + 1) & ~1;
+    return 2048 * nsp + 128 * ndp * nsp;
+}
+
 template <bool BIG>
 inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st)
 {
@@ -371,11 +394,14 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
         static_smem = (int)fa.sharedSizeBytes;
         cudaFuncSetAttribute(k_bconv_tc<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - static_smem);
     }
-    const int nsp = (max_ns + 1) & ~1, ndp = (max_dst + 1) & ~1;
+    (void)max_ns;
+    const int ndp = (max_dst + 1) & ~1;
     u32 ncols = 32;
     while (ncols < (u32)(8 * ndp)) ncols <<= 1;
     const int cap = std::min(2, (int)(512 / ncols));          // resident CTAs per SM
-    const size_t need = 2048 * (size_t)nsp + 128 * (size_t)ndp * nsp;
+    const size_t need = (size_t)G.tc_smem;
+    if (need + static_smem > 227 * 1024)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "bconv tc: %zu bytes of shared memory", need);
     const size_t sm_bytes = 228 * 1024, per_cta = sm_bytes / (cap + 1) + 1;   // cap + 1 CTAs must not fit
     size_t smem = std::max(need, per_cta > (size_t)static_smem + 1024 ? per_cta - static_smem - 1024 : 0);
     smem = (smem + 127) & ~(size_t)127;

@@ -216,14 +216,16 @@ static uint16_t f16_of_byte(unsigned k)
 // Appends the tensor-core image of one conversion matrix to img (bconv_tc.cuh):
 // for target t (prime targets[t]) and source s (constant cst(s, z)), one 8 x 8
 // core matrix of fp16 values in 16-byte rows, row b, column a = byte b of
-// (cst(s, z) * 2^(8a) mod p_z).  Targets and sources are padded to even counts
-// with zero blocks.  Returns the image's byte offset.
+// (cst(s, z) * 2^(8a) mod p_z); then, per target, the offset block (2^15 in
+// column 0 of every row, zeros elsewhere).  Targets are padded to an even count,
+// and sources plus the offset block to an even count, with zero blocks.
+// Returns the image's byte offset.
 template <class F>
 static size_t tc_image(const u64 *primes, const std::vector<int> &targets, int ns, F cst,
                        std::vector<uint16_t> &img)
 {
     const size_t off = img.size() * 2;
-    const int nd = (int)targets.size(), ndp = (nd + 1) & ~1, nsp = (ns + 1) & ~1;
+    const int nd = (int)targets.size(), ndp = (nd + 1) & ~1, nsp = (ns + 2) & ~1;
     img.resize(img.size() + (size_t)ndp * nsp * 64, 0);
     uint16_t *base = img.data() + off / 2;
     for (int t = 0; t < nd; ++t) {
@@ -237,6 +239,9 @@ static size_t tc_image(const u64 *primes, const std::vector<int> &targets, int n
                 v = (u64)(((u128)v << 8) % p);
             }
         }
+        // offset column: 2^15 (fp16 0x7800) against A's 256 adds 2^23 to every sum
+        uint16_t *blk = base + ((size_t)t * nsp + ns) * 64;
+        for (int b = 0; b < 8; ++b) blk[b * 8] = 0x7800;
     }
     return off;
 }

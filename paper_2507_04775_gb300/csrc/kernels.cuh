@@ -49,6 +49,7 @@ struct BConvJob {
 struct BConvArgs {
     int njob;
     int tc;                  // 1: every job has a tensor-core image (k_bconv_tc)
+    int tc_smem;             // k_bconv_tc: dynamic shared memory of the largest job (bconv_tc_smem)
     const BConvJob *djob;
     BConvJob job[FIDES_MAX_DIGITS];
 };
@@ -255,6 +256,8 @@ inline int launch_bconv(const fides_ctx *c, const BConvArgs &A, cudaStream_t st)
             max_dst = std::max(max_dst, bconv_targets(A.job[k]));
             ns = std::max(ns, A.job[k].n_src);
         }
+        if (G.tc)
+            for (int k = 0; k < G.njob; ++k) G.tc_smem = std::max(G.tc_smem, bconv_tc_smem(G.job[k]));
         if (int rc = launch_bconv_group(c, G, ns, max_dst, st)) return rc;
     }
     return FIDES_OK;

@@ -88,6 +88,8 @@ void plan_bconv(Plan &P, const std::vector<BConvJob> &jobs)
         l.kind = L_BCONV;
         l.bc.njob = (int)g.size();
         l.bc.tc = key < 0;
+        if (l.bc.tc)
+            for (const BConvJob &x : g) l.bc.tc_smem = std::max(l.bc.tc_smem, bconv_tc_smem(x));
         l.ns = ns;
         l.max_dst = max_dst;
         P.launches.push_back(l);
