@@ -197,14 +197,45 @@ __device__ __forceinline__ u64 tc_reduce(const u32 *r, const TcTarget &T, const 
 #pragma unroll
     for (int k = 0; k < 4; ++k) w[k] = r[2 * k + 1] * 256u + r[2 * k];
     constexpr u64 OFF = 0x4B000000ull * (1 + (1ull << 16));
-    const u64 lo = (u64)w[0] + ((u64)w[1] << 16) - OFF;
-    const u64 hi = (u64)w[2] + ((u64)w[3] << 16) - OFF;
     if constexpr (BIG) {
-        const u32 h0 = (u32)hi, h1 = (u32)(hi >> 32), v0 = (u32)T.wp, v1 = (u32)(T.wp >> 32);
-        const u64 mid = (u64)h1 * v0 + (u64)h0 * v1;            // < 2^49
-        const u32 qh = h1 * v1 + (u32)(mid >> 32);              // floor(hi wp / 2^64) or one less
-        return ((u64)h0 << 32) - (u64)qh * T.p + lo;
+        // 32-bit limbs: lo = (l1, l0), hi = (h1, h0), wp = (v1, v0), p = (p1, p0)
+        u32 l0, l1, h0, h1, m0, m1, q, x0, x1;
+        const u32 v0 = (u32)T.wp, v1 = (u32)(T.wp >> 32), p0 = (u32)T.p, p1 = (u32)(T.p >> 32);
+        asm("{\n\t.reg .u32 s;\n\t"
+            // lo = w0 + 2^16 w1 - OFF, hi = w2 + 2^16 w3 - OFF
+            "shl.b32 s, %10, 16;\n\t"
+            "add.cc.u32 %0, %9, s;\n\t"
+            "shr.u32 s, %10, 16;\n\t"
+            "addc.u32 %1, s, 0;\n\t"
+            "sub.cc.u32 %0, %0, 0x4B000000;\n\t"
+            "subc.u32 %1, %1, 0x4B00;\n\t"
+            "shl.b32 s, %12, 16;\n\t"
+            "add.cc.u32 %2, %11, s;\n\t"
+            "shr.u32 s, %12, 16;\n\t"
+            "addc.u32 %3, s, 0;\n\t"
+            "sub.cc.u32 %2, %2, 0x4B000000;\n\t"
+            "subc.u32 %3, %3, 0x4B00;\n\t"
+            // mid = h1 v0 + h0 v1 (< 2^49); q = h1 v1 + mid / 2^32
+            "mul.lo.u32 %4, %3, %13;\n\t"
+            "mul.hi.u32 %5, %3, %13;\n\t"
+            "mad.lo.cc.u32 %4, %2, %14, %4;\n\t"
+            "madc.hi.u32 %5, %2, %14, %5;\n\t"
+            "mad.lo.u32 %6, %3, %14, %5;\n\t"
+            // x = lo + 2^32 h0 - q p (mod 2^64)
+            "mul.lo.u32 s, %6, %15;\n\t"
+            "sub.cc.u32 %7, %0, s;\n\t"
+            "mul.hi.u32 s, %6, %15;\n\t"
+            "add.u32 %8, %1, %2;\n\t"
+            "subc.u32 %8, %8, s;\n\t"
+            "mul.lo.u32 s, %6, %16;\n\t"
+            "sub.u32 %8, %8, s;\n\t"
+            "}"
+            : "=&r"(l0), "=&r"(l1), "=&r"(h0), "=&r"(h1), "=&r"(m0), "=&r"(m1), "=&r"(q), "=&r"(x0), "=&r"(x1)
+            : "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(v0), "r"(v1), "r"(p0), "r"(p1));
+        return ((u64)x1 << 32) | x0;
     } else {
+        const u64 lo = (u64)w[0] + ((u64)w[1] << 16) - OFF;
+        const u64 hi = (u64)w[2] + ((u64)w[3] << 16) - OFF;
         const u64 x = hi * T.w - mulhi64(hi, T.wp) * T.p;       // [0, 2p)
         return x + reduce64_lazy(lo, P);                        // < 4p
     }
@@ -346,9 +377,7 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
                 T1.dst[n] = tc_reduce<BIG>(r + 8, T1, sp[BIG ? 0 : t0 + 1]);
             }
         }
-        tc_fence_before();
-        __syncthreads();   // accumulator and A operand free for the next tile
-        tc_fence_after();
+        tc_fence_before();   // the next tile's MMAs follow its conversion barrier
     }
     tc_fence_before();
     __syncthreads();
