@@ -136,6 +136,14 @@ int fides_ctx_tune_table(fides_ctx *ctx, unsigned char *table, int set);
 int fides_ctx_status(fides_ctx *ctx, int *flags);
 
 /*
+ * Self-test of the bounded device waits: launches one thread that waits on an
+ * mbarrier nothing arrives on, for limit_us (1..100000) microseconds, then
+ * sets FIDES_STATUS_WAIT_TIMEOUT in the context's status word and returns.
+ * The context stays usable.  Asynchronous on `stream`.
+ */
+int fides_ctx_selftest_wait(fides_ctx *ctx, int limit_us, void *stream);
+
+/*
  * Whether base conversions of this context run on the tensor cores (1: every
  * digit and K have at most 16 primes) or on the integer pipes (0).  Results
  * are identical.

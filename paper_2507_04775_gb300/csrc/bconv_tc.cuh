@@ -85,14 +85,15 @@ __device__ __forceinline__ u64 global_ns()
     return t;
 }
 
-// true once the phase of `parity` has completed; false after about 2 s
-__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
+// true once the phase of `parity` has completed; false after `limit_ns`
+// (about 2 s by default) or 2^26 polls
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity, u64 limit_ns = 2000000000ull)
 {
     if (mbar_test(bar, parity)) return true;
     const u64 t0 = global_ns();
     for (u32 it = 1; it < (1u << 26); ++it) {
         if (mbar_test(bar, parity)) return true;
-        if ((it & 255) == 0 && global_ns() - t0 > 2000000000ull) return false;
+        if ((it & 255) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -109,6 +109,30 @@ static int ntt_entry(fides_ctx *c, uint64_t *dev, int first_prime, int n_limbs, 
     return FIDES_OK;
 }
 
+namespace {
+
+// A wait that runs out: one thread waits on an mbarrier that nothing arrives
+// on, with the given limit, and reports the timeout the way the tensor-core
+// conversion does.
+__global__ void k_wait_selftest(u64 limit_ns, int *status)
+{
+    __shared__ __align__(8) u64 bar;
+    const u32 b = smem_addr(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(b, 0, limit_ns)) atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" int fides_ctx_selftest_wait(fides_ctx *c, int limit_us, void *stream)
+{
+    if (!c || limit_us < 1 || limit_us > 100000)
+        return fides_set_error(FIDES_ERR_ARG, "fides_ctx_selftest_wait: limit_us must be 1..100000");
+    k_wait_selftest<<<1, 1, 0, (cudaStream_t)stream>>>((u64)limit_us * 1000, c->d_status);
+    return fides_check_cuda(cudaGetLastError(), "fides_ctx_selftest_wait");
+}
+
 extern "C" int fides_ntt(fides_ctx *c, uint64_t *dev, int first_prime, int n_limbs, int batch, void *stream)
 {
     return ntt_entry(c, dev, first_prime, n_limbs, batch, stream, false);

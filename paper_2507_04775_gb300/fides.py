@@ -37,7 +37,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
            "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
-           "fides_ctx_status", "fides_ctx_tensor_bconv"]
+           "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -152,6 +152,7 @@ def lib():
         L.fides_ctx_autotune.argtypes = [_vp, _i, _vp]
         L.fides_ctx_status.argtypes = [_vp, ctypes.POINTER(_i)]
         L.fides_ctx_tensor_bconv.argtypes = [_vp]
+        L.fides_ctx_selftest_wait.argtypes = [_vp, _i, _vp]
         L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
         L.fides_batch_create.argtypes = [_vp, ctypes.POINTER(fides_op), _i, ctypes.POINTER(_vp)]
         L.fides_batch_run.argtypes = [_vp, _vp]
@@ -308,6 +309,11 @@ class Context:
         f = _i(0)
         _check(lib().fides_ctx_status(self._h, ctypes.byref(f)))
         return f.value
+
+    def selftest_wait(self, limit_us: int = 1000, stream=None):
+        """Runs a device wait that nothing completes, limited to limit_us; it
+        sets STATUS_WAIT_TIMEOUT in the status word (see status())."""
+        _check(lib().fides_ctx_selftest_wait(self._h, limit_us, _stream(stream)))
 
     @property
     def tensor_bconv(self) -> bool:

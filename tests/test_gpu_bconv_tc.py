@@ -1,10 +1,10 @@
 """Base conversion on the tensor cores (Eq. 1 as an exact byte-matrix product,
-bf16 x bf16 -> fp32): residue for residue against the oracle on extreme
+fp16 x fp16 -> fp32): residue for residue against the oracle on extreme
 inputs, on contexts where only one of ModUp / ModDown has tensor-core images
-(the other converts on the integer kernel), and with the device status word
-left clear.  The standard parameter sets (SMALL, MID, FULL, WIDE) run every
-conversion on the tensor cores; their ModUp / ModDown / key-switching parity
-at every level is in test_gpu_parity."""
+(the other converts on the integer kernel), with the device status word left
+clear, and a bounded device wait that runs out.  The standard parameter sets
+(SMALL, MID, FULL, WIDE) run every conversion on the tensor cores; their
+ModUp / ModDown / key-switching parity at every level is in test_gpu_parity."""
 import numpy as np
 import pytest
 
@@ -113,5 +113,24 @@ def test_full_size_ragged_levels_and_status():
         g.hmult(to_device(a), to_device(b), nl, drlk, m)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(m).reshape(a.shape), o.hmult(a, b, rlk)), nl
+    assert g.status() == 0
+    g.close()
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_context_stays_usable():
+    """The bounded-wait machinery of the tensor-core conversion: a device wait
+    that nothing completes gives up after its limit (1 ms here), sets the
+    status bit, and the context then runs a key switch bit-exactly."""
+    need_gpu()
+    P = si.MID
+    g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
+    assert g.status() == 0
+    g.selftest_wait(1000)
+    assert g.status() == 1            # reported once ...
+    assert g.status() == 0            # ... and cleared
+    st = si.Stream(1520, 1)
+    d = si.uniform_poly(st, o.q, o.N)
+    x = si.uniform_poly(st, o.q + o.p, o.N)
+    check_modup_moddown(g, o, d, x, P.nq, "after a timeout")
     assert g.status() == 0
     g.close()
