@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--bootstrap-only", action="store_true",
                     help="run only the bootstrapping workload and print its JSON (for profiler launch lists)")
     ap.add_argument("--bootstrap-batch", type=int, default=8)
+    ap.add_argument("--bootstrap-lanes", type=int, default=2,
+                    help="programs (each with its own work buffer) run on this many streams of one context")
     ap.add_argument("--ops-only", action="store_true",
                     help="run only the hoisted-rotation / linear-transform / element-wise legs (profiler captures)")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -743,7 +745,9 @@ def run_bootstrap(args):
     bits, K = 10 special 60-bit primes, dnum = 3; the library's planner builds
     the program (CoeffToSlot / SlotToCoeff with level budget 3/3, EvalMod of
     Chebyshev degree 119 plus 2 double-angle steps).  A batch of 8 one-limb
-    ciphertexts is bootstrapped one after another.  Keys and ciphertexts are
+    ciphertexts is bootstrapped one after another on one stream, then dealt
+    over --bootstrap-lanes streams of the same context (one program, with its
+    own work buffer, per lane).  Keys and ciphertexts are
     uniform residues of the right shapes (timing only; the decryption check is
     in the GPU tests)."""
     import torch
@@ -782,7 +786,33 @@ def run_bootstrap(args):
         dp.run(c, o, 2.0 ** 50)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms_one = e0.elapsed_time(e1)
+    # the same batch over several lanes: one program (own work buffer) per
+    # stream of the same context, ciphertexts dealt round robin; the events
+    # on the launching stream bracket every lane (each lane waits on e0 and
+    # e1 waits on each lane)
+    lanes = max(1, args.bootstrap_lanes)
+    ms = ms_one
+    if lanes > 1:
+        dps = [dp] + [bt.DeviceProgram(ctx, prog, rlk, ck, rks) for _ in range(lanes - 1)]
+        sts = [torch.cuda.Stream() for _ in range(lanes)]
+        for k in range(lanes):      # warm every program once
+            dps[k].run(cts[k % len(cts)], outs[k % len(cts)], 2.0 ** 50, stream=sts[k])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s_ in sts:
+            s_.wait_event(e0)
+        for k, (c, o) in enumerate(zip(cts, outs)):
+            dps[k % lanes].run(c, o, 2.0 ** 50, stream=sts[k % lanes])
+        for s_ in sts:
+            ev = torch.cuda.Event()
+            ev.record(s_)
+            stream.wait_event(ev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        for d_ in dps[1:]:
+            d_.close()
     # one more bootstrap with every operation and kernel bracketed by events
     fides.trace_reset()
     fides.trace_enable(True)
@@ -801,6 +831,7 @@ def run_bootstrap(args):
     res = {"workload": "bootstrap logN=16, 2^15 slots, L=30 (1 x 60-bit + 29 x 54-bit), K=10, dnum=3, "
                        "CtS/StC level budget 3/3, EvalMod Chebyshev degree 119 + 2 double angles, batch of %d" % len(cts),
            "ms_per_ciphertext": round(ms / len(cts), 2), "ms_per_batch": round(ms, 2), "batch": len(cts),
+           "lanes": lanes, "one_lane_ms_per_batch": round(ms_one, 2),
            "limbs_out": dp.out_limbs, "rotation_keys": len(prog.rot_steps),
            "plaintexts": sum(len(t["coeffs"]) for t in prog.lts), "instructions": len(prog.instr),
            "instruction_mix": {names[k]: v for k, v in sorted(counts.items())},

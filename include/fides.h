@@ -32,6 +32,9 @@
  *    entry point is asynchronous with respect to the host.
  *  - Calls on one context use the context's scratch memory and must not run
  *    concurrently (issue them on one stream, or create one context per stream).
+ *    Programs (fides_program_run) are the exception: each run uses the scratch
+ *    inside its own work buffer, so runs with different work buffers may
+ *    overlap on several streams of one context.
  *  - Return value: FIDES_OK (0) or a negative FIDES_ERR_* code; the message of
  *    the last error on the calling thread is available from fides_last_error().
  *    Argument errors are detected before anything is queued.
@@ -511,11 +514,14 @@ int64_t fides_now_ns(void);
  * copies every host table (device plaintexts and keys are referenced and must
  * outlive the program) and maps the virtual registers onto as few
  * ciphertext-sized buffers as their lifetimes allow.
- * fides_program_info reports the device work buffer the program needs (words),
- * the buffer count and the output's limb count.
+ * fides_program_info reports the device work buffer the program needs (words:
+ * the register buffers, the linear transforms' buffers and a key-switching
+ * scratch pool of the context's size), the buffer count and the output's limb
+ * count.
  * fides_program_run executes it on `stream` from `in` (in_limbs limbs) into
- * `out` (the output register's limbs; out->scale = desc->out_scale); it uses
- * the context's scratch like the single-operation entry points.
+ * `out` (the output register's limbs; out->scale = desc->out_scale).  It
+ * touches no context scratch: runs of one or several programs on one context
+ * with distinct work buffers may proceed concurrently on different streams.
  */
 #define FIDES_I_MODRAISE 1
 #define FIDES_I_LT 2

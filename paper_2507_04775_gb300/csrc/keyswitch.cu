@@ -7,11 +7,13 @@
 #include <vector>
 
 #include "fides_internal.cuh"
+#include "ops_ws.h"
 #include "plan.cuh"
 
 namespace {
 
-// Scratch layout of one operation (words from ctx->scratch):
+// Scratch layout of one operation (words from the caller's pool, by default
+// the context's ctx->scratch):
 //   dsrc  [L]      key-switch input of HMult (d2) or HRotate (sigma(c1))
 //   key switch     coeff, ext, acc, pc, conv at the top level (ks_carve)
 //   last  [2]      Rescale: coefficient form of the dropped limb
@@ -19,10 +21,10 @@ struct Scratch {
     u64 *dsrc, *ks, *last;
 };
 
-Scratch carve(const fides_ctx *c)
+Scratch carve(const fides_ctx *c, u64 *ws)
 {
     Scratch s;
-    s.dsrc = c->scratch;
+    s.dsrc = ws ? ws : c->scratch;
     s.ks = s.dsrc + (size_t)c->L * c->N;
     s.last = s.ks + ks_scratch_words(c, c->L);
     return s;
@@ -149,7 +151,7 @@ extern "C" int fides_modup(fides_ctx *c, const uint64_t *d, int nl, uint64_t *ex
     if (int rc = check_level(c, nl, "fides_modup")) return rc;
     if (!d || !ext) return fides_set_error(FIDES_ERR_ARG, "fides_modup: NULL buffer");
     cudaStream_t st = as_stream(stream);
-    KsBuffers B = ks_buffers(c, d, nl, nullptr, nullptr, nullptr, 0, 0, carve(c));
+    KsBuffers B = ks_buffers(c, d, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, nullptr));
     B.ext = ext;
     if (int rc = run_modup(c, B, st)) return rc;
     // the digits' own limbs are the input's limbs
@@ -170,7 +172,7 @@ extern "C" int fides_moddown(fides_ctx *c, const uint64_t *x, int nl, uint64_t *
     if (int rc = check_level(c, nl, "fides_moddown")) return rc;
     if (!x || !out) return fides_set_error(FIDES_ERR_ARG, "fides_moddown: NULL buffer");
     cudaStream_t st = as_stream(stream);
-    KsBuffers B = ks_buffers(c, nullptr, nl, nullptr, out, nullptr, 0, 0, carve(c));
+    KsBuffers B = ks_buffers(c, nullptr, nl, nullptr, out, nullptr, 0, 0, carve(c, nullptr));
     const size_t N = c->N;
     std::vector<Seg> v(1, seg_of(x + (size_t)nl * N, B.pc, c->K, c->L, nullptr, nullptr, 1, 0, c->d_md_nscale));
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
@@ -189,11 +191,17 @@ extern "C" int fides_keyswitch(fides_ctx *c, const uint64_t *d, int nl, const ui
     if (int rc = check_level(c, nl, "fides_keyswitch")) return rc;
     if (!d || !evk || !out0 || !out1) return fides_set_error(FIDES_ERR_ARG, "fides_keyswitch: NULL buffer");
     OpTrace op("op_keyswitch", as_stream(stream));
-    return run_keyswitch(c, ks_buffers(c, d, nl, evk, out0, out1, 0, 0, carve(c)), as_stream(stream));
+    return run_keyswitch(c, ks_buffers(c, d, nl, evk, out0, out1, 0, 0, carve(c, nullptr)), as_stream(stream));
 }
 
 extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
                            void *stream)
+{
+    return fides_hmult_ws(c, a, b, rlk, out, stream, nullptr);
+}
+
+int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
+                   void *stream, u64 *ws)
 {
     if (int rc = check_ctx(c, "fides_hmult")) return rc;
     if (!a || !b || !out || !rlk || !a->data || !b->data || !out->data)
@@ -206,7 +214,8 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult", st);
-    KsBuffers B = ks_buffers(c, carve(c).dsrc, nl, rlk, out->data, out->data + S, 1, 1, carve(c));
+    const Scratch sc = carve(c, ws);
+    KsBuffers B = ks_buffers(c, sc.dsrc, nl, rlk, out->data, out->data + S, 1, 1, sc);
     B.prep = 1;
     B.pa = a->data;
     B.pb = b->data;
@@ -218,7 +227,7 @@ extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
 
 // sigma_g of a ciphertext with key switching (HRotate, Conjugate)
 static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_t *rk, fides_ct *out, void *stream,
-                           const char *fn, const char *trace)
+                           const char *fn, const char *trace, u64 *ws)
 {
     if (int rc = check_ctx(c, fn)) return rc;
     if (!a || !out || !rk || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
@@ -228,7 +237,8 @@ static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op(trace, st);
-    KsBuffers B = ks_buffers(c, carve(c).dsrc, nl, rk, out->data, out->data + S, 1, 0, carve(c));
+    const Scratch sc = carve(c, ws);
+    KsBuffers B = ks_buffers(c, sc.dsrc, nl, rk, out->data, out->data + S, 1, 0, sc);
     B.prep = 2;
     B.pa = a->data;
     B.pout = out->data;
@@ -238,17 +248,28 @@ static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_
     return rc;
 }
 
+int fides_rotate_ws(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out, void *stream,
+                    u64 *ws)
+{
+    if (int rc = check_ctx(c, "fides_rotate")) return rc;
+    return automorph_entry(c, a, fides_galois_elt(c, steps), rk, out, stream, "fides_rotate", "op_rotate", ws);
+}
+
 extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out,
                             void *stream)
 {
-    if (int rc = check_ctx(c, "fides_rotate")) return rc;
-    return automorph_entry(c, a, fides_galois_elt(c, steps), rk, out, stream, "fides_rotate", "op_rotate");
+    return fides_rotate_ws(c, a, steps, rk, out, stream, nullptr);
+}
+
+int fides_conjugate_ws(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fides_ct *out, void *stream, u64 *ws)
+{
+    if (int rc = check_ctx(c, "fides_conjugate")) return rc;
+    return automorph_entry(c, a, 2 * (u64)c->N - 1, ck, out, stream, "fides_conjugate", "op_conjugate", ws);
 }
 
 extern "C" int fides_conjugate(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fides_ct *out, void *stream)
 {
-    if (int rc = check_ctx(c, "fides_conjugate")) return rc;
-    return automorph_entry(c, a, 2 * (u64)c->N - 1, ck, out, stream, "fides_conjugate", "op_conjugate");
+    return fides_conjugate_ws(c, a, ck, out, stream, nullptr);
 }
 
 extern "C" int fides_hsquare(fides_ctx *c, const fides_ct *a, const uint64_t *rlk, fides_ct *out, void *stream)
@@ -258,6 +279,12 @@ extern "C" int fides_hsquare(fides_ctx *c, const fides_ct *a, const uint64_t *rl
 
 extern "C" int fides_rotate_hoisted(fides_ctx *c, const fides_ct *a, int n_rot, const int64_t *steps,
                                     const uint64_t *const *rks, fides_ct *outs, void *stream)
+{
+    return fides_rotate_hoisted_ws(c, a, n_rot, steps, rks, outs, stream, nullptr);
+}
+
+int fides_rotate_hoisted_ws(fides_ctx *c, const fides_ct *a, int n_rot, const int64_t *steps,
+                            const uint64_t *const *rks, fides_ct *outs, void *stream, u64 *ws)
 {
     const char *fn = "fides_rotate_hoisted";
     if (int rc = check_ctx(c, fn)) return rc;
@@ -273,7 +300,7 @@ extern "C" int fides_rotate_hoisted(fides_ctx *c, const fides_ct *a, int n_rot, 
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_rotate_hoisted", st);
     // one ModUp of c1 (the INTT reads c1 itself; the digits' own limbs are c1's)
-    KsBuffers B = ks_buffers(c, a->data + S, nl, nullptr, nullptr, nullptr, 0, 0, carve(c));
+    KsBuffers B = ks_buffers(c, a->data + S, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, ws));
     if (int rc = run_modup(c, B, st)) return rc;
     for (int k = 0; k < n_rot; ++k) {
         B.evk = rks[k];
@@ -305,6 +332,11 @@ extern "C" int fides_rotate_hoisted(fides_ctx *c, const fides_ct *a, int n_rot, 
 
 extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
 {
+    return fides_rescale_ws(c, a, out, stream, nullptr);
+}
+
+int fides_rescale_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws)
+{
     if (int rc = check_ctx(c, "fides_rescale")) return rc;
     if (!a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "fides_rescale: NULL argument");
     const int nl = a->n_limbs;
@@ -313,7 +345,7 @@ extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, voi
         return fides_set_error(FIDES_ERR_ARG, "fides_rescale: needs n_limbs >= 2 and out->n_limbs = n_limbs - 1");
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_rescale", st);
-    Scratch s = carve(c);
+    Scratch s = carve(c, ws);
     std::vector<Seg> v;
     rs_intt_segs(c, a->data, nl, s.last, v);
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
@@ -326,6 +358,11 @@ extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, voi
 
 extern "C" int fides_modraise(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
 {
+    return fides_modraise_ws(c, a, out, stream, nullptr);
+}
+
+int fides_modraise_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws)
+{
     const char *fn = "fides_modraise";
     if (int rc = check_ctx(c, fn)) return rc;
     if (!a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
@@ -336,7 +373,7 @@ extern "C" int fides_modraise(fides_ctx *c, const fides_ct *a, fides_ct *out, vo
     const size_t N = c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_modraise", st);
-    Scratch s = carve(c);
+    Scratch s = carve(c, ws);
     std::vector<Seg> v;
     for (int t = 0; t < 2; ++t) v.push_back(seg_of(a->data + (size_t)t * N, s.last + (size_t)t * N, 1, 0));
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;

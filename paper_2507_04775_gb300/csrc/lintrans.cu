@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fides_internal.cuh"
+#include "ops_ws.h"
 
 namespace {
 
@@ -68,6 +69,15 @@ extern "C" int fides_linear_transform(fides_ctx *c, const fides_ct *a, int n_dia
                                       const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
                                       size_t work_words, fides_ct *out, void *stream)
 {
+    return fides_linear_transform_ws(c, a, n_diag, diag_idx, pts, pt_scale, n1, n_keys, key_steps, keys, work,
+                                     work_words, out, stream, nullptr);
+}
+
+int fides_linear_transform_ws(fides_ctx *c, const fides_ct *a, int n_diag, const int *diag_idx,
+                              const uint64_t *const *pts, double pt_scale, int n1, int n_keys,
+                              const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
+                              size_t work_words, fides_ct *out, void *stream, u64 *ws)
+{
     const char *fn = "fides_linear_transform";
     if (!c || !a || !a->data || !out || !out->data || !pts || (n_keys > 0 && (!key_steps || !keys)))
         return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
@@ -110,7 +120,8 @@ extern "C" int fides_linear_transform(fides_ctx *c, const fides_ct *a, int n_dia
             outs[r].scale = 0.0;
             baby[P.baby[r]] = outs[r].data;
         }
-        if (int rc = fides_rotate_hoisted(c, a, (int)steps.size(), steps.data(), baby_keys.data(), outs.data(), stream))
+        if (int rc = fides_rotate_hoisted_ws(c, a, (int)steps.size(), steps.data(), baby_keys.data(), outs.data(),
+                                             stream, ws))
             return rc;
     }
     u64 *inner = work + P.baby.size() * ct_words;
@@ -134,7 +145,7 @@ extern "C" int fides_linear_transform(fides_ctx *c, const fides_ct *a, int n_dia
         if (int rc = launch_ptmac(c, cts.data(), ps.data(), (int)cts.size(), inner, nl, false, st)) return rc;
         fides_ct ci = {inner, nl, a->scale * pt_scale};
         fides_ct ct = {have_out ? term : out->data, nl, 0.0};
-        if (int rc = fides_rotate(c, &ci, (int64_t)n1 * g, giant_keys[g], &ct, stream)) return rc;
+        if (int rc = fides_rotate_ws(c, &ci, (int64_t)n1 * g, giant_keys[g], &ct, stream, ws)) return rc;
         if (have_out) {
             fides_ct co = {out->data, nl, 0.0};
             if (int rc = fides_hadd(c, &co, &ct, &co, stream)) return rc;

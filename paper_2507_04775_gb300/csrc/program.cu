@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "fides_internal.cuh"
+#include "ops_ws.h"
 
 struct fides_program {
     fides_ctx *ctx;
@@ -264,7 +265,10 @@ extern "C" int fides_program_info(const fides_program *p, size_t *work_words, in
 {
     if (!p) return fides_set_error(FIDES_ERR_ARG, "fides_program_info: NULL program");
     const size_t ct = 2 * (size_t)p->ctx->L * p->ctx->N;
-    if (work_words) *work_words = (size_t)p->n_phys * ct + p->lt_words;
+    // registers, linear-transform buffers, and the program's own scratch pool
+    // for its key-switching operations (so that programs on one context can
+    // run concurrently on several streams)
+    if (work_words) *work_words = (size_t)p->n_phys * ct + p->lt_words + p->ctx->scratch_words;
     if (buffers) *buffers = p->n_phys;
     if (out_limbs) *out_limbs = p->level[p->out_reg];
     return FIDES_OK;
@@ -287,6 +291,7 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
     cudaStream_t st = (cudaStream_t)stream;
     OpTrace tr("op_program", st);
     uint64_t *lt_work = work + (size_t)p->n_phys * ct_words;
+    u64 *ws = lt_work + p->lt_words;
     std::vector<double> scale(p->n_regs, 0.0);
     scale[p->in_reg] = in->scale;
     auto reg = [&](int r) {
@@ -319,15 +324,15 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
             d.scale = sc;
             break;
         }
-        case FIDES_I_MODRAISE: rc = fides_modraise(c, &a, &d, stream); break;
+        case FIDES_I_MODRAISE: rc = fides_modraise_ws(c, &a, &d, stream, ws); break;
         case FIDES_I_LT: {
             const fides_program::Lt &t = p->lt[I.arg];
-            rc = fides_linear_transform(c, &a, (int)t.idx.size(), t.idx.data(), t.pts.data(), t.pt_scale, t.n1,
-                                        (int)p->rot_steps.size(), p->rot_steps.data(), p->rot_keys.data(), lt_work,
-                                        p->lt_words, &d, stream);
+            rc = fides_linear_transform_ws(c, &a, (int)t.idx.size(), t.idx.data(), t.pts.data(), t.pt_scale, t.n1,
+                                           (int)p->rot_steps.size(), p->rot_steps.data(), p->rot_keys.data(),
+                                           lt_work, p->lt_words, &d, stream, ws);
             break;
         }
-        case FIDES_I_RESCALE: rc = fides_rescale(c, &a, &d, stream); break;
+        case FIDES_I_RESCALE: rc = fides_rescale_ws(c, &a, &d, stream, ws); break;
         case FIDES_I_DROP:
             for (int t = 0; t < 2 && !rc; ++t)
                 rc = fides_check_cuda(cudaMemcpyAsync(d.data + (size_t)t * d.n_limbs * N, a.data + (size_t)t * a.n_limbs * N,
@@ -343,8 +348,8 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
             break;
         case FIDES_I_HADD: rc = fides_hadd(c, &a, &b, &d, stream); break;
         case FIDES_I_HSUB: rc = fides_hsub(c, &a, &b, &d, stream); break;
-        case FIDES_I_HMULT: rc = fides_hmult(c, &a, &b, p->relin, &d, stream); break;
-        case FIDES_I_CONJ: rc = fides_conjugate(c, &a, p->conj, &d, stream); break;
+        case FIDES_I_HMULT: rc = fides_hmult_ws(c, &a, &b, p->relin, &d, stream, ws); break;
+        case FIDES_I_CONJ: rc = fides_conjugate_ws(c, &a, p->conj, &d, stream, ws); break;
         case FIDES_I_MULI: rc = fides_mul_i(c, &a, I.arg, &d, stream); break;
         case FIDES_I_CMULT:
             rc = fides_scalar_mult(c, &a, p->consts[I.arg].data(), p->const_scale[I.arg], &d, stream);

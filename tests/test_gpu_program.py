@@ -100,3 +100,35 @@ def test_modraise_program_matches_the_oracle():
     assert np.array_equal(to_host(out).reshape(ref.shape), ref)
     dp.close()
     g.close()
+
+
+def test_runs_overlap_on_two_streams_of_one_context():
+    """Two programs on one context, each with its own work buffer (and so its
+    own key-switching scratch), run on two streams at once: each result equals
+    the oracle interpreter's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.MID
+    q = find_primes(P.logN, P.q_bits, P.nq)
+    p = find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    g, o = Context(P.logN, q, p, P.dnum), oracle.Context(P.logN, q, p, P.dnum)
+    st = si.Stream(1103)
+    prog, nl = build(o, st)
+    rlk, ck = rand_key(st, o), rand_key(st, o)
+    rks = {s: rand_key(st, o) for s in (1, 4)}
+    keys = (to_device(rlk), to_device(ck), {s: to_device(k) for s, k in rks.items()})
+    ins = [np.stack([si.uniform_poly(st, o.q, o.N) for _ in range(2)]) for _ in range(4)]
+    refs = [obt.run(o, prog, a, rlk, ck, rks) for a in ins]
+    dps = [bt.DeviceProgram(g, prog, *keys, in_limbs=nl) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in dps]
+    outs = [torch.empty(2 * 7 * o.N, dtype=torch.int64, device="cuda") for _ in ins]
+    dins = [to_device(a) for a in ins]
+    torch.cuda.synchronize()
+    for k in range(len(ins)):
+        dps[k % 2].run(dins[k], outs[k], stream=streams[k % 2])
+    torch.cuda.synchronize()
+    for k in range(len(ins)):
+        assert np.array_equal(to_host(outs[k]).reshape(refs[k].shape), refs[k]), k
+    for dp in dps:
+        dp.close()
+    g.close()
