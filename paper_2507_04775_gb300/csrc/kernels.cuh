@@ -315,20 +315,21 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
                 k1[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 1) * nfull + pz) * N + n);
             }
         }
-        U128 a0 = {0, 0}, a1 = {0, 0}, b0 = {0, 0}, b1 = {0, 0};
+        // 128-bit sums as 32-bit carry chains (each product < 2^122, at most
+        // FIDES_MAX_DIGITS of them)
+        Acc128 a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0}, b0 = {0, 0, 0, 0}, b1 = {0, 0, 0, 0};
 #pragma unroll
         for (int j = 0; j < MAXB; ++j) {
             if (j < beta) {
-                mac128(a0, e[j].x, k0[j].x);
-                mac128(b0, e[j].y, k0[j].y);
-                mac128(a1, e[j].x, k1[j].x);
-                mac128(b1, e[j].y, k1[j].y);
+                mac_wide(a0, e[j].x, k0[j].x);
+                mac_wide(b0, e[j].y, k0[j].y);
+                mac_wide(a1, e[j].x, k1[j].x);
+                mac_wide(b1, e[j].y, k1[j].y);
             }
         }
-        *reinterpret_cast<ulonglong2 *>(acc + (size_t)z * N + n) =
-            make_ulonglong2(reduce128(a0.hi, a0.lo, pr), reduce128(b0.hi, b0.lo, pr));
+        *reinterpret_cast<ulonglong2 *>(acc + (size_t)z * N + n) = make_ulonglong2(reduce_acc(a0, pr), reduce_acc(b0, pr));
         *reinterpret_cast<ulonglong2 *>(acc + ((size_t)ne + z) * N + n) =
-            make_ulonglong2(reduce128(a1.hi, a1.lo, pr), reduce128(b1.hi, b1.lo, pr));
+            make_ulonglong2(reduce_acc(a1, pr), reduce_acc(b1, pr));
         return;
     }
     // hoisted rotation: the digits are read through sigma_g (evaluation form:
@@ -350,16 +351,16 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
             k1[j] = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
         }
     }
-    U128 a0 = {0, 0}, a1 = {0, 0};
+    Acc128 a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
 #pragma unroll
     for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
-            mac128(a0, e[j], k0[j]);
-            mac128(a1, e[j], k1[j]);
+            mac_wide(a0, e[j], k0[j]);
+            mac_wide(a1, e[j], k1[j]);
         }
     }
-    acc[(size_t)z * N + n] = reduce128(a0.hi, a0.lo, pr);
-    acc[((size_t)ne + z) * N + n] = reduce128(a1.hi, a1.lo, pr);
+    acc[(size_t)z * N + n] = reduce_acc(a0, pr);
+    acc[((size_t)ne + z) * N + n] = reduce_acc(a1, pr);
 }
 
 // whether an op can take the paired path

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "fides_internal.cuh"
+
 int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
                    void *stream, u64 *ws);
 int fides_rotate_ws(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out, void *stream,
