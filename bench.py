@@ -304,6 +304,26 @@ def run_fides(args, world, rank, local):
     ops = 2 * args.steps * world
     value = ops / (ms_max / 1e3)
 
+    # ------- the same steps with HMult and Rescale as one call (reported
+    # beside the single-op value, which stays the headline) -------
+    def step_fused(k):
+        i = k % POOL
+        ctx.hmult_rescale(dA[i], dB[i], nl, rlk, out_s, scale, scale)
+        ctx.rotate(dA[i], nl, 1 << (k % N_ROT), rks[k % N_ROT], out_r, scale)
+
+    for k in range(args.warmup):
+        step_fused(k)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step_fused(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fused = max_over_ranks(e0.elapsed_time(e1), world)
+    fused = {"workload": "the same steps with fides_hmult_rescale (HMult+relin and Rescale in one key switch, "
+                         "residues equal to the two calls), then HRotate",
+             "value": round(ops / (ms_fused / 1e3), 2), "unit": "ops/s", "ms_per_step": round(ms_fused / args.steps, 4)}
+
     # ------- the same K steps again, every launch bracketed by events -------
     # (events between launches serialise programmatic dependent launch, so
     # this pass gives per-kernel durations, not the value above)
@@ -394,6 +414,7 @@ def run_fides(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": ck,
         "e2e": e2e,
+        "fused_hmult_rescale": fused,
         "batched": batched,
         "serving": serving,
         "ops": ops_extra,

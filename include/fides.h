@@ -206,6 +206,20 @@ int fides_hmult(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint
                 fides_ct *out, void *stream);
 
 /*
+ * HMult with relinearisation followed by Rescale, in one key switch: out
+ * (a->n_limbs - 1 limbs, n_limbs >= 2) receives exactly the residues of
+ * fides_hmult then fides_rescale; out->scale = a->scale * b->scale / q_l.
+ * By linearity of the NTT the Rescale folds into the ModDown (Sec. III-F5
+ * "ModDown fusion" and "Rescale fusion" combined): the ModDown's INTT also
+ * transforms the dropped limb of the tensor product and of the accumulators,
+ * and one forward NTT over the remaining limbs computes
+ * q_l^-1 (d_i + P^-1 acc_i - NTT(P^-1 conv_i + [last]_{q_i})).  out may not
+ * alias a or b.
+ */
+int fides_hmult_rescale(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint64_t *dev_rlk,
+                        fides_ct *out, void *stream);
+
+/*
  * HRotate (Table I): rotation of the slots left by `steps` (g = 5^steps mod
  * 2N); out = (sigma_g(c0) + ks0, ks1) with (ks0, ks1) = KeySwitch(sigma_g(c1),
  * rk) and rk the switching key of s(X^g).  out may not alias a.

@@ -159,6 +159,7 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_md_mat);
     cudaFree(c->d_md_pinv);
     cudaFree(c->d_rs_qlinv);
+    cudaFree(c->d_hr);
     cudaFree(c->d_mu_nscale);
     cudaFree(c->d_md_nscale);
     cudaFree(c->d_raise);
@@ -254,7 +255,9 @@ static size_t scratch_words_for(int L, int K, int dnum, int alpha, int N)
     size_t ne = (size_t)(L + K);
     // d2 / rotated c1 (L) + coeff copy (L) + ext (beta*ne) + acc (2*ne)
     // + P-limb INTT (2K) + conversion outputs (2L) + two spare limbs
-    return (size_t)N * (2 * (size_t)L + beta * ne + 2 * ne + 2 * (size_t)K + 2 * (size_t)L + 2);
+    // + HMult fused with Rescale: the tensor product d0, d1 (2L) and the
+    //   coefficient forms of their and the accumulators' dropped limb (4)
+    return (size_t)N * (2 * (size_t)L + beta * ne + 2 * ne + 2 * (size_t)K + 2 * (size_t)L + 2 + 2 * (size_t)L + 4);
 }
 
 extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out)
@@ -399,6 +402,14 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     for (int l = 1; l < L; ++l)
         for (int i = 0; i < l; ++i) rs[(size_t)l * L + i] = pair_of(hinv(primes[l] % primes[i], primes[i]), primes[i]);
 
+    // HMult fused with Rescale: (P^-1, q_l^-1) mod q_i
+    std::vector<TwPair> hr((size_t)L * L * 2);
+    for (int l = 1; l < L; ++l)
+        for (int i = 0; i < l; ++i) {
+            hr[((size_t)l * L + i) * 2] = md_pinv[i];
+            hr[((size_t)l * L + i) * 2 + 1] = rs[(size_t)l * L + i];
+        }
+
     // ModRaise: q_0 mod q_i (the centred lift subtracts q_0 from the upper half)
     std::vector<TwPair> raise((size_t)L);
     for (int i = 0; i < L; ++i) raise[i] = pair_of(primes[0] % primes[i], primes[i]);
@@ -432,6 +443,7 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     if (!rc) rc = upload(&c->d_md_mat, md_mat, "moddown tables");
     if (!rc) rc = upload(&c->d_md_pinv, md_pinv, "moddown tables");
     if (!rc) rc = upload(&c->d_rs_qlinv, rs, "rescale tables");
+    if (!rc) rc = upload(&c->d_hr, hr, "rescale tables");
     if (!rc) rc = upload(&c->d_mu_nscale, mu_ns, "modup tables");
     if (!rc) rc = upload(&c->d_md_nscale, md_ns, "moddown tables");
     if (!rc) rc = upload(&c->d_raise, raise, "modraise tables");

@@ -118,6 +118,9 @@ struct fides_ctx {
 
     // Rescale: [L][L], entry (l, i) = q_l^-1 mod q_i
     TwPair *d_rs_qlinv;
+    // HMult fused with Rescale: [L][L][2], entry (l, i) = (P^-1 mod q_i,
+    // q_l^-1 mod q_i)
+    TwPair *d_hr;
 
     // Combined final constants of the inverse NTTs that feed a base conversion
     // (the N^-1 of the INTT times the conversion's qhat^-1):

@@ -17,8 +17,10 @@ namespace {
 //   dsrc  [L]      key-switch input of HMult (d2) or HRotate (sigma(c1))
 //   key switch     coeff, ext, acc, pc, conv at the top level (ks_carve)
 //   last  [2]      Rescale: coefficient form of the dropped limb
+//   dd    [2][L]   HMult fused with Rescale: the tensor product d0, d1
+//   lastc [4]      ... and the coefficient forms of d0, d1, acc0, acc1 at the dropped limb
 struct Scratch {
-    u64 *dsrc, *ks, *last;
+    u64 *dsrc, *ks, *last, *dd, *lastc;
 };
 
 Scratch carve(const fides_ctx *c, u64 *ws)
@@ -27,7 +29,30 @@ Scratch carve(const fides_ctx *c, u64 *ws)
     s.dsrc = ws ? ws : c->scratch;
     s.ks = s.dsrc + (size_t)c->L * c->N;
     s.last = s.ks + ks_scratch_words(c, c->L);
+    s.dd = s.last + 2 * (size_t)c->N;
+    s.lastc = s.dd + 2 * (size_t)c->L * c->N;
     return s;
+}
+
+// HMult fused with Rescale: the coefficient form of the dropped limb l of the
+// HMult result, last_t = INTT(d_t,l) + P^-1 (INTT(acc_t,l) - conv_t,l) mod q_l
+// (canonical), for t = 0, 1; lastc = [INTT(d0), INTT(d1), INTT(acc0),
+// INTT(acc1)] at limb l, conv_t,l < 4 q_l.
+__global__ void __launch_bounds__(256) k_hr_last(const u64 *__restrict__ lastc, const u64 *__restrict__ conv0,
+                                                 const u64 *__restrict__ conv1, u64 *__restrict__ last,
+                                                 const TwPair *__restrict__ md_pinv, const PrimeInfo *__restrict__ P,
+                                                 int l, int N)
+{
+    pdl_enter();
+    const TwPair pinv = md_pinv[l];
+    const PrimeInfo p = P[l];
+    const int t = blockIdx.y;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (size_t)N) return;
+    const u64 dv = lastc[(size_t)t * N + n], av = lastc[(size_t)(2 + t) * N + n];
+    const u64 cv = (t ? conv1 : conv0)[n];
+    const u64 x = mul_shoup(av + 4 * p.q - cv, pinv, p.q) + dv;   // < 3q
+    last[(size_t)t * N + n] = csub(csub(x, p.q2), p.q);
 }
 
 int run_modup(const fides_ctx *c, const KsBuffers &B, cudaStream_t st)
@@ -222,6 +247,72 @@ int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uin
     B.pout = out->data;
     int rc = run_keyswitch(c, B, st);
     if (!rc) out->scale = a->scale * b->scale;
+    return rc;
+}
+
+extern "C" int fides_hmult_rescale(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk,
+                                   fides_ct *out, void *stream)
+{
+    return fides_hmult_rescale_ws(c, a, b, rlk, out, stream, nullptr);
+}
+
+// Rescale(HMult(a, b)) in one key switch: the tensor product goes to scratch;
+// the ModDown's INTT also transforms limb l = nl - 1 of d0, d1, acc0, acc1;
+// k_hr_last forms the coefficient form of the dropped limb; one forward NTT
+// over the remaining limbs gives q_l^-1 (d + P^-1 acc - NTT(P^-1 conv +
+// [last])) (ProHmRs / EpiHmRs).  Residues equal fides_hmult then
+// fides_rescale.
+int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
+                           void *stream, u64 *ws)
+{
+    const char *fn = "fides_hmult_rescale";
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!a || !b || !out || !rlk || !a->data || !b->data || !out->data)
+        return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    const int nl = a->n_limbs, l = nl - 1;
+    if (int rc = check_level(c, nl, fn)) return rc;
+    if (nl < 2 || b->n_limbs != nl || out->n_limbs != l)
+        return fides_set_error(FIDES_ERR_ARG, "%s: needs n_limbs >= 2, equal input levels and out->n_limbs = n_limbs - 1",
+                               fn);
+    const size_t N = c->N, S = (size_t)nl * N, ne = (size_t)nl + c->K;
+    cudaStream_t st = as_stream(stream);
+    OpTrace op("op_hmult_rescale", st);
+    const Scratch sc = carve(c, ws);
+    KsBuffers B = ks_buffers(c, sc.dsrc, nl, rlk, sc.dd, sc.dd + S, 1, 1, sc);
+    B.prep = 1;
+    B.pa = a->data;
+    B.pb = b->data;
+    B.pout = sc.dd;
+    if (int rc = run_modup(c, B, st)) return rc;
+    IPArgs ip;
+    memset(&ip, 0, sizeof(ip));
+    ip.one = ks_ip_op(c, B);
+    if (int rc = launch_inner(c, ip, nl + c->K, ks_beta(c, nl), st)) return rc;
+    // ModDown INTT of the special limbs, plus limb l of d0, d1, acc0, acc1
+    std::vector<Seg> v;
+    ks_pinv_segs(c, B, v);
+    for (int t = 0; t < 2; ++t) v.push_back(seg_of(sc.dd + t * S + (size_t)l * N, sc.lastc + t * N, 1, l));
+    for (int t = 0; t < 2; ++t)
+        v.push_back(seg_of(B.acc + (t * ne + l) * N, sc.lastc + (2 + t) * N, 1, l));
+    if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
+    std::vector<BConvJob> jb;
+    ks_moddown_jobs(c, B, jb);
+    if (int rc = launch_bconv(c, inline_bconv(jb), st)) return rc;
+    FIDES_LAUNCH("k_hr_last", st, k_hr_last, dim3((c->N + 255) / 256, 2), dim3(256), (const u64 *)sc.lastc,
+                 (const u64 *)(B.conv + (size_t)l * N), (const u64 *)(B.conv + (size_t)(nl + l) * N), sc.last,
+                 (const TwPair *)c->d_md_pinv, (const PrimeInfo *)c->d_prime, l, c->N);
+    if (int rc = fides_check_cuda(cudaGetLastError(), "fides_hmult_rescale: last limb")) return rc;
+    // one forward NTT over limbs 0 .. l-1 of both polynomials
+    v.clear();
+    for (int t = 0; t < 2; ++t) {
+        u64 *cv = B.conv + (size_t)t * nl * N;
+        Seg g = seg_of(sc.last + t * N, cv, l, 0, B.acc + t * ne * N, out->data + (size_t)t * l * N, 0, 0,
+                       c->d_hr + (size_t)l * c->L * 2);
+        g.side = sc.dd + t * S;
+        v.push_back(g);
+    }
+    int rc = ntt_forward(c, inline_set(v), ProHmRs{}, EpiHmRs{}, st);
+    if (!rc) out->scale = a->scale * b->scale / (double)c->primes[l];
     return rc;
 }
 

@@ -40,6 +40,7 @@ int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &s, cudaStream_t st)
     FIDES_NTT_DISPATCH(ntt_fwd_submul_rot, c, s, st)
 }
 int ntt_fwd_raise(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_fwd_raise, c, s, st) }
+int ntt_fwd_hmrs(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_fwd_hmrs, c, s, st) }
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &s, cudaStream_t st) { FIDES_NTT_DISPATCH(ntt_inv_canon, c, s, st) }
 
 namespace {

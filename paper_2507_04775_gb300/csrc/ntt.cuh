@@ -200,6 +200,37 @@ struct EpiSubMulRot {
     }
 };
 
+// HMult followed by Rescale in one pass (fides_hmult_rescale).  By linearity
+// of the NTT, Rescale(HMult) gives for every remaining limb i < l
+//   res_i = q_l^-1 (d_i + P^-1 acc_i - NTT(P^-1 conv_i + [last]_{q_i})),
+// with d the tensor product, acc the key inner product, conv the ModDown
+// conversion (coefficient form, < 4q) and last the coefficient form of the
+// dropped limb l of the HMult result.  The segment's src is `last` (src_step
+// 0: one limb for every limb of the run), dst holds conv_i (the pass works in
+// place), aux = acc_i, side = d_i, out = res_i; cst holds two constants per
+// prime: cst[2i] = P^-1 mod q_i, cst[2i + 1] = q_l^-1 mod q_i.
+struct ProHmRs {
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
+    {
+        const u64 x = mul_shoup(J.dst[j], J.cst[2 * J.prime], p.q);   // [0, 2q)
+        return x + reduce64_lazy(J.src[j], p);                        // [0, 4q)
+    }
+};
+struct EpiHmRs {
+    static constexpr bool kRaw = false;
+    __device__ __forceinline__ void load(const Job &J, u32 j, u64 &a, u64 &o) const
+    {
+        a = J.aux[j];
+        o = J.side[j];
+    }
+    __device__ __forceinline__ void store(const Job &J, u32 j, u64 v, u64 a, u64 o, const PrimeInfo &p) const
+    {
+        const u64 y = csub(v, p.q);
+        const u64 r = o + mul_shoup(a, J.cst[2 * J.prime], p.q) + p.q - y;   // < 4q
+        J.out[j] = csub(mul_shoup(r, J.cst[2 * J.prime + 1], p.q), p.q);
+    }
+};
+
 // One round of up to four radix-2 stages on the thread's 16 registers, whose
 // local indices differ in the four bits [B, B+3] (the round's window).  A full
 // round runs the four stages of the window; the last round of a pass whose
@@ -391,6 +422,7 @@ int ntt_fwd_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);    
 int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t st);   // ProSwitchMod, EpiSubMul
 int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &set, cudaStream_t st);      // ProSrc, EpiSubMulRot
 int ntt_fwd_raise(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProRaise, EpiCanon
+int ntt_fwd_hmrs(const fides_ctx *c, const LimbSet &set, cudaStream_t st);            // ProHmRs, EpiHmRs
 int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep, EpiCanon
 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
@@ -412,6 +444,10 @@ inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiSubMulRo
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProRaise, EpiCanon, cudaStream_t st)
 {
     return ntt_fwd_raise(c, s, st);
+}
+inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProHmRs, EpiHmRs, cudaStream_t st)
+{
+    return ntt_fwd_hmrs(c, s, st);
 }
 inline int ntt_inverse(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {

@@ -136,6 +136,7 @@ void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStr
     int ntt_fwd_switch_submul_##L(const fides_ctx *, const LimbSet &, cudaStream_t);              \
     int ntt_fwd_submul_rot_##L(const fides_ctx *, const LimbSet &, cudaStream_t);                 \
     int ntt_fwd_raise_##L(const fides_ctx *, const LimbSet &, cudaStream_t);                      \
+    int ntt_fwd_hmrs_##L(const fides_ctx *, const LimbSet &, cudaStream_t);                       \
     int ntt_inv_canon_##L(const fides_ctx *, const LimbSet &, cudaStream_t);                      \
     void ntt_tune_one_##L(const fides_ctx *, int, int, const LimbSet &, cudaStream_t);
 
@@ -159,6 +160,10 @@ void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStr
     int ntt_fwd_raise_##L(const fides_ctx *c, const LimbSet &s, cudaStream_t st)                                \
     {                                                                                                             \
         return forward<L>(c, s, ProRaise{}, EpiCanon{}, st);                                                      \
+    }                                                                                                             \
+    int ntt_fwd_hmrs_##L(const fides_ctx *c, const LimbSet &s, cudaStream_t st)                                 \
+    {                                                                                                             \
+        return forward<L>(c, s, ProHmRs{}, EpiHmRs{}, st);                                                        \
     }                                                                                                             \
     int ntt_inv_canon_##L(const fides_ctx *c, const LimbSet &s, cudaStream_t st)                                \
     {                                                                                                             \

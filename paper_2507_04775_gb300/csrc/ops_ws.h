@@ -19,3 +19,5 @@ int fides_linear_transform_ws(fides_ctx *c, const fides_ct *a, int n_diag, const
                               const uint64_t *const *pts, double pt_scale, int n1, int n_keys,
                               const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
                               size_t work_words, fides_ct *out, void *stream, u64 *ws);
+int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
+                           void *stream, u64 *ws);

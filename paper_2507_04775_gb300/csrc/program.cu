@@ -43,6 +43,9 @@ struct fides_program {
     std::vector<int> phys;      // buffer of each virtual register (-1: the input)
     int n_phys;
     size_t lt_words;
+    // fuse[i]: instruction i is an HMULT whose product only the RESCALE at
+    // i + 1 reads; the pair runs as one fides_hmult_rescale
+    std::vector<char> fuse;
 };
 
 namespace {
@@ -57,6 +60,37 @@ std::vector<int> operands(const fides_program *p, const fides_instr &I)
     std::vector<int> r(1, I.a);
     if (reads_b(I.op) && I.b != I.a) r.push_back(I.b);
     return r;
+}
+
+// Registers are written once, so an instruction may move earlier as long as
+// its operands are defined before it.  Every RESCALE that is the only reader
+// of an HMULT's product moves to just after that HMULT, where the executor
+// runs the pair as one fused call.  Out-of-range registers are left for
+// analyse() to report.
+void hoist_rescales(fides_program *p)
+{
+    const int n = (int)p->instr.size();
+    auto readers = [&](std::vector<int> &count, std::vector<int> &at) {
+        count.assign(p->n_regs, 0);
+        at.assign(p->n_regs, -1);
+        for (int i = 0; i < n; ++i) {
+            const fides_instr &I = p->instr[i];
+            if (I.op == FIDES_I_CMAC && (I.arg < 0 || I.arg + 1 >= (int)p->lin_start.size())) continue;
+            for (int r : operands(p, I))
+                if (r >= 0 && r < p->n_regs) { ++count[r]; at[r] = i; }
+        }
+    };
+    std::vector<int> count, at;
+    readers(count, at);
+    for (int i = 0; i < n; ++i) {
+        const fides_instr I = p->instr[i];
+        if (I.op != FIDES_I_HMULT || I.dst < 0 || I.dst >= p->n_regs || I.dst == p->out_reg) continue;
+        if (count[I.dst] != 1) continue;
+        const int j = at[I.dst];
+        if (j <= i + 1 || p->instr[j].op != FIDES_I_RESCALE || p->instr[j].a != I.dst) continue;
+        std::rotate(p->instr.begin() + i + 1, p->instr.begin() + j, p->instr.begin() + j + 1);
+        readers(count, at);
+    }
 }
 
 int analyse(fides_program *p)
@@ -160,6 +194,16 @@ int analyse(fides_program *p)
         if (last[I.dst] < 0) free_list.push_back(b);   // never read
     }
     p->n_phys = count;
+    p->fuse.assign(n, 0);
+    for (int i = 0; i + 1 < n; ++i) {
+        const fides_instr &I = p->instr[i], &J = p->instr[i + 1];
+        if (I.op != FIDES_I_HMULT || J.op != FIDES_I_RESCALE || J.a != I.dst || I.dst == p->out_reg) continue;
+        if (last[I.dst] != i + 1) continue;
+        const int pd = p->phys[J.dst];
+        auto buf = [&](int r) { return r == p->in_reg ? -1 : p->phys[r]; };
+        if (pd == buf(I.a) || pd == buf(I.b)) continue;
+        p->fuse[i] = 1;
+    }
     // linear-transform scratch at the top level
     p->lt_words = 0;
     for (const fides_program::Lt &t : p->lt) {
@@ -235,6 +279,7 @@ extern "C" int fides_program_create(fides_ctx *c, const fides_program_desc *d, f
     p->conj = d->dev_conj_key;
     p->rot_steps.assign(d->rot_steps, d->rot_steps + d->n_rot_keys);
     p->rot_keys.assign(d->dev_rot_keys, d->dev_rot_keys + d->n_rot_keys);
+    hoist_rescales(p);
     if (int rc = analyse(p)) {
         delete p;
         return rc;
@@ -303,6 +348,19 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
     };
     for (size_t i = 0; i < p->instr.size(); ++i) {
         const fides_instr &I = p->instr[i];
+        if (p->fuse[i]) {
+            const fides_instr &J = p->instr[i + 1];
+            fides_ct a = reg(I.a), b = reg(I.b), d = reg(J.dst);
+            if (int rc = fides_hmult_rescale_ws(c, &a, &b, p->relin, &d, stream, ws)) {
+                char msg[400];
+                snprintf(msg, sizeof(msg), "%s", fides_last_error());
+                return fides_set_error(rc, "%s: instructions %zu-%zu (HMULT+RESCALE): %s", fn, i, i + 1, msg);
+            }
+            scale[I.dst] = a.scale * b.scale;
+            scale[J.dst] = d.scale;
+            ++i;
+            continue;
+        }
         fides_ct d = reg(I.dst), a, b;
         if (I.op != FIDES_I_CMAC) a = reg(I.a);
         if (reads_b(I.op)) b = reg(I.b);

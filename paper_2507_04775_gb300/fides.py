@@ -37,7 +37,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
            "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
-           "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait"]
+           "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -142,6 +142,7 @@ def lib():
         L.fides_keyswitch.argtypes = [_vp, _vp, _i, _vp, _vp, _vp, _vp]
         ctp = ctypes.POINTER(fides_ct)
         L.fides_hmult.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
+        L.fides_hmult_rescale.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
         L.fides_rotate.argtypes = [_vp, ctp, ctypes.c_int64, _vp, ctp, _vp]
         L.fides_rescale.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_rescale_noalloc.argtypes = [_vp, ctp, ctp, _vp]
@@ -400,6 +401,15 @@ class Context:
         co = self._ct(out, n_limbs, 0.0, "out")
         _check(lib().fides_hmult(self._h, ctypes.byref(ca), ctypes.byref(cb), _ptr(rlk, self.key_words(), "rlk"),
                                  ctypes.byref(co), _stream(stream)))
+        return co.scale
+
+    def hmult_rescale(self, a, b, n_limbs: int, rlk, out, scale_a: float = 1.0, scale_b: float = 1.0,
+                      stream=None) -> float:
+        """Rescale(HMult(a, b)) in one key switch; out has n_limbs - 1 limbs."""
+        ca, cb = self._ct(a, n_limbs, scale_a, "a"), self._ct(b, n_limbs, scale_b, "b")
+        co = self._ct(out, n_limbs - 1, 0.0, "out")
+        _check(lib().fides_hmult_rescale(self._h, ctypes.byref(ca), ctypes.byref(cb),
+                                         _ptr(rlk, self.key_words(), "rlk"), ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def rotate(self, a, n_limbs: int, steps: int, rk, out, scale: float = 1.0, stream=None) -> float:

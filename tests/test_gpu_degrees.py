@@ -1,7 +1,7 @@
 """GPU parity at the other ring degrees (logN 13, 14, 15, 17: two-pass NTTs
 whose passes are not multiples of four stages, so their last register round is
-partial): the NTT with every compiled tile variant, and HMult+relin, HRotate
-and Rescale, residue for residue against the oracle."""
+partial): the NTT with every compiled tile variant, and HMult+relin, HRotate,
+Rescale and the fused HMult+Rescale, residue for residue against the oracle."""
 import numpy as np
 import pytest
 
@@ -63,13 +63,17 @@ def test_key_switching_ops(pair):
         da, db = to_device(a), to_device(b)
         m, r = torch.empty_like(da), torch.empty_like(da)
         s = torch.empty(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+        hr = torch.empty(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
         g.hmult(da, db, nl, drlk, m)
         g.rotate(da, nl, 3, drk, r)
         g.rescale(da, nl, s)
+        g.hmult_rescale(da, db, nl, drlk, hr)
         torch.cuda.synchronize()
-        assert np.array_equal(to_host(m).reshape(a.shape), o.hmult(a, b, rlk)), nl
+        ref_m = o.hmult(a, b, rlk)
+        assert np.array_equal(to_host(m).reshape(a.shape), ref_m), nl
         assert np.array_equal(to_host(r).reshape(a.shape), o.rotate(a, 3, rk)), nl
         assert np.array_equal(to_host(s).reshape(2, nl - 1, o.N), o.rescale(a)), nl
+        assert np.array_equal(to_host(hr).reshape(2, nl - 1, o.N), o.rescale(ref_m)), nl
 
 
 def test_autotune_runs(pair):

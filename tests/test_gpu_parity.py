@@ -162,6 +162,23 @@ def test_rescale(pair):
         assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), o.rescale(a)), "rescale differs at nl=%d" % nl
 
 
+def test_hmult_rescale(pair):
+    """The fused HMult+Rescale against the oracle's HMult then Rescale, at
+    every level the other tests use (2 and up); the plain HMult on the same
+    inputs is unchanged."""
+    P, g, o = pair
+    st = si.Stream(1011, 12)
+    key = rand_key(st, o)
+    dk = to_device(key)
+    for nl in sorted({n for n in levels(P) if n >= 2} | {2}):
+        a, b = rand_poly(st, o.q[:nl], o.N, 2), rand_poly(st, o.q[:nl], o.N, 2)
+        out = torch.zeros(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+        scale = g.hmult_rescale(to_device(a), to_device(b), nl, dk, out, 2.0**40, 2.0**40)
+        assert scale == 2.0**80 / o.q[nl - 1]
+        ref = o.rescale(o.hmult(a, b, key))
+        assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), ref), "hmult_rescale differs at nl=%d" % nl
+
+
 def test_galois_and_psi(pair):
     P, g, o = pair
     for i in range(len(o.primes)):
