@@ -9,6 +9,8 @@ at ragged levels; a logN=12 set with the most primes a context takes (48 q +
 covers the generic paths.  Keys are uniform residues (parity does not depend on key
 structure); decryption through real keys is checked separately.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -197,6 +199,17 @@ def test_argument_errors(pair):
         g.ntt(d, len(o.primes), 1)
     with pytest.raises(ValueError):
         g.ntt(d, 0, 3)
+    # fused HMult+Rescale: one limb cannot be rescaled; the ABI checks the
+    # output level before queueing anything
+    key = torch.zeros(g.key_words(), dtype=torch.int64, device="cuda")
+    with pytest.raises(FidesError) as e:
+        g.hmult_rescale(d, d, 1, key, d)
+    assert e.value.code == -1
+    from paper_2507_04775_gb300 import fides as F
+    ct = F.fides_ct(d.data_ptr(), 2, 1.0)
+    bad = F.fides_ct(d.data_ptr(), 2, 0.0)      # out must have n_limbs - 1 = 1 limb
+    rc = F.lib().fides_hmult_rescale(g._h, ctypes.byref(ct), ctypes.byref(ct), key.data_ptr(), ctypes.byref(bad), None)
+    assert rc == -1
 
 
 def test_decrypts_through_gpu_with_real_keys():
