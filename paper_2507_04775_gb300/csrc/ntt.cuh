@@ -35,13 +35,15 @@
 // 4 rho - a uses 2^s + (X << (3 - a)) + (r >> (a + 1)).  X collects the bits of
 // the global index above the round's bits (the row for row passes).
 //
-// Arithmetic is lazy (Harvey): forward values stay in [0, 4q) between
-// stages, inverse values in [0, 2q); primes are below 2^61, so 4q < 2^63.
-// Each butterfly costs one Shoup product and one conditional subtraction.
+// Arithmetic is lazy (Harvey): forward values stay in [0, 6q) at round
+// boundaries and [0, 8q) in between (one conditional subtraction every other
+// stage), inverse values in [0, 2q); primes are below 2^61, so 8q < 2^64.
+// Each butterfly costs one Shoup product, and at most one conditional
+// subtraction.
 // Prologue and epilogue functors let callers fuse element-wise work into the
 // first load and the last store (Sec. III-F5 "Operation Fusions"); epilogues
 // receive values in [0, 2q), except the raw intermediate store of a forward
-// column pass, which keeps [0, 4q) (the row pass accepts it).
+// column pass, which keeps [0, 6q) (the row pass accepts it).
 #pragma once
 
 #include "fides_internal.cuh"
@@ -52,10 +54,15 @@ __device__ __forceinline__ int kmap(int u, int r, int b)
     return ((u >> b) << (b + 4)) | (r << b) | (u & ((1 << b) - 1));
 }
 
-// Forward butterfly: x, y in [0, 4q) -> x + w y, x - w y in [0, 4q).
-__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, u64 q2)
+// Forward butterfly, reducing x on every other stage only (red): with
+// t = w y in [0, 2q), a reducing stage maps inputs in [0, 8q) to [0, 6q)
+// (x -> csub(x, 4q) in [0, 4q)), a skipping one maps [0, 6q) to [0, 8q);
+// 8q < 2^64 for primes below 2^61, and the Shoup product takes any 64-bit
+// input.  Rounds start and end on [0, 6q).
+// (red is a constant once the stage loop is unrolled)
+__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, u64 q2, u64 q4, bool red)
 {
-    u64 a = csub(x, q2);                  // [0, 2q)
+    u64 a = red ? csub(x, q4) : x;
     u64 t = mul_shoup(y, w, q);           // [0, 2q)
     x = a + t;
     y = a + q2 - t;
@@ -138,7 +145,7 @@ struct ProPrep {
 // Each epilogue has a load step (the global reads it needs for element j) and
 // a store step, so that the kernel can issue the loads of several elements
 // before computing any of them.
-// intermediate store of the first pass (raw: forward values stay in [0, 4q))
+// intermediate store of the first pass (raw: forward values stay in [0, 6q))
 struct EpiLazy {
     static constexpr bool kRaw = true;
     __device__ __forceinline__ void load(const Job &, u32, u64 &, u64 &) const {}
@@ -243,6 +250,7 @@ template <bool INV, int S0, int S, int B, int A0, bool TWS>
 __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__restrict__ tw,
                                           const TwPair *stw, u64 q, u64 q2)
 {
+    const u64 q4 = 2 * q2;
 #pragma unroll
     for (int a = A0; a < 4; ++a) {
         const int s = INV ? S0 + S - 1 - B - a : S0 + (S - 4 - B) + a;
@@ -254,7 +262,7 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__r
             const int idx = base + (INV ? (r >> (a + 1)) : (r >> (4 - a)));
             const TwPair w = TWS ? stw[idx] : tw[idx];
             if (INV) gs_bfly(x[r], x[r + h], w, q, q2);
-            else ct_bfly(x[r], x[r + h], w, q, q2);
+            else ct_bfly(x[r], x[r + h], w, q, q2, q4, (a & 1) != 0);   // stages a = 1, 3 reduce
         }
     }
 }
@@ -368,7 +376,7 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     // ---------------- store ----------------
     if (!INV && !Epi::kRaw) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = csub(x[r], q2);      // [0, 4q) -> [0, 2q)
+        for (int r = 0; r < 16; ++r) x[r] = csub(csub(x[r], 2 * q2), q2);   // [0, 6q) -> [0, 2q)
     }
     if (NINV) {
         // N^-1, or the segment's combined constant (N^-1 times the qhat^-1 of
