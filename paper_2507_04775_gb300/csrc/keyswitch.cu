@@ -236,6 +236,8 @@ int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uin
     if (b->n_limbs != nl || out->n_limbs != nl)
         return fides_set_error(FIDES_ERR_ARG, "fides_hmult: level mismatch (%d, %d, %d)", nl, b->n_limbs,
                                out->n_limbs);
+    if (out->data == a->data || out->data == b->data)
+        return fides_set_error(FIDES_ERR_ARG, "fides_hmult: out may not alias a or b");
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult", st);
@@ -274,6 +276,8 @@ int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     if (nl < 2 || b->n_limbs != nl || out->n_limbs != l)
         return fides_set_error(FIDES_ERR_ARG, "%s: needs n_limbs >= 2, equal input levels and out->n_limbs = n_limbs - 1",
                                fn);
+    if (out->data == a->data || out->data == b->data)
+        return fides_set_error(FIDES_ERR_ARG, "%s: out may not alias a or b", fn);
     const size_t N = c->N, S = (size_t)nl * N, ne = (size_t)nl + c->K;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult_rescale", st);
@@ -325,6 +329,7 @@ static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_
     const int nl = a->n_limbs;
     if (int rc = check_level(c, nl, fn)) return rc;
     if (out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "%s: level mismatch", fn);
+    if (out->data == a->data) return fides_set_error(FIDES_ERR_ARG, "%s: out may not alias a", fn);
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op(trace, st);

@@ -46,6 +46,8 @@
 // column pass, which keeps [0, 6q) (the row pass accepts it).
 #pragma once
 
+#include <type_traits>
+
 #include "fides_internal.cuh"
 
 // k with its four bits [b, b+3] set to r and the other bits taken from u
@@ -114,30 +116,54 @@ struct ProRaise {
 //   2: HRotate automorphism sigma_g in evaluation form (Sec. III-F1):
 //      sigma_g(a)[j] = a[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)]; sigma_g(c0)
 //      goes to out, sigma_g(c1) to side, and sigma_g(c1) is transformed.
+// A prologue in two steps, so that the kernel can issue the loads of several
+// elements before it computes and stores any of them (each call reads up to
+// four words and stores up to three): load() reads what element j needs,
+// apply() computes, stores the side outputs and returns the value.  The
+// operands go through the read-only path (outputs may not alias inputs).
 struct ProPrep {
     int logN;
-    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
+    __device__ __forceinline__ void load(const Job &J, u32 j, u64 (&v)[4]) const
     {
-        if (J.mode == 0) return J.src[j];
+        const size_t S = (size_t)J.pstride;
+        if (J.mode == 0) {
+            v[0] = __ldg(J.src + j);
+        } else if (J.mode == 1) {
+            v[0] = __ldg(J.src + j);
+            v[1] = __ldg(J.src + S + j);
+            v[2] = __ldg(J.aux + j);
+            v[3] = __ldg(J.aux + S + j);
+        } else {
+            const u32 rj = __brev(j) >> (32 - logN);
+            const u64 e = ((2 * (u64)rj + 1) * J.g) & ((2ull << logN) - 1);
+            const u32 src = __brev((u32)((e - 1) >> 1)) >> (32 - logN);
+            v[0] = __ldg(J.src + src);
+            v[1] = __ldg(J.src + S + src);
+        }
+    }
+    __device__ __forceinline__ u64 apply(const Job &J, u32 j, const u64 (&v)[4], const PrimeInfo &p) const
+    {
+        if (J.mode == 0) return v[0];
         const size_t S = (size_t)J.pstride;
         if (J.mode == 1) {
-            const u64 a0 = J.src[j], a1 = J.src[S + j], b0 = J.aux[j], b1 = J.aux[S + j];
-            J.out[j] = mul_mod(a0, b0, p);
+            J.out[j] = mul_mod(v[0], v[2], p);
             U128 m = {0, 0};
-            mac128(m, a0, b1);
-            mac128(m, a1, b0);
+            mac128(m, v[0], v[3]);
+            mac128(m, v[1], v[2]);
             J.out[S + j] = reduce128(m.hi, m.lo, p);
-            const u64 d2 = mul_mod(a1, b1, p);
+            const u64 d2 = mul_mod(v[1], v[3], p);
             J.side[j] = d2;
             return d2;
         }
-        const u32 rj = __brev(j) >> (32 - logN);
-        const u64 e = ((2 * (u64)rj + 1) * J.g) & ((2ull << logN) - 1);
-        const u32 src = __brev((u32)((e - 1) >> 1)) >> (32 - logN);
-        J.out[j] = J.src[src];
-        const u64 v = J.src[S + src];
-        J.side[j] = v;
-        return v;
+        J.out[j] = v[0];
+        J.side[j] = v[1];
+        return v[1];
+    }
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
+    {
+        u64 v[4];
+        load(J, j, v);
+        return apply(J, j, v, p);
     }
 };
 
@@ -342,6 +368,28 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = pro(J, gidx(cbase, kmap(u, r, b0)), pr);
         if (TWS) __syncthreads();
+    } else if constexpr (std::is_same<Pro, ProPrep>::value) {
+        // four elements' loads in flight before any of them is computed
+#pragma unroll
+        for (int g = 0; g < 16; g += 4) {
+            u32 jj[4];
+            int ww[4];
+            u64 v[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = t + THREADS * (g + i);
+                const int cc = e >> S, k = e & ((1 << S) - 1);
+                const int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
+                jj[i] = gidx(cb, k);
+                ww[i] = widx(cc, k);
+                pro.load(J, jj[i], v[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sm[ww[i]] = pro.apply(J, jj[i], v[i], pr);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, 0))];
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
