@@ -204,10 +204,14 @@ def launch_model(nl, K, alpha, N, bconv="k_bconv_tc"):
                   2 * W * limbs + extra_bytes, half_bfly * limbs + extra_mm + (N * limbs if ninv else 0)))
 
     def keyswitch(mode0, mode1, prep):
-        # ModUp INTT; its first pass also prepares d (HMult: reads a, b and
-        # writes d0, d1, d2 with 4 products; HRotate: gathers c0, c1 and
-        # writes sigma(c0), sigma(c1))
-        fb, fm = (6 * W * nl, 4 * N * nl) if prep == "tensor" else (3 * W * nl, 0)
+        # HMult: the tensor product as its own pass (reads a, b, writes d0,
+        # d1, d2 with 4 products), then a plain ModUp INTT of d2.  HRotate:
+        # the INTT's first pass gathers c0, c1 and writes sigma(c0), sigma(c1)
+        if prep == "tensor":
+            L.append(("k_tensor", 7 * W * nl, 4 * N * nl))
+            fb, fm = 0, 0
+        else:
+            fb, fm = 3 * W * nl, 0
         ntt("inv", nl, ninv=True, first_bytes=fb, first_mm=fm)
         ntgt = beta * ne - nl
         L.append((bconv, W * (nl + ntgt), N * sum(min(alpha, nl - j * alpha) * (ne - min(alpha, nl - j * alpha)) for j in range(beta))))
