@@ -10,9 +10,10 @@
 // the product of a [coefficients x 8 ns] byte matrix with a [8 ns x 8 nd] byte
 // matrix.  Bytes are exact in fp16 and every partial sum is an integer below
 // 8 * 16 * 255^2 < 2^23 (2^24 with the offset below), exact in the fp32
-// accumulator whatever the order of the additions, so the MMA gives D exactly.  The epilogue folds the eight
-// sums of a target into a value below 2^80 and reduces it mod p_t.  The
-// result equals the integer kernel's (both are canonical residues).
+// accumulator whatever the order of the additions, so the MMA gives D
+// exactly.  The epilogue folds the eight sums of a target into a value below
+// 2^80 and reduces it to [0, 4p_t), the range the forward NTT that follows
+// takes; after that NTT the residues equal the integer kernel's.
 //
 // Persistent CTAs of 512 threads, each on one job with the job's matrix image
 // resident in shared memory (one bulk TMA copy, completing on an mbarrier) and
@@ -20,12 +21,14 @@
 // tiles of 128 coefficients (M = 128) round robin.  Per tile:
 //   1. every thread writes the bytes of its prefetched source words (row m,
 //      sources s0, s0 + 4, ...), as fp16, into the A operand;
-//   2. thread 0 issues ns/2 MMAs (K = 16: two sources each) per 32 targets
-//      (N = 8 targets <= 256 per instruction) and commits them to an mbarrier;
-//   3. every thread issues the loads of its words of the next tile, waits for
-//      the MMAs, and reads accumulator lanes 32 (w mod 4) .. +31 (tcgen05.ld)
-//      for a quarter of the targets, reduces and stores (coalesced 256-byte
-//      rows).  Two CTAs per SM overlap one's MMAs with the other's epilogue.
+//   2. thread 0 issues nsp/2 MMAs (K = 16: two columns of sources each) per
+//      32 targets (N = 8 targets <= 256 per instruction) and commits them to
+//      an mbarrier;
+//   3. every thread issues the loads of its words of the next tile; thread 0
+//      polls the mbarrier while the others wait at the CTA barrier; then
+//      warp w reads accumulator lanes 32 (w mod 4) .. +31 (tcgen05.ld) for a
+//      quarter of the targets, reduces and stores (coalesced 256-byte rows).
+//      Two CTAs per SM overlap one's MMAs with the other's epilogue.
 // Operand layout (K-major, no swizzle): 8-row x 16-byte core matrices, row r
 // of a core matrix at +16 r; core matrices adjacent along K (one source: its
 // eight bytes) 128 bytes apart (leading byte offset), adjacent 8-row groups

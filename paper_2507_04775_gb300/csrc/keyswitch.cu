@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(256) k_tensor(const u64 *__restrict__ a, const
     for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < half; w += (size_t)gridDim.x * blockDim.x) {
         const size_t i = 2 * w;
         const PrimeInfo p = P[i >> logN];
-        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(a + i), a1 = *reinterpret_cast<const ulonglong2 *>(a + S + i);
-        const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b + i), b1 = *reinterpret_cast<const ulonglong2 *>(b + S + i);
+        auto ld = [](const u64 *q) { return *reinterpret_cast<const ulonglong2 *>(q); };
+        const ulonglong2 a0 = ld(a + i), a1 = ld(a + S + i), b0 = ld(b + i), b1 = ld(b + S + i);
         U128 mx = {0, 0}, my = {0, 0};
         mac128(mx, a0.x, b1.x);
         mac128(mx, a1.x, b0.x);
@@ -319,8 +319,8 @@ int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     const int nl = a->n_limbs, l = nl - 1;
     if (int rc = check_level(c, nl, fn)) return rc;
     if (nl < 2 || b->n_limbs != nl || out->n_limbs != l)
-        return fides_set_error(FIDES_ERR_ARG, "%s: needs n_limbs >= 2, equal input levels and out->n_limbs = n_limbs - 1",
-                               fn);
+        return fides_set_error(FIDES_ERR_ARG,
+                               "%s: needs n_limbs >= 2, equal input levels and out->n_limbs = n_limbs - 1", fn);
     if (out->data == a->data || out->data == b->data)
         return fides_set_error(FIDES_ERR_ARG, "%s: out may not alias a or b", fn);
     const size_t N = c->N, S = (size_t)nl * N, ne = (size_t)nl + c->K;
