@@ -923,8 +923,10 @@ def sources_sha(kernel: str = "k_ntt") -> str:
 def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     """Same steps through the public API with host buffers: every step copies
     its input pair from pinned host memory and reads its three results back.
-    Copies run on their own streams, double-buffered, so the input copy of
-    step k+1 and the output copy of step k-1 overlap the compute of step k."""
+    Copies run on their own streams over three buffer slots, so the input copy
+    of step k+1 and the output copy of step k-1 overlap the compute of step k
+    (the input copy of a slot waits only for the output copy of three steps
+    before)."""
     import torch
     steps = max(5, min(args.steps, 50))
     hA = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in A]
@@ -935,7 +937,8 @@ def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
 
     w_in, w_rs = 2 * nl * N, 2 * (nl - 1) * N
     slots = []
-    for _ in range(2):
+    NSLOT = 3
+    for _ in range(NSLOT):
         slots.append({"a": dev(w_in), "b": dev(w_in), "m": dev(w_in), "r": dev(w_in), "s": dev(w_rs),
                       "hm": torch.empty(w_in, dtype=torch.int64).pin_memory(),
                       "hr": torch.empty(w_in, dtype=torch.int64).pin_memory(),
@@ -944,9 +947,9 @@ def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     comp, h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
     def step(k):
-        sl, i = slots[k % 2], k % POOL
+        sl, i = slots[k % NSLOT], k % POOL
         with torch.cuda.stream(h2d):
-            h2d.wait_event(sl["drained"])          # outputs of step k-2 copied out, inputs consumed
+            h2d.wait_event(sl["drained"])          # outputs of step k-3 copied out, inputs consumed
             sl["a"].copy_(hA[i], non_blocking=True)
             sl["b"].copy_(hB[i], non_blocking=True)
             sl["in_ready"].record(h2d)
@@ -982,7 +985,7 @@ def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     return {"value": round(2 * steps * world / (ms / 1e3), 2), "unit": "ops/s", "steps": steps,
             "h2d_bytes_per_step": 2 * hA[0].numel() * 8,
             "d2h_bytes_per_step": (2 * w_in + w_rs) * 8,
-            "pipelined": "input copies, compute and result copies on three streams, two buffers deep"}
+            "pipelined": "input copies, compute and result copies on three streams, three buffers deep"}
 
 
 # ---------------------------------------------------------------------------
