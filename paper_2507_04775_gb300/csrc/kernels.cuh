@@ -426,6 +426,78 @@ inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, in
 }
 
 // ---------------------------------------------------------------------------
+// Tensor product of HMult (Table I) in evaluation form, as its own pass:
+// d0 = a0 b0 and d1 = a0 b1 + a1 b0 into out, d2 = a1 b1 into d2 (the
+// key-switch input), two words per thread with 16-byte accesses.  The pass is
+// bound by HBM (four words read, three written per coefficient); the INTT of
+// d2 that follows runs without a prologue.  One op inline, or a device table
+// of ops with exclusive prefix sums of their limb counts (grid.y = the total).
+// ---------------------------------------------------------------------------
+struct TensorOp {
+    const u64 *a, *b;   // [2][nl][N]
+    u64 *out;           // [2][nl][N]: d0, d1
+    u64 *d2;            // [nl][N]
+    int nl;
+};
+
+struct TensorArgs {
+    const TensorOp *dop;
+    const int *dpre;
+    int nop;
+    TensorOp one;
+};
+
+__device__ __forceinline__ void tensor_body(const TensorOp &o, int limb, const PrimeInfo *__restrict__ P, int logN)
+{
+    const size_t S = (size_t)o.nl << logN;
+    const size_t i = ((size_t)limb << logN) + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const PrimeInfo p = P[limb];
+    auto ld = [](const u64 *q) { return *reinterpret_cast<const ulonglong2 *>(q); };
+    const ulonglong2 a0 = ld(o.a + i), a1 = ld(o.a + S + i), b0 = ld(o.b + i), b1 = ld(o.b + S + i);
+    Acc128 mx = {0, 0, 0, 0}, my = {0, 0, 0, 0};
+    mac_wide(mx, a0.x, b1.x);
+    mac_wide(mx, a1.x, b0.x);
+    mac_wide(my, a0.y, b1.y);
+    mac_wide(my, a1.y, b0.y);
+    *reinterpret_cast<ulonglong2 *>(o.out + i) = make_ulonglong2(mul_mod(a0.x, b0.x, p), mul_mod(a0.y, b0.y, p));
+    *reinterpret_cast<ulonglong2 *>(o.out + S + i) = make_ulonglong2(reduce_acc(mx, p), reduce_acc(my, p));
+    *reinterpret_cast<ulonglong2 *>(o.d2 + i) = make_ulonglong2(mul_mod(a1.x, b1.x, p), mul_mod(a1.y, b1.y, p));
+}
+
+__global__ void __launch_bounds__(256) k_tensor(TensorArgs A, const PrimeInfo *__restrict__ P, int logN)
+{
+    pdl_enter();
+    const int z = blockIdx.y;
+    if (A.dop) {
+        const int k = find_op(A.dpre, A.nop, z);
+        tensor_body(A.dop[k], z - __ldg(A.dpre + k), P, logN);
+    } else {
+        tensor_body(A.one, z, P, logN);
+    }
+}
+
+// whether an HMult's tensor product can take the 16-byte pass
+inline bool tensor_pass_ok(const void *a, const void *b, const void *out, const void *d2)
+{
+    return ((((uintptr_t)a | (uintptr_t)b | (uintptr_t)out | (uintptr_t)d2) & 15) == 0);
+}
+
+inline int launch_tensor_args(const fides_ctx *c, const TensorArgs &A, int total_limbs, cudaStream_t st)
+{
+    FIDES_LAUNCH("k_tensor", st, k_tensor, dim3(c->N / 512, total_limbs), dim3(256), A, (const PrimeInfo *)c->d_prime,
+                 c->logN);
+    return fides_check_cuda(cudaGetLastError(), "tensor product");
+}
+
+inline int launch_tensor(const fides_ctx *c, const u64 *a, const u64 *b, u64 *out, u64 *d2, int nl, cudaStream_t st)
+{
+    TensorArgs A;
+    memset(&A, 0, sizeof(A));
+    A.one = TensorOp{a, b, out, d2, nl};
+    return launch_tensor_args(c, A, nl, st);
+}
+
+// ---------------------------------------------------------------------------
 // Limb-set helpers
 // ---------------------------------------------------------------------------
 inline Seg seg_of(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux = nullptr, u64 *out = nullptr,

@@ -34,47 +34,6 @@ Scratch carve(const fides_ctx *c, u64 *ws)
     return s;
 }
 
-// Tensor product of HMult in evaluation form, as its own pass over the words:
-// d0 = a0 b0 and d1 = a0 b1 + a1 b0 into out, d2 = a1 b1 into d2 (the
-// key-switch input), two words per thread with 16-byte accesses.  The pass is
-// bound by HBM (four words read, three written per coefficient); the INTT of
-// d2 that follows runs without a prologue.
-__global__ void __launch_bounds__(256) k_tensor(const u64 *__restrict__ a, const u64 *__restrict__ b,
-                                                u64 *__restrict__ out, u64 *__restrict__ d2, int nl, int logN,
-                                                const PrimeInfo *__restrict__ P)
-{
-    pdl_enter();
-    const size_t S = (size_t)nl << logN, half = S / 2;
-    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < half; w += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = 2 * w;
-        const PrimeInfo p = P[i >> logN];
-        auto ld = [](const u64 *q) { return *reinterpret_cast<const ulonglong2 *>(q); };
-        const ulonglong2 a0 = ld(a + i), a1 = ld(a + S + i), b0 = ld(b + i), b1 = ld(b + S + i);
-        U128 mx = {0, 0}, my = {0, 0};
-        mac128(mx, a0.x, b1.x);
-        mac128(mx, a1.x, b0.x);
-        mac128(my, a0.y, b1.y);
-        mac128(my, a1.y, b0.y);
-        *reinterpret_cast<ulonglong2 *>(out + i) = make_ulonglong2(mul_mod(a0.x, b0.x, p), mul_mod(a0.y, b0.y, p));
-        *reinterpret_cast<ulonglong2 *>(out + S + i) =
-            make_ulonglong2(reduce128(mx.hi, mx.lo, p), reduce128(my.hi, my.lo, p));
-        *reinterpret_cast<ulonglong2 *>(d2 + i) = make_ulonglong2(mul_mod(a1.x, b1.x, p), mul_mod(a1.y, b1.y, p));
-    }
-}
-
-// whether the tensor product can take its own 16-byte pass
-bool tensor_pass_ok(const void *a, const void *b, const void *out, const void *d2)
-{
-    return ((((uintptr_t)a | (uintptr_t)b | (uintptr_t)out | (uintptr_t)d2) & 15) == 0);
-}
-
-int launch_tensor(const fides_ctx *c, const u64 *a, const u64 *b, u64 *out, u64 *d2, int nl, cudaStream_t st)
-{
-    FIDES_LAUNCH("k_tensor", st, k_tensor, dim3(c->sms * 8), dim3(256), a, b, out, d2, nl, c->logN,
-                 (const PrimeInfo *)c->d_prime);
-    return fides_check_cuda(cudaGetLastError(), "tensor product");
-}
-
 // HMult fused with Rescale: the coefficient form of the dropped limb l of the
 // HMult result, last_t = INTT(d_t,l) + P^-1 (INTT(acc_t,l) - conv_t,l) mod q_l
 // (canonical), for t = 0, 1; lastc = [INTT(d0), INTT(d1), INTT(acc0),

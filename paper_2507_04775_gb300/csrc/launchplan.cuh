@@ -14,7 +14,7 @@
 
 namespace {
 
-enum LaunchKind { L_INTT, L_BCONV, L_NTT, L_INNER, L_NTT_SUBMUL, L_NTT_SWITCH_SUBMUL };
+enum LaunchKind { L_INTT, L_BCONV, L_NTT, L_INNER, L_NTT_SUBMUL, L_NTT_SWITCH_SUBMUL, L_TENSOR };
 
 struct Launch {
     LaunchKind kind;
@@ -24,14 +24,15 @@ struct Launch {
     IPArgs ip;         // L_INNER
     int max_beta;      // L_INNER
     int ip_pairs;      // L_INNER: every op can take the paired path
-    int total;         // grid.y of L_INNER
+    int total;         // grid.y of L_INNER and L_TENSOR
+    TensorArgs tp;     // L_TENSOR (device ops)
 };
 
 // Table references: a launch records the offset of each of its tables in the
 // table image; the device addresses are patched in once the image has a home.
 struct Pending {
     int launch;
-    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.dpre
+    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.dpre, 5: tp.dop, 6: tp.dpre
     size_t off;
 };
 
@@ -119,6 +120,23 @@ void plan_inner(Plan &P, const std::vector<IPOp> &ops, const std::vector<int> &r
     P.pend.push_back(Pending{id, 4, P.add(pre.data(), sizeof(int) * pre.size())});
 }
 
+void plan_tensor(Plan &P, const std::vector<TensorOp> &ops)
+{
+    if (ops.empty()) return;
+    Launch l;
+    memset(&l, 0, sizeof(l));
+    l.kind = L_TENSOR;
+    std::vector<int> pre(ops.size());
+    int tot = 0;
+    for (size_t i = 0; i < ops.size(); ++i) { pre[i] = tot; tot += ops[i].nl; }
+    l.total = tot;
+    l.tp.nop = (int)ops.size();
+    P.launches.push_back(l);
+    const int id = (int)P.launches.size() - 1;
+    P.pend.push_back(Pending{id, 5, P.add(ops.data(), sizeof(TensorOp) * ops.size())});
+    P.pend.push_back(Pending{id, 6, P.add(pre.data(), sizeof(int) * pre.size())});
+}
+
 // Checks one operation's descriptor (levels, buffers, key); `fn` names the
 // caller in the error message.
 int plan_validate(const fides_ctx *c, const fides_op &o, int i, const char *fn)
@@ -162,6 +180,7 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
     std::vector<BConvJob> up, down;
     std::vector<IPOp> ip;
     std::vector<int> ip_rows;
+    std::vector<TensorOp> tens;
     for (int i = 0; i < n_ops; ++i) {
         fides_op &o = ops[i];
         if (o.stage != stage) continue;
@@ -181,10 +200,14 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
         B.d = dsrc; B.nl = nl; B.evk = o.key;
         B.out0 = o.out.data; B.out1 = o.out.data + S;
         B.mode0 = 1; B.mode1 = hm ? 1 : 0;
-        B.prep = hm ? 1 : 2;
-        B.pa = o.a.data;
-        B.pb = hm ? o.b.data : nullptr;
-        B.pout = o.out.data;
+        if (hm && tensor_pass_ok(o.a.data, o.b.data, o.out.data, dsrc)) {
+            tens.push_back(TensorOp{o.a.data, o.b.data, o.out.data, dsrc, nl});   // d2 in dsrc, plain INTT
+        } else {
+            B.prep = hm ? 1 : 2;
+            B.pa = o.a.data;
+            B.pb = hm ? o.b.data : nullptr;
+            B.pout = o.out.data;
+        }
         B.g = hm ? 0 : fides_galois_elt(c, o.steps);
         ks_carve(c, B, dsrc + S);
         ks_intt_segs(c, B, intt);
@@ -197,6 +220,7 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
         ks_final_segs(c, B, fin);
         o.out.scale = hm ? o.a.scale * o.b.scale : o.a.scale;
     }
+    plan_tensor(P, tens);
     plan_ntt(P, L_INTT, intt);
     plan_bconv(P, up);
     plan_ntt(P, L_NTT, ntt);
@@ -219,6 +243,8 @@ void plan_patch(Plan &P, unsigned char *dmem)
         case 2: l.bc.djob = (const BConvJob *)a; break;
         case 3: l.ip.dop = (const IPOp *)a; break;
         case 4: l.ip.dpre = (const int *)a; break;
+        case 5: l.tp.dop = (const TensorOp *)a; break;
+        case 6: l.tp.dpre = (const int *)a; break;
         }
     }
 }
@@ -234,6 +260,7 @@ int plan_run(const fides_ctx *c, const std::vector<Launch> &launches, cudaStream
         case L_NTT_SWITCH_SUBMUL: rc = ntt_forward(c, l.set, ProSwitchMod{}, EpiSubMul{}, st); break;
         case L_BCONV: rc = launch_bconv_group(c, l.bc, l.ns, l.max_dst, st); break;
         case L_INNER: rc = launch_inner(c, l.ip, l.total, l.max_beta, st, l.ip_pairs); break;
+        case L_TENSOR: rc = launch_tensor_args(c, l.tp, l.total, st); break;
         }
         if (rc) return rc;
     }
