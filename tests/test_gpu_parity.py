@@ -164,6 +164,29 @@ def test_rescale(pair):
         assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), o.rescale(a)), "rescale differs at nl=%d" % nl
 
 
+def test_hmult_on_8_byte_aligned_buffers(pair):
+    """Buffers that are only 8-byte aligned take the tensor product fused into
+    the first INTT pass instead of its own 16-byte pass; the residues are the
+    same."""
+    P, g, o = pair
+    st = si.Stream(1012, 13)
+    key = rand_key(st, o)
+    dk = to_device(key)
+    nl = P.nq
+    a, b = rand_poly(st, o.q[:nl], o.N, 2), rand_poly(st, o.q[:nl], o.N, 2)
+    w = 2 * nl * o.N
+    pool = torch.zeros(3 * w + 5, dtype=torch.int64, device="cuda")
+    da, db, out = pool[1:1 + w], pool[w + 3:2 * w + 3], pool[2 * w + 5:3 * w + 5]   # odd word offsets
+    da.copy_(to_device(a).reshape(-1))
+    db.copy_(to_device(b).reshape(-1))
+    g.hmult(da, db, nl, dk, out)
+    ref = o.hmult(a, b, key)
+    assert np.array_equal(to_host(out).reshape(ref.shape), ref)
+    out2 = torch.zeros(2 * (nl - 1) * o.N + 1, dtype=torch.int64, device="cuda")[1:]
+    g.hmult_rescale(da, db, nl, dk, out2)
+    assert np.array_equal(to_host(out2).reshape(2, nl - 1, o.N), o.rescale(ref))
+
+
 def test_hmult_rescale(pair):
     """The fused HMult+Rescale against the oracle's HMult then Rescale, at
     every level the other tests use (2 and up); the plain HMult on the same
