@@ -81,6 +81,7 @@ def lib():
         L.or_automorph_eval.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, ctypes.c_uint64]
         L.or_rotate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int64, _u64p, _u64p]
         L.or_rescale.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
+        L.or_rescale_round.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
         L.or_automorph_ct.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_uint64, _u64p, _u64p]
         L.or_conjugate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p, _u64p]
         L.or_rotate_hoisted.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _u64p,
@@ -305,10 +306,12 @@ class Context:
     def scalar_mult(self, a, k) -> np.ndarray:
         return self._ct_op("or_scalar_mult", a, k)
 
-    def rescale(self, a) -> np.ndarray:
+    def rescale(self, a, nearest: bool = False) -> np.ndarray:
+        """Rescale by the last prime: floor(x / q_l), or round(x / q_l) with nearest."""
         a = _u64(a); nl = a.shape[1]
         out = np.empty((2, nl - 1, self.N), dtype=np.uint64)
-        lib().or_rescale(self._h, _p(a), nl, _p(out)); return out
+        fn = lib().or_rescale_round if nearest else lib().or_rescale
+        fn(self._h, _p(a), nl, _p(out)); return out
 
     # client side
     def from_signed(self, v, pidx) -> np.ndarray:

@@ -822,11 +822,15 @@ int or_linear_transform(const or_ctx *c, const u64 *a, int nl, int n_diag, const
 
 /*
  * Rescale (Table I; Sec. III-F5 "Rescale fusion"): with l = nl - 1, INTT limb
- * l, take its canonical [0, q_l) representative modulo each q_i (SwitchModulo),
- * NTT under q_i, and return q_l^-1 (x_i - that) mod q_i for i < l.
+ * l, take a representative of each of its coefficients modulo each q_i
+ * (SwitchModulo), NTT under q_i, and return q_l^-1 (x_i - that) mod q_i for
+ * i < l.  Floor (or_rescale): the canonical representative r in [0, q_l), so
+ * the result is floor(x / q_l).  Nearest (or_rescale_round): the centred one,
+ * r - q_l when r > (q_l - 1) / 2, so the result is round(x / q_l) (q_l odd:
+ * no ties).
  * a: [2][nl][N] -> out: [2][nl-1][N].
  */
-void or_rescale(const or_ctx *c, const u64 *a, int nl, u64 *out)
+static void rescale_impl(const or_ctx *c, const u64 *a, int nl, u64 *out, int nearest)
 {
     u64 N = c->N;
     int l = nl - 1;
@@ -841,7 +845,13 @@ void or_rescale(const or_ctx *c, const u64 *a, int nl, u64 *out)
         for (int i = 0; i < l; i++) {
             u64 q = c->primes[i];
             u64 *y = (u64 *)malloc(sizeof(u64) * N);
-            for (u64 n = 0; n < N; n++) y[n] = last[n] % q;
+            for (u64 n = 0; n < N; n++) {
+                u64 r = last[n];
+                if (nearest && r > (ql - 1) / 2)
+                    y[n] = sub_mod(0, (ql - r) % q, q);   /* r - q_l, a negative integer, mod q */
+                else
+                    y[n] = r % q;
+            }
             or_ntt(c, i, y);
             u64 qinv = inv_mod(ql % q, q);
             for (u64 n = 0; n < N; n++)
@@ -851,6 +861,9 @@ void or_rescale(const or_ctx *c, const u64 *a, int nl, u64 *out)
         free(last);
     }
 }
+
+void or_rescale(const or_ctx *c, const u64 *a, int nl, u64 *out) { rescale_impl(c, a, nl, out, 0); }
+void or_rescale_round(const or_ctx *c, const u64 *a, int nl, u64 *out) { rescale_impl(c, a, nl, out, 1); }
 
 /* ------------------------------------------------------------------------
  * Client side (KeyGen / Encrypt / Decrypt are OpenFHE's job in the paper,

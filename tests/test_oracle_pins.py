@@ -260,6 +260,39 @@ def test_rescale_is_exact_floor(mid):
         assert O == [x // ql for x in X]
 
 
+def test_rescale_nearest_is_exact_round(mid):
+    """Round-to-nearest Rescale: round(x / q_l) = floor((2x + q_l) / (2 q_l))
+    (q_l odd, so no ties), reduced mod Q_{l-1} (x just below Q_l rounds up to
+    Q_{l-1} = 0), on random x and on x whose remainder mod q_l sits at the
+    rounding boundary ((q_l -+ 1) / 2), at 0 and at q_l - 1."""
+    nl = 9
+    ql = mid.q[nl - 1]
+    Ql, Ql1 = 1, 1
+    for q in mid.q[:nl]:
+        Ql *= q
+    Ql1 = Ql // ql
+    rng = random.Random(19)
+    X = [[rng.randrange(Ql) for _ in range(mid.N)] for _ in range(2)]
+    edges = [0, 1, (ql - 1) // 2, (ql + 1) // 2, ql - 1]
+    for n in range(0, mid.N, 3):
+        k = rng.randrange(Ql1)
+        X[0][n] = k * ql + edges[(n // 3) % len(edges)]
+    X[1][0], X[1][1], X[1][2] = Ql - 1, Ql - (ql - 1) // 2, Ql - (ql + 1) // 2
+    a = np.stack([mid.ntt_limbs(np.array([[x % q for x in Xp] for q in mid.q[:nl]], dtype=np.uint64),
+                                list(range(nl))) for Xp in X])
+    out = mid.rescale(a, nearest=True)
+    for poly in range(2):
+        O = oracle.crt(_coeff(mid, out[poly], list(range(nl - 1))), mid.q[:nl - 1])
+        assert O == [((2 * x + ql) // (2 * ql)) % Ql1 for x in X[poly]]
+    # floor and nearest differ exactly where the remainder passes (q_l - 1) / 2
+    fl = mid.rescale(a)
+    for poly in range(2):
+        F = oracle.crt(_coeff(mid, fl[poly], list(range(nl - 1))), mid.q[:nl - 1])
+        O = oracle.crt(_coeff(mid, out[poly], list(range(nl - 1))), mid.q[:nl - 1])
+        for x, f, o in zip(X[poly], F, O):
+            assert o == (f + (1 if x % ql > (ql - 1) // 2 else 0)) % Ql1
+
+
 # ---------------------------------------------------------------- automorphism
 def test_automorphism_coeff_is_substitution(tiny):
     N = tiny.N
