@@ -236,6 +236,16 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
 /*
+ * Rescale rounding to nearest instead of down: as fides_rescale, but
+ * SwitchModulo takes the centred representative of each coefficient r of
+ * INTT(x_l) (r - q_l when r > (q_l - 1) / 2), which gives round(x / q_l)
+ * limb-wise (q_l is odd, so there are no ties; a value just below Q_l rounds
+ * to Q_{l-1}, that is 0).  Same arguments, layout, errors and scale as
+ * fides_rescale.  The batched, program and server paths rescale by floor.
+ */
+int fides_rescale_round(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
+
+/*
  * HSquare (Table I): HMult+relin of a with itself, identical to
  * fides_hmult(ctx, a, a, rlk, out, stream).  out may not alias a.
  */

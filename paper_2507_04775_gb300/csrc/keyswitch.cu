@@ -434,30 +434,43 @@ int fides_rotate_hoisted_ws(fides_ctx *c, const fides_ct *a, int n_rot, const in
     return FIDES_OK;
 }
 
-extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
+// Rescale (Table I): floor(x / q_l), or round(x / q_l) with nearest (the
+// centred SwitchModulo of the dropped limb).
+static int rescale_entry(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws, bool nearest)
 {
-    return fides_rescale_ws(c, a, out, stream, nullptr);
-}
-
-int fides_rescale_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws)
-{
-    if (int rc = check_ctx(c, "fides_rescale")) return rc;
-    if (!a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "fides_rescale: NULL argument");
+    const char *fn = nearest ? "fides_rescale_round" : "fides_rescale";
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!a || !out || !a->data || !out->data) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
     const int nl = a->n_limbs;
-    if (int rc = check_level(c, nl, "fides_rescale")) return rc;
+    if (int rc = check_level(c, nl, fn)) return rc;
     if (nl < 2 || out->n_limbs != nl - 1)
-        return fides_set_error(FIDES_ERR_ARG, "fides_rescale: needs n_limbs >= 2 and out->n_limbs = n_limbs - 1");
+        return fides_set_error(FIDES_ERR_ARG, "%s: needs n_limbs >= 2 and out->n_limbs = n_limbs - 1", fn);
     cudaStream_t st = as_stream(stream);
-    OpTrace op("op_rescale", st);
+    OpTrace op(nearest ? "op_rescale_round" : "op_rescale", st);
     Scratch s = carve(c, ws);
     std::vector<Seg> v;
     rs_intt_segs(c, a->data, nl, s.last, v);
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
     v.clear();
-    rs_final_segs(c, a->data, nl, s.last, out->data, v);
+    rs_final_segs(c, a->data, nl, s.last, out->data, v, nearest);
     int rc = ntt_forward(c, inline_set(v), ProSwitchMod{}, EpiSubMul{}, st);
     if (!rc) out->scale = a->scale / (double)c->primes[nl - 1];
     return rc;
+}
+
+extern "C" int fides_rescale(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
+{
+    return fides_rescale_ws(c, a, out, stream, nullptr);
+}
+
+extern "C" int fides_rescale_round(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)
+{
+    return rescale_entry(c, a, out, stream, nullptr, true);
+}
+
+int fides_rescale_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws)
+{
+    return rescale_entry(c, a, out, stream, ws, false);
 }
 
 extern "C" int fides_modraise(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream)

@@ -85,11 +85,16 @@ struct ProSrc {
 struct ProDst {
     __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return J.dst[j]; }
 };
-// reduce a value of another prime's range (SwitchModulo of Rescale)
+// reduce a value of another prime's range (SwitchModulo of Rescale): the
+// canonical representative v in [0, q_l), or, when the segment's g holds q_l
+// (round-to-nearest Rescale), the centred one v - q_l for v > (q_l - 1) / 2.
 struct ProSwitchMod {
     __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
     {
-        return reduce64_lazy(J.src[j], p);
+        const u64 v = J.src[j];
+        u64 r = reduce64_lazy(v, p);                                     // [0, 2q)
+        if (J.g && v > (J.g >> 1)) r += p.q - csub(reduce64_lazy(J.g, p), p.q);   // v - q_l mod q, < 3q
+        return r;
     }
 };
 

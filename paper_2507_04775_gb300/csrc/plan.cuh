@@ -176,13 +176,18 @@ inline void rs_intt_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, st
     for (int t = 0; t < 2; ++t) v.push_back(seg_of(x + ((size_t)t * nl + nl - 1) * N, last + t * N, 1, nl - 1));
 }
 
-inline void rs_final_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, u64 *out, std::vector<Seg> &v)
+// nearest: round-to-nearest Rescale (the centred SwitchModulo, ProSwitchMod
+// with g = q_l) instead of floor.
+inline void rs_final_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, u64 *out, std::vector<Seg> &v,
+                          bool nearest = false)
 {
     const size_t N = c->N;
     const int l = nl - 1;
     for (int t = 0; t < 2; ++t) {
         u64 *o = out + (size_t)t * l * N;
-        v.push_back(seg_of(last + t * N, o, l, 0, x + (size_t)t * nl * N, o, 0, 0, c->d_rs_qlinv + (size_t)l * c->L));
+        Seg g = seg_of(last + t * N, o, l, 0, x + (size_t)t * nl * N, o, 0, 0, c->d_rs_qlinv + (size_t)l * c->L);
+        g.g = nearest ? c->primes[l] : 0;
+        v.push_back(g);
     }
 }
 

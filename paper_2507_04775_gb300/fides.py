@@ -37,7 +37,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ptadd", "fides_ptmult", "fides_scalar_add", "fides_scalar_mult", "fides_linear_transform",
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
            "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
-           "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale"]
+           "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale",
+           "fides_rescale_round"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -145,6 +146,7 @@ def lib():
         L.fides_hmult_rescale.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
         L.fides_rotate.argtypes = [_vp, ctp, ctypes.c_int64, _vp, ctp, _vp]
         L.fides_rescale.argtypes = [_vp, ctp, ctp, _vp]
+        L.fides_rescale_round.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_rescale_noalloc.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_trace_enable.argtypes = [_i]
         L.fides_trace_reset.restype = None
@@ -418,9 +420,11 @@ class Context:
                                   ctypes.byref(co), _stream(stream)))
         return co.scale
 
-    def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None) -> float:
+    def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None, nearest: bool = False) -> float:
+        """floor(x / q_l) limb-wise, or round(x / q_l) with nearest (fides_rescale_round)."""
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs - 1, 0.0, "out")
-        _check(lib().fides_rescale(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
+        fn = lib().fides_rescale_round if nearest else lib().fides_rescale
+        _check(fn(self._h, ctypes.byref(ca), ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def hsquare(self, a, n_limbs: int, rlk, out, scale: float = 1.0, stream=None) -> float:

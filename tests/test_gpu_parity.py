@@ -164,6 +164,28 @@ def test_rescale(pair):
         assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), o.rescale(a)), "rescale differs at nl=%d" % nl
 
 
+def test_rescale_round(pair):
+    """Round-to-nearest Rescale against the oracle's, with the dropped limb's
+    coefficients at the rounding boundary (q_l -+ 1) / 2, at 0, 1 and q_l - 1,
+    and random; the floor Rescale of the same input differs from it."""
+    P, g, o = pair
+    st = si.Stream(1013, 14)
+    for nl in sorted({P.nq, 2, max(2, P.nq // 2 + 1)}):
+        a = rand_poly(st, o.q[:nl], o.N, 2)
+        ql = o.q[nl - 1]
+        edges = np.array([0, 1, (ql - 1) // 2, (ql + 1) // 2, ql - 1], dtype=np.uint64)
+        for poly in range(2):
+            coef = o.intt(a[poly, nl - 1], nl - 1)
+            coef[::7] = np.resize(edges, coef[::7].shape)
+            a[poly, nl - 1] = o.ntt(coef, nl - 1)
+        out = torch.zeros(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+        scale = g.rescale(to_device(a), nl, out, 2.0**80, nearest=True)
+        assert scale == 2.0**80 / ql
+        want = o.rescale(a, nearest=True)
+        assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), want), "rescale_round differs at nl=%d" % nl
+        assert not np.array_equal(want, o.rescale(a))
+
+
 def test_hmult_on_8_byte_aligned_buffers(pair):
     """Buffers that are only 8-byte aligned take the tensor product fused into
     the first INTT pass instead of its own 16-byte pass; the residues are the
@@ -218,6 +240,9 @@ def test_argument_errors(pair):
     with pytest.raises(FidesError) as e:
         g.rescale(d, 1, d)
     assert e.value.code == -1
+    with pytest.raises(FidesError) as e:
+        g.rescale(d, 1, d, nearest=True)
+    assert e.value.code == -1
     with pytest.raises(FidesError):
         g.ntt(d, len(o.primes), 1)
     with pytest.raises(ValueError):
@@ -257,6 +282,10 @@ def test_decrypts_through_gpu_with_real_keys():
     s2 = g.rescale(out, nl, rs, s)
     err2 = np.max(np.abs(cl.decrypt(to_host(rs).reshape(2, nl - 1, o.N), s2) - ref)) / max(1.0, np.max(np.abs(ref)))
     assert err2 < 2.0**-20, err2
+    s3 = g.rescale(out, nl, rs, s, nearest=True)
+    assert s3 == s2
+    err2r = np.max(np.abs(cl.decrypt(to_host(rs).reshape(2, nl - 1, o.N), s3) - ref)) / max(1.0, np.max(np.abs(ref)))
+    assert err2r < 2.0**-20, err2r
     rot = torch.zeros_like(out)
     g.rotate(to_device(a), nl, 3, to_device(rk), rot)
     err3 = np.max(np.abs(cl.decrypt(to_host(rot).reshape(2, nl, o.N), 2.0**40) - np.roll(z1, -3)))
