@@ -437,6 +437,22 @@ def test_hrotate_decrypts_to_rotation(small, small_client):
     assert _rel_err(small_client.decrypt(o3, 2.0**40), np.roll(z, -3)) < 2.0**-20
 
 
+def test_rotation_by_half_the_ring_is_the_identity(small, small_client):
+    """5 has order N/2 modulo 2N, so a rotation by N/2 slots is sigma_1: the
+    Galois element is 1, the evaluation-form automorphism leaves every limb as
+    it is, and the ciphertext decrypts to the same slots."""
+    N = small.N
+    assert sympy.n_order(5, 2 * N) == N // 2
+    assert small.galois_elt(N // 2) == 1 and small.galois_elt(-(N // 2)) == 1
+    st = si.Stream(21)
+    a = si.uniform_poly(st, small.q, N)
+    assert np.array_equal(small.automorph_eval(a, 1), a)
+    z = small_client.random_slots()
+    ct = small_client.encrypt(z, small.nq, 2.0**40)
+    o = small.rotate(ct, N // 2, small_client.rotation_key(N // 2))
+    assert _rel_err(small_client.decrypt(o, 2.0**40), z) < 2.0**-20
+
+
 def test_lower_level_hmult(mid):
     """Ragged digits: HMult at 5 of 12 limbs (digits of 4 and 1 limbs)."""
     cl = Client(mid, seed=21)
