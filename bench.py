@@ -922,11 +922,13 @@ def sources_sha(kernel: str = "k_ntt") -> str:
 
 def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     """Same steps through the public API with host buffers: every step copies
-    its input pair from pinned host memory and reads its three results back.
-    Copies run on their own streams over three buffer slots, so the input copy
-    of step k+1 and the output copy of step k-1 overlap the compute of step k
-    (the input copy of a slot waits only for the output copy of three steps
-    before)."""
+    its input pair from pinned host memory and reads its two results back
+    (the rescaled product and the rotation; the unrescaled product stays on
+    the device as the intermediate it is).  Copies run on their own streams
+    over three buffer slots, so the input copy of step k+1 and the output copy
+    of step k-1 overlap the compute of step k (the input copy of a slot waits
+    only for the output copy of three steps before).  Also reported: the host
+    time to issue a step, and the time per step of the same copies alone."""
     import torch
     steps = max(5, min(args.steps, 50))
     hA = [torch.from_numpy(x.view(np.int64).reshape(-1)).pin_memory() for x in A]
@@ -940,28 +942,29 @@ def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     NSLOT = 3
     for _ in range(NSLOT):
         slots.append({"a": dev(w_in), "b": dev(w_in), "m": dev(w_in), "r": dev(w_in), "s": dev(w_rs),
-                      "hm": torch.empty(w_in, dtype=torch.int64).pin_memory(),
                       "hr": torch.empty(w_in, dtype=torch.int64).pin_memory(),
                       "hs": torch.empty(w_rs, dtype=torch.int64).pin_memory(),
                       "in_ready": torch.cuda.Event(), "computed": torch.cuda.Event(), "drained": torch.cuda.Event()})
     comp, h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
-    def step(k):
+    def step(k, compute=True):
         sl, i = slots[k % NSLOT], k % POOL
         with torch.cuda.stream(h2d):
             h2d.wait_event(sl["drained"])          # outputs of step k-3 copied out, inputs consumed
             sl["a"].copy_(hA[i], non_blocking=True)
             sl["b"].copy_(hB[i], non_blocking=True)
             sl["in_ready"].record(h2d)
-        with torch.cuda.stream(comp):
-            comp.wait_event(sl["in_ready"])
-            s = ctx.hmult(sl["a"], sl["b"], nl, rlk, sl["m"], scale, scale, stream=comp)
-            ctx.rescale(sl["m"], nl, sl["s"], s, stream=comp)
-            ctx.rotate(sl["a"], nl, 1 << (k % N_ROT), rks[k % N_ROT], sl["r"], scale, stream=comp)
-            sl["computed"].record(comp)
+        if compute:
+            with torch.cuda.stream(comp):
+                comp.wait_event(sl["in_ready"])
+                s = ctx.hmult(sl["a"], sl["b"], nl, rlk, sl["m"], scale, scale, stream=comp)
+                ctx.rescale(sl["m"], nl, sl["s"], s, stream=comp)
+                ctx.rotate(sl["a"], nl, 1 << (k % N_ROT), rks[k % N_ROT], sl["r"], scale, stream=comp)
+                sl["computed"].record(comp)
+        else:
+            sl["computed"].record(h2d)
         with torch.cuda.stream(d2h):
             d2h.wait_event(sl["computed"])
-            sl["hm"].copy_(sl["m"], non_blocking=True)
             sl["hs"].copy_(sl["s"], non_blocking=True)
             sl["hr"].copy_(sl["r"], non_blocking=True)
             sl["drained"].record(d2h)
@@ -975,16 +978,32 @@ def run_e2e(args, world, ctx, A, B, rlk, rks, nl, N, scale):
     barrier(world)
     torch.cuda.synchronize()
     e0.record(h2d)
+    t0 = time.perf_counter()
     for k in range(steps):
         step(k)
+    host_ms = (time.perf_counter() - t0) * 1e3
     d2h.synchronize()
     e1.record(d2h)
     torch.cuda.synchronize()
     barrier(world)
     ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # the same copies without the compute (what the copies alone would allow)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(h2d)
+    for k in range(steps):
+        step(k, compute=False)
+    d2h.synchronize()
+    c1.record(d2h)
+    torch.cuda.synchronize()
+    h2d_b, d2h_b = 2 * hA[0].numel() * 8, (w_in + w_rs) * 8
+    copy_ms = c0.elapsed_time(c1) / steps
     return {"value": round(2 * steps * world / (ms / 1e3), 2), "unit": "ops/s", "steps": steps,
-            "h2d_bytes_per_step": 2 * hA[0].numel() * 8,
-            "d2h_bytes_per_step": (2 * w_in + w_rs) * 8,
+            "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+            "ms_per_step": round(ms / steps, 4),
+            "host_issue_ms_per_step": round(host_ms / steps, 4),
+            "copies_alone_ms_per_step": round(copy_ms, 4),
+            "copies_alone_gbs": round((h2d_b + d2h_b) / (copy_ms / 1e3) / 1e9, 1),
             "pipelined": "input copies, compute and result copies on three streams, three buffers deep"}
 
 
