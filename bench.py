@@ -372,6 +372,16 @@ def run_fides(args, world, rank, local):
            "peak_source": "measured in-run: register-resident Shoup product, all SMs (fides_measure_modmul_peak)",
            "derived_peak": round(derived_alu, 1),
            "derived_source": "152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max}
+    # every kernel of the step against both peaks (same launch model, same live durations)
+    kernel_roofline = {}
+    for name, (cnt, by, mm) in per_kernel.items():
+        if name not in kern:
+            continue
+        avg = kern[name][1] / kern[name][0]
+        kernel_roofline[name] = {
+            "launches_per_step": cnt, "avg_launch_us": round(avg * 1e3, 2),
+            "hbm_frac": round(by / cnt / (avg / 1e3) / 1e9 / hbm_peak, 4),
+            "alu_frac": round(mm / cnt / (avg / 1e3) / 1e9 / alu_peak, 4)}
     roof = dict(hbm if hbm["frac"] >= alu["frac"] else alu)
     roof["kernel"] = top
     roof["avg_launch_us"] = round(avg_ms * 1e3, 2)
@@ -415,6 +425,10 @@ def run_fides(args, world, rank, local):
         "per_op_us": {k[3:]: round(v[1] / v[0] * 1e3, 1) for k, v in trace.items() if k.startswith("op_")},
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items(), key=lambda x: -x[1][1])},
         "roofline": roof,
+        "kernel_roofline": kernel_roofline,
+        "kernel_roofline_note": ("algorithmic bytes (launch model) / live launch time against the measured HBM peak; "
+                                 "modular products (Shoup butterflies, conversion and inner-product multiply-adds) "
+                                 "/ live launch time against the measured Shoup-product peak"),
         "gpu_launches": int(launches),
         "clocks": ck,
         "e2e": e2e,
