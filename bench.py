@@ -232,6 +232,28 @@ def launch_model(nl, K, alpha, N, bconv="k_bconv_tc"):
     return L
 
 
+def bconv_tc_flops(nl, K, alpha, N):
+    """fp16 flops one step's tensor-core conversions issue: per job of ns
+    sources and nd targets, 2 * N coefficients * 8 nd output columns * 8 nsp
+    byte rows, nsp = ns + 1 (the offset column) rounded up to even.  Two key
+    switches, each one ModUp job per digit and two ModDown jobs."""
+    beta, ne = -(-nl // alpha), nl + K
+    per_ks = 0
+    for j in range(beta):
+        ns = min(alpha, nl - j * alpha)
+        per_ks += 2 * N * 8 * (ne - ns) * 8 * ((ns + 2) & ~1)
+    per_ks += 2 * (2 * N * 8 * nl * 8 * ((K + 2) & ~1))
+    return 2 * per_ks
+
+
+def tensor_peak():
+    """Measured dense bf16 TFLOP/s (burst) from MEASURED_PEAKS.json, or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -372,16 +394,23 @@ def run_fides(args, world, rank, local):
            "peak_source": "measured in-run: register-resident Shoup product, all SMs (fides_measure_modmul_peak)",
            "derived_peak": round(derived_alu, 1),
            "derived_source": "152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max}
-    # every kernel of the step against both peaks (same launch model, same live durations)
+    # every kernel of the step against both peaks (same launch model, same live
+    # durations); the tensor-core conversion against the tensor peak instead
     kernel_roofline = {}
+    tc_peak = tensor_peak()
     for name, (cnt, by, mm) in per_kernel.items():
         if name not in kern:
             continue
         avg = kern[name][1] / kern[name][0]
-        kernel_roofline[name] = {
-            "launches_per_step": cnt, "avg_launch_us": round(avg * 1e3, 2),
-            "hbm_frac": round(by / cnt / (avg / 1e3) / 1e9 / hbm_peak, 4),
-            "alu_frac": round(mm / cnt / (avg / 1e3) / 1e9 / alu_peak, 4)}
+        ent = {"launches_per_step": cnt, "avg_launch_us": round(avg * 1e3, 2),
+               "hbm_frac": round(by / cnt / (avg / 1e3) / 1e9 / hbm_peak, 4)}
+        if name == "k_bconv_tc":
+            fl = bconv_tc_flops(nl, P.nk, ctx.alpha, N)
+            ent["tensor_tflops"] = round(fl / cnt / (avg / 1e3) / 1e12, 1)
+            ent["tensor_frac"] = round(fl / cnt / (avg / 1e3) / 1e12 / tc_peak, 4) if tc_peak else None
+        else:
+            ent["alu_frac"] = round(mm / cnt / (avg / 1e3) / 1e9 / alu_peak, 4)
+        kernel_roofline[name] = ent
     roof = dict(hbm if hbm["frac"] >= alu["frac"] else alu)
     roof["kernel"] = top
     roof["avg_launch_us"] = round(avg_ms * 1e3, 2)
@@ -427,8 +456,10 @@ def run_fides(args, world, rank, local):
         "roofline": roof,
         "kernel_roofline": kernel_roofline,
         "kernel_roofline_note": ("algorithmic bytes (launch model) / live launch time against the measured HBM peak; "
-                                 "modular products (Shoup butterflies, conversion and inner-product multiply-adds) "
-                                 "/ live launch time against the measured Shoup-product peak"),
+                                 "modular products (Shoup butterflies, inner-product and tensor-product multiply-adds) "
+                                 "/ live launch time against the measured Shoup-product peak; k_bconv_tc: fp16 "
+                                 "flops of the MMA shapes it issues against the measured dense bf16 peak (fp16 runs "
+                                 "at the bf16 rate)"),
         "gpu_launches": int(launches),
         "clocks": ck,
         "e2e": e2e,
