@@ -35,6 +35,12 @@
  *    Programs (fides_program_run) are the exception: each run uses the scratch
  *    inside its own work buffer, so runs with different work buffers may
  *    overlap on several streams of one context.
+ *  - Key buffers (relinearisation, rotation, conjugation keys) are read while
+ *    the kernels queued before them on the same stream may still be finishing
+ *    (they stream in during the previous kernel's last wave).  Fill them with
+ *    copies, or with kernels that complete before the call's first kernel
+ *    starts (any kernel that does not allow programmatic dependent launch),
+ *    not with a kernel still running under programmatic launch.
  *  - Return value: FIDES_OK (0) or a negative FIDES_ERR_* code; the message of
  *    the last error on the calling thread is available from fides_last_error().
  *    Argument errors are detected before anything is queued.

@@ -294,6 +294,11 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     }
     __syncthreads();
     if (t == 0) bulk_load(smem_addr(sB), B.tc, (u32)ndp * nsp * 128, bar0);
+    // everything above reads only the job and the context's tables; the
+    // sources below are the previous kernel's output, and no tensor memory is
+    // taken before it has finished (an early-launched conversion must not
+    // hold it while this one waits)
+    pdl_wait();
     __syncwarp();
     if (w == 0) tmem_alloc(smem_addr(&tslot), ncols);
 
@@ -393,10 +398,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_bconv_tc(BConvArgs A, const P
                                                             const TwPair *__restrict__ c32, int logN, u32 ncols,
                                                             int *status)
 {
-    // the dependents may launch now; nothing is read (and no tensor memory
-    // taken, so an early-launched conversion cannot hold it while this one
-    // waits) before the previous kernel has finished
-    pdl_enter();
+    // the dependents may launch now; the body waits for the previous kernel
+    // after staging the job's constants
+    pdl_trigger();
     if (A.djob) bconv_tc_body<BIG>(A.djob[blockIdx.y], P, c32, logN, ncols, status);
     else bconv_tc_body<BIG>(A.job[blockIdx.y], P, c32, logN, ncols, status);
 }

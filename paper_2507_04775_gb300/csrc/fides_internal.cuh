@@ -286,6 +286,13 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The two halves of pdl_enter, for kernels that first read data no kernel
+// writes (twiddles, conversion matrices, keys, launch tables uploaded by the
+// host) so that those reads overlap the previous kernel's last wave: trigger
+// at entry, wait before the first read of anything a kernel produces.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename... Params, typename... Args>
 inline cudaError_t fides_launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, cudaStream_t st,
                                        Args &&...args)

@@ -304,15 +304,23 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const u64 *__restrict__ dsrc = op.dsrc;
     u64 *acc = op.acc;
     if (V2) {
-        // issue every load before the first product (the kernel is bound by HBM)
+        // issue every load before the first product (the kernel is bound by
+        // HBM); the keys, which no kernel writes, before the wait for the
+        // previous kernel, so that they stream during its last wave
         ulonglong2 e[MAXB], k0[MAXB], k1[MAXB];
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+            if (j < beta) {
+                k0[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 0) * nfull + pz) * N + n);
+                k1[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 1) * nfull + pz) * N + n);
+            }
+        }
+        pdl_wait();
 #pragma unroll
         for (int j = 0; j < MAXB; ++j) {
             if (j < beta) {
                 const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
                 e[j] = *reinterpret_cast<const ulonglong2 *>(src + n);
-                k0[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 0) * nfull + pz) * N + n);
-                k1[j] = *reinterpret_cast<const ulonglong2 *>(evk + (((size_t)j * 2 + 1) * nfull + pz) * N + n);
             }
         }
         // 128-bit sums as 32-bit carry chains (each product < 2^122, at most
@@ -340,15 +348,22 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
         const u64 e2 = ((2 * (u64)rn + 1) * op.g) & ((2ull << logN) - 1);
         sn = __brev((u32)((e2 - 1) >> 1)) >> (32 - logN);
     }
-    // issue every load before the first product (the kernel is bound by HBM)
+    // issue every load before the first product (the kernel is bound by HBM),
+    // the keys before the wait for the previous kernel
     u64 e[MAXB], k0[MAXB], k1[MAXB];
+#pragma unroll
+    for (int j = 0; j < MAXB; ++j) {
+        if (j < beta) {
+            k0[j] = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
+            k1[j] = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
+        }
+    }
+    pdl_wait();
 #pragma unroll
     for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
             const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
             e[j] = src[sn];
-            k0[j] = evk[(((size_t)j * 2 + 0) * nfull + pz) * N + n];
-            k1[j] = evk[(((size_t)j * 2 + 1) * nfull + pz) * N + n];
         }
     }
     Acc128 a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
@@ -385,7 +400,7 @@ __device__ __forceinline__ int find_op(const int *__restrict__ pre, int nop, int
 template <int MAXB, bool V2>
 __global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
 {
-    pdl_enter();
+    pdl_trigger();   // inner_body waits after issuing its key loads
     const int z = blockIdx.y;
     if (A.dop) {
         const int k = find_op(A.dpre, A.nop, z);

@@ -337,7 +337,10 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     __shared__ u64 sm[C << S];
     __shared__ TwPair stw[TWS ? (1 << S) : 1];
 
-    pdl_enter();
+    // the job table, the primes and the twiddles are the context's or the
+    // host's: read (and the column twiddles staged) before waiting for the
+    // previous kernel, whose output is read only below
+    pdl_trigger();
     const int t = threadIdx.x;
     const Job J = get_job(set, blockIdx.y, 1 << LOGN);
     const PrimeInfo pr = P[J.prime];
@@ -346,6 +349,7 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     if (TWS) {
         for (int i = t; i < (1 << S); i += THREADS) stw[i] = tw[i];
     }
+    pdl_wait();
 
     int c, u;
     if (KIND == 0) { c = t % C; u = t / C; }
