@@ -307,7 +307,7 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
         P.r64p = shoup_of(P.r64, q);
         P.ninv = hinv((u64)N % q, q);
         P.ninvp = shoup_of(P.ninv, q);
-        P.pad = 0;
+        P.ninvw = P.ninvwp = P.pad = 0;   // after the twiddles
         // powers in natural order, then scattered to bit-reversed positions
         u64 x = 1, y = 1;
         for (int k = 0; k < N; ++k) {
@@ -317,6 +317,8 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
             x = hmul(x, psi, q);
             y = hmul(y, ipsi, q);
         }
+        P.ninvw = hmul(P.ninv, itw[(size_t)i * N + 1].w, q);
+        P.ninvwp = shoup_of(P.ninvw, q);
     }
 
     // ModUp tables per (nl, j)
@@ -418,19 +420,24 @@ extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t
     for (int i = 0; i < L; ++i) iroot[i] = pair_of(hpow(c->psi[i], (u64)N / 2, primes[i]), primes[i]);
 
     // combined N^-1 * qhat^-1 constants of the inverse NTTs feeding a conversion
-    std::vector<TwPair> mu_ns((size_t)L * (L + 1) / 2), md_ns((size_t)np);
+    std::vector<TwPair> mu_ns((size_t)L * (L + 1)), md_ns(2 * (size_t)np);
+    auto with_w1 = [&](std::vector<TwPair> &t, size_t at, u64 cval, int pi) {
+        const u64 q = primes[pi];
+        t[2 * at] = pair_of(cval, q);
+        t[2 * at + 1] = pair_of(hmul(cval, itw[(size_t)pi * N + 1].w, q), q);
+    };
     for (int nl = 1; nl <= L; ++nl) {
         for (int i = 0; i < nl; ++i) {
             const int j = i / alpha, lo = j * alpha, hi = std::min(lo + alpha, nl);
             u64 qi = primes[i], prod = 1;
             for (int k = lo; k < hi; ++k)
                 if (k != i) prod = hmul(prod, primes[k] % qi, qi);
-            mu_ns[(size_t)nl * (nl - 1) / 2 + i] = pair_of(hmul(hinv(prod, qi), pinfo[i].ninv, qi), qi);
+            with_w1(mu_ns, (size_t)nl * (nl - 1) / 2 + i, hmul(hinv(prod, qi), pinfo[i].ninv, qi), i);
         }
     }
     for (int k = 0; k < K; ++k) {
         u64 pk = primes[L + k];
-        md_ns[L + k] = pair_of(hmul(md_scale[k].w, pinfo[L + k].ninv, pk), pk);
+        with_w1(md_ns, (size_t)L + k, hmul(md_scale[k].w, pinfo[L + k].ninv, pk), L + k);
     }
 
     int rc = FIDES_OK;

@@ -46,6 +46,8 @@ struct __align__(16) PrimeInfo {
     u64 r64p;   // Shoup companion of r64
     u64 ninv;   // N^-1 mod q
     u64 ninvp;  // Shoup companion of ninv
+    u64 ninvw;  // N^-1 w1 mod q, w1 the twiddle of the last inverse stage (psi^-N/2)
+    u64 ninvwp; // Shoup companion of ninvw
     u64 pad;
 };
 
@@ -123,9 +125,10 @@ struct fides_ctx {
     TwPair *d_hr;
 
     // Combined final constants of the inverse NTTs that feed a base conversion
-    // (the N^-1 of the INTT times the conversion's qhat^-1):
-    //   d_mu_nscale[nl(nl-1)/2 + i] = N^-1 qhat_{j(i),i}^-1 mod q_i, i < nl
-    //   d_md_nscale[L + k]          = N^-1 Phat_k^-1 mod p_k
+    // (the N^-1 of the INTT times the conversion's qhat^-1), each c followed
+    // by c w1 (w1 the twiddle of the last inverse stage, folded into it):
+    //   d_mu_nscale[2 (nl(nl-1)/2 + i) + {0, 1}] = N^-1 qhat_{j(i),i}^-1 {1, w1} mod q_i, i < nl
+    //   d_md_nscale[2 (L + k) + {0, 1}]          = N^-1 Phat_k^-1 {1, w1} mod p_k
     TwPair *d_mu_nscale;
     TwPair *d_md_nscale;
 

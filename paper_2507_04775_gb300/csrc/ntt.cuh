@@ -78,6 +78,16 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, const TwPair &w, u64 q, 
     y = mul_shoup(a + q2 - b, w, q);
 }
 
+// The last inverse stage (one twiddle w1) with the final scale c folded in:
+// (x + y) c and (x - y) (w1 c), both in [0, 2q) -- two Shoup products in
+// place of the stage's product, its subtraction and two scalings.
+__device__ __forceinline__ void gs_bfly_scaled(u64 &x, u64 &y, const TwPair &c, const TwPair &cw, u64 q, u64 q2)
+{
+    u64 a = x, b = y;
+    x = mul_shoup(a + b, c, q);
+    y = mul_shoup(a + q2 - b, cw, q);
+}
+
 // ---- prologue functors: value of input element j, in [0, 4q) ----
 struct ProSrc {
     __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return J.src[j]; }
@@ -277,9 +287,11 @@ struct EpiHmRs {
 // inverse one, and the window bits an earlier round transformed act as
 // independent lanes).  X: the global-index bits above the window; TWS:
 // twiddles come from shared memory instead of global.
-template <bool INV, int S0, int S, int B, int A0, bool TWS>
+// SCALED: an inverse pass that ends with stage 0 multiplies by the final
+// constant there (gs_bfly_scaled with c, cw = c w1) instead of after it.
+template <bool INV, int S0, int S, int B, int A0, bool TWS, bool SCALED>
 __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__restrict__ tw,
-                                          const TwPair *stw, u64 q, u64 q2)
+                                          const TwPair *stw, u64 q, u64 q2, const TwPair &c, const TwPair &cw)
 {
     const u64 q4 = 2 * q2;
 #pragma unroll
@@ -290,6 +302,10 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[16], int X, const TwPair *__r
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             if (r & h) continue;
+            if (INV && SCALED && s == 0) {
+                gs_bfly_scaled(x[r], x[r + h], c, cw, q, q2);
+                continue;
+            }
             const int idx = base + (INV ? (r >> (a + 1)) : (r >> (4 - a)));
             const TwPair w = TWS ? stw[idx] : tw[idx];
             if (INV) gs_bfly(x[r], x[r + h], w, q, q2);
@@ -334,6 +350,7 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     constexpr int SH = LOGN - S;                       // column stride shift
     constexpr bool TWS = (KIND == 0);                  // column twiddles staged in shared memory
     static_assert(S >= 5 && R <= 3, "tile shape");
+    static_assert(!NINV || (INV && KIND != 1), "the final scale is applied in stage 0, which only this pass holds");
     __shared__ u64 sm[C << S];
     __shared__ TwPair stw[TWS ? (1 << S) : 1];
 
@@ -412,6 +429,21 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
         for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, 0))];
     }
 
+    // The final constant of an inverse pass (NINV): N^-1, or the segment's
+    // combined constant (N^-1 times the qhat^-1 of the base conversion that
+    // reads this output, Eq. 1), with its product by the last stage's twiddle;
+    // applied in that stage (gs_bfly_scaled).
+    TwPair nc = {0, 0}, nw = {0, 0};
+    if (NINV) {
+        if (J.cst) {
+            nc = J.cst[2 * J.prime];
+            nw = J.cst[2 * J.prime + 1];
+        } else {
+            nc = TwPair{pr.ninv, pr.ninvp};
+            nw = TwPair{pr.ninvw, pr.ninvwp};
+        }
+    }
+
     // ---------------- rounds ----------------
 #define FIDES_NTT_ROUND(RHO)                                                                 \
     if (RHO < R) {                                                                           \
@@ -419,7 +451,7 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
         if (RHO > 0) {                                                                       \
             _Pragma("unroll") for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, b))]; \
         }                                                                                    \
-        ntt_round<INV, S0, S, b, round_first<S>(RHO < R ? RHO : 0), TWS>(x, Xof(b), tw, stw, q, q2); \
+        ntt_round<INV, S0, S, b, round_first<S>(RHO < R ? RHO : 0), TWS, NINV>(x, Xof(b), tw, stw, q, q2, nc, nw); \
         if (RHO < R - 1) {                                                                   \
             _Pragma("unroll") for (int r = 0; r < 16; ++r) sm[widx(c, kmap(u, r, b))] = x[r]; \
             __syncthreads();                                                                 \
@@ -434,13 +466,6 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     if (!INV && !Epi::kRaw) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = csub(csub(x[r], 2 * q2), q2);   // [0, 6q) -> [0, 2q)
-    }
-    if (NINV) {
-        // N^-1, or the segment's combined constant (N^-1 times the qhat^-1 of
-        // the base conversion that reads this output, Eq. 1)
-        const TwPair nc = J.cst ? J.cst[J.prime] : TwPair{pr.ninv, pr.ninvp};
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = mul_shoup(x[r], nc, q);
     }
     if (INV || KIND == 0) {
         const int bl = INV ? S - 4 : 0;

@@ -67,7 +67,7 @@ inline void ks_intt_segs(const fides_ctx *c, const KsBuffers &B, std::vector<Seg
 {
     const size_t nl = B.nl;
     Seg g = seg_of(B.prep ? B.pa : B.d, B.coeff, B.nl, 0, B.pb, B.pout, 1, B.prep,
-                   c->d_mu_nscale + nl * (nl - 1) / 2);
+                   c->d_mu_nscale + nl * (nl - 1));   // pairs: 2 (nl(nl-1)/2) entries precede level nl
     g.side = B.prep ? const_cast<u64 *>(B.d) : nullptr;
     g.g = B.g;
     g.pstride = (int)(nl * c->N);
