@@ -133,6 +133,30 @@ def test_hmult(pair):
         assert np.array_equal(to_host(out).reshape(2, nl, o.N), o.hmult(a, b, key)), "hmult differs at nl=%d" % nl
 
 
+def test_key_written_just_before_the_call(pair):
+    """The key switch reads its key before it waits for the kernels queued
+    ahead of it; a key produced on the same stream right before the call -- by
+    a device copy, then by an element-wise kernel that overwrites it -- is
+    still the one used, on two back-to-back calls with different keys."""
+    P, g, o = pair
+    st = si.Stream(1014, 15)
+    k1, k2 = rand_key(st, o), rand_key(st, o)
+    nl = P.nq
+    a, b = rand_poly(st, o.q[:nl], o.N, 2), rand_poly(st, o.q[:nl], o.N, 2)
+    da, db = to_device(a), to_device(b)
+    src1, src2 = to_device(k1), to_device(k2)
+    dk = torch.zeros_like(src1)
+    out1 = torch.empty(2 * nl * o.N, dtype=torch.int64, device="cuda")
+    out2 = torch.empty_like(out1)
+    dk.copy_(src1)                                 # a copy on the current stream
+    g.hmult(da, db, nl, dk, out1)
+    torch.add(src2, 0, out=dk)                     # a kernel on the current stream
+    g.hmult(da, db, nl, dk, out2)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(out1).reshape(2, nl, o.N), o.hmult(a, b, k1))
+    assert np.array_equal(to_host(out2).reshape(2, nl, o.N), o.hmult(a, b, k2))
+
+
 def test_rotate(pair):
     P, g, o = pair
     st = si.Stream(1006, 7)
