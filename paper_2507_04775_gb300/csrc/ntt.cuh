@@ -336,8 +336,9 @@ __host__ __device__ constexpr int ntt_threads()
 // KIND: 0 = column pass (CT strided columns of 2^S elements, stages 0..S-1),
 //       1 = row pass (CT contiguous rows of 2^S elements, stages LOGN-S..LOGN-1),
 //       2 = whole limb (S == LOGN == 12, 256 threads; CT ignored).
-// INV selects Gentleman-Sande stages in reverse order; NINV multiplies by
-// N^-1 before the epilogue.  MINB is the resident-CTA target per SM.
+// INV selects Gentleman-Sande stages in reverse order; NINV applies N^-1 (or
+// the segment's constant) within the last stage, before the epilogue.  MINB
+// is the resident-CTA target per SM.
 template <int LOGN, int S, int KIND, bool INV, bool NINV, int CT, int MINB, class Pro, class Epi>
 __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
     k_ntt(LimbSet set, const PrimeInfo *__restrict__ P, const TwPair *__restrict__ TW, Pro pro, Epi epi)
