@@ -281,8 +281,8 @@ int fides_trace_set(int on);
 // Programmatic dependent launch: every kernel of the library lets the next
 // kernel in its stream launch as soon as all of its CTAs are running, and waits
 // for the previous kernel to finish (and its memory to be visible) before it
-// reads anything.  The next kernel's CTAs thus occupy SMs freed during this
-// kernel's last wave instead of after a launch gap.
+// reads anything a kernel produced.  The next kernel's CTAs thus occupy SMs
+// freed during this kernel's last wave instead of after a launch gap.
 __device__ __forceinline__ void pdl_enter()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
