@@ -232,6 +232,23 @@ def launch_model(nl, K, alpha, N, bconv="k_bconv_tc"):
     return L
 
 
+def op_work(nl, K, alpha, N):
+    """Compulsory HBM bytes and modmul-equivalents of one HMult+relin, HRotate
+    and Rescale at nl limbs: inputs + the key limbs in use + outputs; (beta+2)
+    (nl+K) transforms of (N/2) log2 N butterflies, the conversions' multiply-adds
+    and the element-wise products (the tensor product for HMult)."""
+    import math
+    W = 8 * N
+    beta, ne = -(-nl // alpha), nl + K
+    digits = [min(alpha, nl - j * alpha) for j in range(beta)]
+    bfly = (N // 2) * int(math.log2(N))
+    ks_mm = (beta + 2) * ne * bfly + N * (sum(a * (ne - a) for a in digits) + 2 * K * nl) \
+        + N * (sum(digits) + 2 * beta * ne + 2 * K + 2 * nl)
+    return {"hmult": (W * (4 * nl + 2 * beta * ne + 2 * nl), ks_mm + N * 4 * nl),
+            "rotate": (W * (2 * nl + 2 * beta * ne + 2 * nl), ks_mm),
+            "rescale": (W * (2 * nl + 2 * (nl - 1)), (2 + 2 * (nl - 1)) * bfly + N * 2 * (nl - 1))}
+
+
 def bconv_tc_flops(nl, K, alpha, N):
     """fp16 flops one step's tensor-core conversions issue: per job of ns
     sources and nd targets, 2 * N coefficients * 8 nd output columns * 8 nsp
@@ -411,6 +428,25 @@ def run_fides(args, world, rank, local):
         else:
             ent["alu_frac"] = round(mm / cnt / (avg / 1e3) / 1e9 / alu_peak, 4)
         kernel_roofline[name] = ent
+    # whole operations: compulsory bytes and modmul-equivalents against the
+    # same two peaks (per op from its traced time, the step from the untraced one)
+    work = op_work(nl, P.nk, ctx.alpha, N)
+    op_roofline = {}
+    for name, (by, mm) in work.items():
+        key = "op_" + name
+        if key in trace:
+            us = trace[key][1] / trace[key][0] * 1e3
+            op_roofline[name] = {"us": round(us, 1), "compulsory_mb": round(by / 1e6, 1),
+                                 "modmul_equiv_m": round(mm / 1e6, 1),
+                                 "hbm_frac": round(by / (us / 1e6) / 1e9 / hbm_peak, 4),
+                                 "alu_frac": round(mm / (us / 1e6) / 1e9 / alu_peak, 4)}
+    st_by = sum(v[0] for v in work.values())
+    st_mm = sum(v[1] for v in work.values())
+    st_ms = ms_max / args.steps
+    op_roofline["step"] = {"ms": round(st_ms, 4), "compulsory_mb": round(st_by / 1e6, 1),
+                           "modmul_equiv_m": round(st_mm / 1e6, 1),
+                           "hbm_frac": round(st_by / (st_ms / 1e3) / 1e9 / hbm_peak, 4),
+                           "alu_frac": round(st_mm / (st_ms / 1e3) / 1e9 / alu_peak, 4)}
     roof = dict(hbm if hbm["frac"] >= alu["frac"] else alu)
     roof["kernel"] = top
     roof["avg_launch_us"] = round(avg_ms * 1e3, 2)
@@ -455,6 +491,11 @@ def run_fides(args, world, rank, local):
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items(), key=lambda x: -x[1][1])},
         "roofline": roof,
         "kernel_roofline": kernel_roofline,
+        "op_roofline": op_roofline,
+        "op_roofline_note": ("compulsory bytes = input ciphertexts + the key limbs in use + outputs; modmul-equivalents "
+                             "= (beta+2)(nl+K) transforms x (N/2) log2 N butterflies + conversion multiply-adds + "
+                             "element-wise products (conversions run on the tensor cores, so alu_frac overstates "
+                             "the integer pipes' share)"),
         "kernel_roofline_note": ("algorithmic bytes (launch model) / live launch time against the measured HBM peak; "
                                  "modular products (Shoup butterflies, inner-product and tensor-product multiply-adds) "
                                  "/ live launch time against the measured Shoup-product peak; k_bconv_tc: fp16 "
