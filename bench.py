@@ -282,10 +282,20 @@ def peaks():
 
 # ALU roofline of a 64-bit Shoup product: 10 IMAD-class instructions (4 for the
 # high half of a 64x64 product, 3 for each low half), 64 IMAD per clock per
-# SM, 152 SMs.
+# SM, 152 SMs: the peak derived from unit counts and the SM clock.
 IMAD_PER_MODMUL = 10
 IMAD_PER_CLK_SM = 64
 SMS = 152
+
+# What limits each kernel, from its ncu profile: the NTT passes the integer
+# multiply pipe, the inner and tensor products DRAM, the conversion the
+# tensor-core issue path.
+KERNEL_BOUND = {"k_ntt": "alu", "k_inner": "hbm", "k_tensor": "hbm", "k_elem": "hbm", "k_ptmac": "hbm",
+                "k_bconv_tc": "tensor"}
+
+
+def kernel_bound(name):
+    return next((v for k, v in KERNEL_BOUND.items() if name.startswith(k)), None)
 
 
 def run_fides(args, world, rank, local):
@@ -401,16 +411,17 @@ def run_fides(args, world, rank, local):
     hbm_ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
     clk = (ck or {}).get("sm_mhz") or sm_max
     derived_alu = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / IMAD_PER_MODMUL / 1e9   # Gmodmul/s at max clock
-    alu_peak = peak_mm
+    alu_peak = derived_alu
     alu_ach = mm_per_launch / (avg_ms / 1e3) / 1e9
     traffic = load_traffic(top, bytes_per_launch)
     hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
            "frac": round(hbm_ach / hbm_peak, 4), "traffic": traffic, "peak_source": hbm_src}
     alu = {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
            "frac": round(alu_ach / alu_peak, 4),
-           "peak_source": "measured in-run: register-resident Shoup product, all SMs (fides_measure_modmul_peak)",
-           "derived_peak": round(derived_alu, 1),
-           "derived_source": "152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max}
+           "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max,
+           "measured_microbenchmark": {
+               "peak": round(peak_mm, 1), "frac": round(alu_ach / peak_mm, 4),
+               "source": "measured in-run: register-resident Shoup products on all SMs (fides_measure_modmul_peak)"}}
     # every kernel of the step against both peaks (same launch model, same live
     # durations); the tensor-core conversion against the tensor peak instead
     kernel_roofline = {}
@@ -419,7 +430,7 @@ def run_fides(args, world, rank, local):
         if name not in kern:
             continue
         avg = kern[name][1] / kern[name][0]
-        ent = {"launches_per_step": cnt, "avg_launch_us": round(avg * 1e3, 2),
+        ent = {"bound": kernel_bound(name), "launches_per_step": cnt, "avg_launch_us": round(avg * 1e3, 2),
                "hbm_frac": round(by / cnt / (avg / 1e3) / 1e9 / hbm_peak, 4)}
         if name == "k_bconv_tc":
             fl = bconv_tc_flops(nl, P.nk, ctx.alpha, N)
@@ -447,7 +458,10 @@ def run_fides(args, world, rank, local):
                            "modmul_equiv_m": round(st_mm / 1e6, 1),
                            "hbm_frac": round(st_by / (st_ms / 1e3) / 1e9 / hbm_peak, 4),
                            "alu_frac": round(st_mm / (st_ms / 1e3) / 1e9 / alu_peak, 4)}
-    roof = dict(hbm if hbm["frac"] >= alu["frac"] else alu)
+    bound = kernel_bound(top)
+    if bound not in ("alu", "hbm"):
+        bound = "hbm" if hbm["frac"] >= alu["frac"] else "alu"
+    roof = dict(hbm if bound == "hbm" else alu)
     roof["kernel"] = top
     roof["avg_launch_us"] = round(avg_ms * 1e3, 2)
     roof["other_bound"] = alu if roof["bound"] == "hbm" else hbm
@@ -492,15 +506,16 @@ def run_fides(args, world, rank, local):
         "roofline": roof,
         "kernel_roofline": kernel_roofline,
         "op_roofline": op_roofline,
-        "op_roofline_note": ("compulsory bytes = input ciphertexts + the key limbs in use + outputs; modmul-equivalents "
-                             "= (beta+2)(nl+K) transforms x (N/2) log2 N butterflies + conversion multiply-adds + "
-                             "element-wise products (conversions run on the tensor cores, so alu_frac overstates "
-                             "the integer pipes' share)"),
+        "op_roofline_note": ("compulsory bytes = input ciphertexts + the key limbs in use + outputs, against the "
+                             "measured HBM peak; modmul-equivalents = (beta+2)(nl+K) transforms x (N/2) log2 N "
+                             "butterflies + conversion multiply-adds + element-wise products, against the derived "
+                             "Shoup-product peak (conversions run on the tensor cores, so alu_frac overstates the "
+                             "integer pipes' share)"),
         "kernel_roofline_note": ("algorithmic bytes (launch model) / live launch time against the measured HBM peak; "
                                  "modular products (Shoup butterflies, inner-product and tensor-product multiply-adds) "
-                                 "/ live launch time against the measured Shoup-product peak; k_bconv_tc: fp16 "
+                                 "/ live launch time against the derived Shoup-product peak; k_bconv_tc: fp16 "
                                  "flops of the MMA shapes it issues against the measured dense bf16 peak (fp16 runs "
-                                 "at the bf16 rate)"),
+                                 "at the bf16 rate); bound: what the kernel's ncu profile shows limits it"),
         "gpu_launches": int(launches),
         "clocks": ck,
         "e2e": e2e,
