@@ -280,11 +280,15 @@ def peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# ALU roofline of a 64-bit Shoup product: 10 IMAD-class instructions (4 for the
-# high half of a 64x64 product, 3 for each low half), 64 IMAD per clock per
-# SM, 152 SMs: the peak derived from unit counts and the SM clock.
-IMAD_PER_MODMUL = 10
-IMAD_PER_CLK_SM = 64
+# ALU roofline of a 64-bit Shoup product, from unit counts and the SM clock:
+# 152 SMs x 64 lanes of the integer multiply (fmaheavy) pipe per clock, and 16
+# lane-cycles per product -- its 10 IMAD-class instructions (4 for the high
+# half of a 64x64 product, 3 for each low half) hold a sub-partition's pipe 32
+# cycles per warp of 32 products (ncu on the register-resident microbenchmark:
+# 10.0 FMA-pipe warp instructions and 1.00 pipe cycle per product per
+# sub-partition, the pipe 95.6 % busy).
+LANE_CYCLES_PER_MODMUL = 16
+FMAHEAVY_LANES_PER_CLK_SM = 64
 SMS = 152
 
 # What limits each kernel, from its ncu profile: the NTT passes the integer
@@ -410,7 +414,7 @@ def run_fides(args, world, rank, local):
     hbm_peak, hbm_src, sm_max = peaks()
     hbm_ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
     clk = (ck or {}).get("sm_mhz") or sm_max
-    derived_alu = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / IMAD_PER_MODMUL / 1e9   # Gmodmul/s at max clock
+    derived_alu = SMS * FMAHEAVY_LANES_PER_CLK_SM * sm_max * 1e6 / LANE_CYCLES_PER_MODMUL / 1e9   # Gmodmul/s
     alu_peak = derived_alu
     alu_ach = mm_per_launch / (avg_ms / 1e3) / 1e9
     traffic = load_traffic(top, bytes_per_launch)
@@ -418,7 +422,8 @@ def run_fides(args, world, rank, local):
            "frac": round(hbm_ach / hbm_peak, 4), "traffic": traffic, "peak_source": hbm_src}
     alu = {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
            "frac": round(alu_ach / alu_peak, 4),
-           "peak_source": "derived: 152 SMs x 64 IMAD/clk x %.0f MHz / 10 IMAD per Shoup product" % sm_max,
+           "peak_source": ("derived: 152 SMs x 64 fmaheavy lanes x %.0f MHz / 16 lane-cycles per Shoup product "
+                           "(10 IMAD-class instructions, 32 pipe cycles per warp; ncu on the microbenchmark)" % sm_max),
            "measured_microbenchmark": {
                "peak": round(peak_mm, 1), "frac": round(alu_ach / peak_mm, 4),
                "source": "measured in-run: register-resident Shoup products on all SMs (fides_measure_modmul_peak)"}}
