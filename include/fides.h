@@ -426,7 +426,10 @@ void fides_batch_destroy(fides_batch *batch);
  *
  * Keys: fides_server_set_relin_key / fides_server_add_rotation_key register
  * device keys ([dnum][2][L+K][N], as for fides_hmult / fides_rotate; rotation
- * keys by step count, modulo N/2).  Keys must stay valid until destroy.
+ * keys by step count, modulo N/2).  Keys must stay valid until destroy, and
+ * hold their final contents before the first request that uses them is
+ * submitted (the server's lanes run on streams of their own; synchronise the
+ * copy or kernel that fills a key first).
  *
  * fides_server_submit validates and queues one request and returns its id:
  *   FIDES_ERR_ARG       bad type, NULL input, level outside [1, L] (Rescale:
