@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fides", choices=["fides", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 128-ciphertext batched workload")
@@ -172,6 +172,15 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+def workload_config(P, world):
+    """The `config` object of the JSON line (the same for both arms)."""
+    return {"workload": "single-op path logN=16 L=30 K=10 dnum=3: HMult+relin, Rescale, HRotate(2^(k mod 15))",
+            "logN": P.logN, "limbs": P.nq, "special_primes": P.nk, "dnum": P.dnum, "q_bits": P.q_bits,
+            "p_bits": P.p_bits, "ops_per_step": 2,
+            "l2": "inputs larger than L2: 8 ciphertext pairs + 16 keys (1.9 GiB) cycled, >400 MB per step",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def workload_inputs(P, q, p, seed):
     """Host arrays of the workload: POOL ciphertext pairs and 16 keys."""
     st = si.Stream(seed, 10)
@@ -323,7 +332,10 @@ def run_fides(args, world, rank, local):
     dA = [fides.to_device(x) for x in A]
     dB = [fides.to_device(x) for x in B]
     dK = [fides.to_device(x) for x in keys]
-    rlk, rks = dK[0], dK[1:]
+    # switching keys as registered handles: the relinearisation key and the
+    # keys of the rotations by 2^k (uniform residues; see the module docstring)
+    rlk = ctx.relin_key(dK[0])
+    rks = [ctx.rotation_key(dK[1 + k], 1 << k) for k in range(N_ROT)]
     out_m = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
     out_r = torch.empty_like(out_m)
     out_s = torch.empty(2 * (nl - 1) * N, dtype=torch.int64, device="cuda")
@@ -501,11 +513,7 @@ def run_fides(args, world, rank, local):
         "metric": METRIC, "value": round(value, 2), "unit": "ops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "single-op path logN=16 L=30 K=10 dnum=3: HMult+relin, Rescale, HRotate(2^(k mod 15))",
-                   "logN": P.logN, "limbs": nl, "special_primes": P.nk, "dnum": P.dnum, "q_bits": P.q_bits,
-                   "p_bits": P.p_bits, "ops_per_step": 2,
-                   "l2": "inputs larger than L2: 8 ciphertext pairs + 16 keys (1.9 GiB) cycled, >400 MB per step",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(P, world),
         "per_op_us": {k[3:]: round(v[1] / v[0] * 1e3, 1) for k, v in trace.items() if k.startswith("op_")},
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items(), key=lambda x: -x[1][1])},
         "roofline": roof,
@@ -566,9 +574,21 @@ def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
                             scale_a=scale * scale))
         plain.append((a, b, m, r, nl, rots[i]))
     batch = fides.Batch(ctx, ops)
-    info = batch.info()
+    info0 = batch.info()            # one launch group per stage
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        t_tune = time.perf_counter()
+        batch.autotune(stream)      # launch-group size and tensor-product placement
+        t_tune = time.perf_counter() - t_tune
+        info = batch.info()
+        # per-kernel times of one traced run (events serialise the launches)
+        fides.trace_reset()
+        fides.trace_enable(True)
+        batch.run(stream)
+        stream.synchronize()
+        fides.trace_enable(False)
+        tr = fides.trace_read()
+        fides.trace_reset()
         batch.capture(stream)
         for _ in range(2):
             batch.run(stream)
@@ -602,7 +622,13 @@ def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
             "ms_per_batch": round(ms_batch, 3), "plain_value": round(nops / (ms_plain / 1e3), 1),
             "plain_ms": round(ms_plain, 3), "speedup": round(ms_plain / ms_batch, 3),
             "graph": True, "kernels_per_batch": info["launches"],
-            "kernels_plain": n * 22, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2)}
+            "kernels_plain": n * 22, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2),
+            "autotune": {"seconds": round(t_tune, 1), "group_limbs": info["group_limbs"], "groups": info["groups"],
+                         "tensor_split": info["tensor_split"],
+                         "one_group_per_stage": {"scratch_gib": round(info0["scratch_bytes"] / 2**30, 2),
+                                                 "kernels": info0["launches"]}},
+            "traced_kernels_ms": {k: round(v[1], 3) for k, v in sorted(tr.items(), key=lambda x: -x[1][1])
+                                  if k.startswith("k_")}}
 
 
 SERVE_STEPS = [k for k in range(1, 33)] + [-k for k in range(1, 33)]    # 64 resident rotation keys
@@ -636,15 +662,15 @@ def run_serving(args, ctx, dA, dK, P, scale):
     N, nq = ctx.N, P.nq
     lo, hi = 2, nq
     # resident keys: 1 relinearisation + 64 rotation keys, separate buffers (120 MiB each)
-    rlk = dK[0].clone()
-    rot = {k: dK[1 + i % (len(dK) - 1)].clone() for i, k in enumerate(SERVE_STEPS)}
+    rlk = ctx.relin_key(dK[0].clone())
+    rot = {k: ctx.rotation_key(dK[1 + i % (len(dK) - 1)].clone(), k) for i, k in enumerate(SERVE_STEPS)}
     # resident operand pool: 256 ciphertexts, levels 2..30 round-robin
     pool_lv = [lo + i % (hi - lo + 1) for i in range(256)]
     pool = [dA[i % len(dA)].view(2, nq, N)[:, :nl].contiguous().view(-1) for i, nl in enumerate(pool_lv)]
     by_level = {}
     for i, nl in enumerate(pool_lv):
         by_level.setdefault(nl, []).append(i)
-    resident = (rlk.numel() + sum(t.numel() for t in rot.values()) + sum(t.numel() for t in pool)) * 8
+    resident = (rlk.tensor.numel() + sum(t.tensor.numel() for t in rot.values()) + sum(t.numel() for t in pool)) * 8
     budget = int(args.serve_budget_gb * 1e9)
     arena = budget - resident
     torch.cuda.synchronize()
@@ -780,7 +806,7 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
 
     res = {}
     steps = [1, 2, 3, 4, 5, 6, 7, 8]
-    keys = [dK[1 + i % (len(dK) - 1)] for i in range(len(steps))]
+    keys = [ctx.rotation_key(dK[1 + i % (len(dK) - 1)], s) for i, s in enumerate(steps)]
     outs = [torch.empty(2 * nl * N, dtype=torch.int64, device="cuda") for _ in steps]
     t_h = timed(lambda: ctx.rotate_hoisted(a, nl, steps, keys, outs, scale), 10)
     t_p = timed(lambda: [ctx.rotate(a, nl, k, key, o, scale) for k, key, o in zip(steps, keys, outs)], 10)
@@ -791,8 +817,8 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
     n1 = 8
     st = si.Stream(si.workload_seed(1), 20)
     pts = [fides.to_device(si.uniform_poly(st, ctx.q, N)) for _ in idx]
-    lt_keys = {k: dK[1 + (k % (len(dK) - 1))] for k in sorted({i % n1 for i in idx if i % n1} |
-                                                                {n1 * (i // n1) for i in idx if i // n1})}
+    lt_keys = [ctx.rotation_key(dK[1 + (k % (len(dK) - 1))], k)
+               for k in sorted({i % n1 for i in idx if i % n1} | {n1 * (i // n1) for i in idx if i // n1})]
     out = torch.empty(2 * nl * N, dtype=torch.int64, device="cuda")
     words = (7 + 2) * 2 * nl * N
     work = torch.empty(words, dtype=torch.int64, device="cuda")
@@ -840,8 +866,8 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
     st2 = si.Stream(si.workload_seed(0), 21)
     sa = fides.to_device(np.stack([si.uniform_poly(st2, sq, sctx.N) for _ in range(2)]))
     sb = fides.to_device(np.stack([si.uniform_poly(st2, sq, sctx.N) for _ in range(2)]))
-    skey = fides.to_device(np.stack([np.stack([si.uniform_poly(st2, sq + sp, sctx.N) for _ in range(2)])
-                                     for _ in range(S.dnum)]))
+    skey = sctx.relin_key(fides.to_device(np.stack([np.stack([si.uniform_poly(st2, sq + sp, sctx.N)
+                                                              for _ in range(2)]) for _ in range(S.dnum)])))
     so = torch.empty_like(sa)
     t_small = timed(lambda: sctx.hmult(sa, sb, S.nq, skey, so), 200)
     l0 = fides.kernel_launches()
@@ -898,8 +924,8 @@ def run_bootstrap(args):
     t_plan = time.perf_counter() - t0
     st = si.Stream(si.workload_seed(4), 30)
     key = fides.to_device(np.stack([np.stack([si.uniform_poly(st, q + p, N) for _ in range(2)]) for _ in range(3)]))
-    rks = {s: key.clone() for s in prog.rot_steps}
-    rlk, ck = key.clone(), key.clone()
+    rks = [ctx.rotation_key(key.clone(), s) for s in prog.rot_steps]
+    rlk, ck = ctx.relin_key(key.clone()), ctx.conjugation_key(key.clone())
     t0 = time.perf_counter()
     dp = bt.DeviceProgram(ctx, prog, rlk, ck, rks)
     t_load = time.perf_counter() - t0
@@ -1121,21 +1147,58 @@ def oracle_steps(P, q, p, A, B, keys, budget_s, max_steps):
     ctx = oracle.Context(P.logN, q, p, P.dnum)
     done, t0 = 0, time.perf_counter()
     while done < max_steps:
-        i = done % POOL
+        i = done % len(A)
         out = ctx.hmult(A[i], B[i], keys[0])
         ctx.rescale(out)
-        ctx.rotate(A[i], 1 << (done % N_ROT), keys[1 + done % N_ROT])
+        ctx.rotate(A[i], 1 << (done % N_ROT), keys[1 + done % (len(keys) - 1)])
         done += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     return done, time.perf_counter() - t0
 
 
+def small_inputs():
+    """The logN=12 workload (3 x 40-bit q, 1 x 50-bit p, dnum=3): two ciphertext
+    pairs, a relinearisation key and two rotation keys, from its own seed."""
+    import oracle
+    P = si.SMALL
+    q = oracle.find_primes(P.logN, P.q_bits, P.nq)
+    p = oracle.find_primes(P.logN, P.p_bits, P.nk, exclude=q)
+    st = si.Stream(si.workload_seed(0), 10)
+    N = 1 << P.logN
+    A = [np.stack([si.uniform_poly(st, q, N) for _ in range(2)]) for _ in range(2)]
+    B = [np.stack([si.uniform_poly(st, q, N) for _ in range(2)]) for _ in range(2)]
+    keys = [np.stack([np.stack([si.uniform_poly(st, q + p, N) for _ in range(2)]) for _ in range(P.dnum)])
+            for _ in range(3)]
+    return P, q, p, A, B, keys
+
+
 def cpu_baseline(P, q, p, A, B, keys, budget_s):
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """The oracle as it stands, on the host cores: the bench workload with the
+    OpenMP loops on every core (the headline `value`) and on one thread, and
+    the logN=12 workload on both."""
+    import oracle
+    cores = oracle.set_threads(0)
     done, el = oracle_steps(P, q, p, A, B, keys, budget_s, 1000)
-    return {"value": round(2 * done / el, 4), "unit": "ops/s", "cores": cores, "kind": "oracle",
-            "sample": "%d step(s) of the same workload (HMult+relin, Rescale, HRotate at 30 limbs), %.1f s" % (done, el)}
+    res = {"value": round(2 * done / el, 4), "unit": "ops/s", "cores": cores, "kind": "oracle",
+           "sample": "%d step(s) of the same workload (HMult+relin, Rescale, HRotate at 30 limbs), %.1f s" % (done, el)}
+    oracle.set_threads(1)
+    try:
+        d1, e1 = oracle_steps(P, q, p, A, B, keys, 0.0, 1)
+        res["single_thread"] = {"value": round(2 * d1 / e1, 4), "unit": "ops/s", "cores": 1,
+                                "sample": "%d step of the same workload, %.1f s" % (d1, e1)}
+        Ps, qs, ps, As, Bs, Ks = small_inputs()
+        small = {"workload": "HMult+relin, Rescale, HRotate of one logN=12 pair (3 x 40-bit q, 1 x 50-bit p, "
+                             "dnum=3)", "unit": "ops/s"}
+        for n in (1, cores):
+            oracle.set_threads(n)
+            ds, es = oracle_steps(Ps, qs, ps, As, Bs, Ks, 1.5, 10000)
+            small["cores_%d" % n] = {"value": round(2 * ds / es, 2), "cores": n,
+                                     "sample": "%d steps, %.2f s" % (ds, es)}
+        res["small_config"] = small
+    finally:
+        oracle.set_threads(cores)
+    return res
 
 
 def run_reference(args, world, rank):
@@ -1156,8 +1219,7 @@ def run_reference(args, world, rank):
     return {"metric": METRIC, "value": round(value, 4), "unit": "ops/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(el / done * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "single-op path logN=16 L=30 K=10 dnum=3: HMult+relin, Rescale, HRotate(2^(k mod 15))",
-                       "logN": P.logN, "limbs": P.nq, "special_primes": P.nk, "dnum": P.dnum},
+            "config": workload_config(P, world),
             "cpu_baseline": {"value": round(value, 4), "unit": "ops/s", "cores": cores, "kind": "oracle",
                              "sample": "%d of %d steps timed (capped at 40 steps / 120 s)" % (done, args.steps)},
             "e2e": {"value": round(value, 4), "unit": "ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -35,12 +35,16 @@
  *    Programs (fides_program_run) are the exception: each run uses the scratch
  *    inside its own work buffer, so runs with different work buffers may
  *    overlap on several streams of one context.
- *  - Key buffers (relinearisation, rotation, conjugation keys) are read while
- *    the kernels queued before them on the same stream may still be finishing
- *    (they stream in during the previous kernel's last wave).  Fill them with
- *    copies, or with kernels that complete before the call's first kernel
- *    starts (any kernel that does not allow programmatic dependent launch),
- *    not with a kernel still running under programmatic launch.
+ *  - Switching keys (relinearisation, rotation, conjugation) are passed as
+ *    handles from fides_key_register, which binds a caller-owned key buffer
+ *    to the Galois element it switches from.  A key's contents must be final
+ *    when it is registered and must not change while the handle exists: the
+ *    key switch reads key words before it waits for the kernels queued ahead
+ *    of it (they stream in during the previous kernel's last wave), and every
+ *    fides_* kernel lets the next one start early (programmatic dependent
+ *    launch), so a key written by a kernel still in flight -- a fides_ntt on
+ *    the same stream, say -- could be read half-written.  Registration
+ *    synchronises the context's device, which ends any such writer.
  *  - Return value: FIDES_OK (0) or a negative FIDES_ERR_* code; the message of
  *    the last error on the calling thread is available from fides_last_error().
  *    Argument errors are detected before anything is queued.
@@ -77,6 +81,30 @@ typedef struct {
     double scale;
 } fides_ct;
 
+/*
+ * Switching-key handles (Sec. II hybrid key switching; Table I: HMult
+ * relinearises with the key of s^2, HRotate by k slots needs the key of
+ * s(X^g) with g = 5^k mod 2N, Conjugate the key of s(X^(2N-1))).
+ *   dev_key    : device buffer [dnum][2][L + K][N] of the context's shape (see
+ *                the conventions above), 8-byte aligned, owned by the caller,
+ *                valid and unchanged until fides_key_destroy.
+ *   galois_elt : FIDES_GALOIS_RELIN (0) for a relinearisation key, otherwise
+ *                the odd Galois element g in [1, 2N) of the automorphism the
+ *                key undoes (fides_galois_elt for rotations, 2N - 1 for
+ *                conjugation).
+ * fides_key_register checks the arguments (FIDES_ERR_ARG: NULL or unaligned
+ * buffer, memory that is not on the context's device, a Galois element that is
+ * not 0 or odd below 2N), synchronises the context's device (so that whatever
+ * filled the buffer has finished) and returns a handle, a small host object;
+ * the buffer is referenced, not copied.  Every entry point that switches keys
+ * checks the handle before it queues anything and returns FIDES_ERR_KEY when
+ * the key belongs to another context or to another Galois element than the
+ * operation needs.  Destroy handles after the work that uses them completes;
+ * fides_key_destroy(NULL) does nothing.
+ */
+typedef struct fides_key fides_key;
+#define FIDES_GALOIS_RELIN 0
+
 /* Last error message of the calling thread ("" if none). */
 const char *fides_last_error(void);
 
@@ -97,14 +125,14 @@ int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, in
  *   logN   : ring degree N = 2^logN, 12 <= logN <= 17 (one tile per limb at
  *            12; two-pass NTTs above).
  *   L      : number of q-primes (maximum ciphertext limbs), 1 <= L.
- *   K      : number of special primes, 1 <= K, L + K <= 64.
  *   dnum   : number of key-switching digits, 1 <= dnum <= L.
  *   primes : host array of L q-primes then K special primes, each prime,
  *            = 1 mod 2N, < 2^61, all distinct.
+ *   K      : number of special primes, 1 <= K, L + K <= 64.
  * Owns device tables (twiddles with Shoup companions, base-conversion
  * matrices) and a scratch pool sized for one operation at the top level.
  */
-int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out);
+int fides_ctx_create(int logN, int L, int dnum, const uint64_t *primes, int K, fides_ctx **out);
 void fides_ctx_destroy(fides_ctx *ctx);
 
 /*
@@ -166,6 +194,11 @@ uint64_t fides_ctx_psi(const fides_ctx *ctx, int prime_index);
 /* Galois element of a left rotation by `steps` slots: 5^steps mod 2N. */
 uint64_t fides_galois_elt(const fides_ctx *ctx, int64_t steps);
 
+int fides_key_register(fides_ctx *ctx, const uint64_t *dev_key, uint64_t galois_elt, fides_key **out);
+void fides_key_destroy(fides_key *key);
+/* Galois element a handle was registered with (0 for a NULL handle). */
+uint64_t fides_key_galois(const fides_key *key);
+
 /*
  * Forward / inverse negacyclic NTT (Sec. III-F4), in place, on `batch`
  * polynomials of n_limbs limbs each stored back to back; limb z of every
@@ -195,20 +228,21 @@ int fides_moddown(fides_ctx *ctx, const uint64_t *dev_x, int n_limbs, uint64_t *
 
 /*
  * Hybrid key switching of one polynomial d (n_limbs limbs, evaluation form)
- * with key dev_evk ([dnum][2][L+K][N]): ModUp, key inner product
+ * with key evk (any registered key of this context): ModUp, key inner product
  * acc_t = sum_j d~_j evk_{j,t} (Sec. III-F5 "Dot product fusion"), ModDown of
  * both accumulators.  Output (dev_out0, dev_out1), each [n_limbs][N], with
- * out0 + out1 s ~= d s'.
+ * out0 + out1 s ~= d s', s' the secret the key switches from.
  */
-int fides_keyswitch(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, const uint64_t *dev_evk,
+int fides_keyswitch(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, const fides_key *evk,
                     uint64_t *dev_out0, uint64_t *dev_out1, void *stream);
 
 /*
  * HMult with relinearisation (Table I): d0 = a0 b0, d1 = a0 b1 + a1 b0,
  * d2 = a1 b1, out = (d0, d1) + KeySwitch(d2, rlk).  a, b and out have the
  * same n_limbs; out->scale = a->scale * b->scale.  out may not alias a or b.
+ * rlk: a key registered with FIDES_GALOIS_RELIN (FIDES_ERR_KEY otherwise).
  */
-int fides_hmult(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint64_t *dev_rlk,
+int fides_hmult(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const fides_key *rlk,
                 fides_ct *out, void *stream);
 
 /*
@@ -222,15 +256,16 @@ int fides_hmult(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint
  * q_l^-1 (d_i + P^-1 acc_i - NTT(P^-1 conv_i + [last]_{q_i})).  out may not
  * alias a or b.
  */
-int fides_hmult_rescale(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const uint64_t *dev_rlk,
+int fides_hmult_rescale(fides_ctx *ctx, const fides_ct *a, const fides_ct *b, const fides_key *rlk,
                         fides_ct *out, void *stream);
 
 /*
  * HRotate (Table I): rotation of the slots left by `steps` (g = 5^steps mod
  * 2N); out = (sigma_g(c0) + ks0, ks1) with (ks0, ks1) = KeySwitch(sigma_g(c1),
- * rk) and rk the switching key of s(X^g).  out may not alias a.
+ * rk) and rk the switching key of s(X^g), registered with that g
+ * (FIDES_ERR_KEY otherwise, nothing queued).  out may not alias a.
  */
-int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const uint64_t *dev_rk,
+int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const fides_key *rk,
                  fides_ct *out, void *stream);
 
 /*
@@ -255,14 +290,15 @@ int fides_rescale_round(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *
  * HSquare (Table I): HMult+relin of a with itself, identical to
  * fides_hmult(ctx, a, a, rlk, out, stream).  out may not alias a.
  */
-int fides_hsquare(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_rlk, fides_ct *out, void *stream);
+int fides_hsquare(fides_ctx *ctx, const fides_ct *a, const fides_key *rlk, fides_ct *out, void *stream);
 
 /*
  * Conjugate (Table I): the automorphism g = 2N - 1 (every slot to its
- * complex conjugate) with key switching by dev_ck, the switching key of
- * s(X^(2N-1)); otherwise as fides_rotate.  out may not alias a.
+ * complex conjugate) with key switching by ck, the switching key of
+ * s(X^(2N-1)) registered with g = 2N - 1; otherwise as fides_rotate.  out may
+ * not alias a.
  */
-int fides_conjugate(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_ck, fides_ct *out, void *stream);
+int fides_conjugate(fides_ctx *ctx, const fides_ct *a, const fides_key *ck, fides_ct *out, void *stream);
 
 /*
  * Hoisted rotations (Sec. III-F6): n_rot rotations of one ciphertext sharing
@@ -276,14 +312,14 @@ int fides_conjugate(fides_ctx *ctx, const fides_ct *a, const uint64_t *dev_ck, f
  * conversion does not commute with the automorphism's sign flips), but both
  * decrypt to the rotated message with the same noise bound.
  *   steps : host array [n_rot]
- *   rks   : host array [n_rot] of device keys (switching keys of s(X^{g_k}))
+ *   rks   : host array [n_rot] of key handles, rks[k] registered with g_k
  *   outs  : host array [n_rot] of output descriptors at a->n_limbs; none may
  *           alias a.  out scales are set to a->scale.
  * 1 <= n_rot <= 64.  Uses the context's scratch (one ModUp + one key
  * switch's accumulators); rotations run one after another on `stream`.
  */
 int fides_rotate_hoisted(fides_ctx *ctx, const fides_ct *a, int n_rot, const int64_t *steps,
-                         const uint64_t *const *dev_rks, fides_ct *outs, void *stream);
+                         const fides_key *const *rks, fides_ct *outs, void *stream);
 
 /*
  * Linear transform of the slots (the diagonal method with a baby-step
@@ -295,9 +331,10 @@ int fides_rotate_hoisted(fides_ctx *ctx, const fides_ct *a, int n_rot, const int
  *   pts      : host [n_diag] of device plaintexts [n_limbs][N] (evaluation form):
  *              pts[k] encodes rot_{-n1 floor(i/n1)}(d_i) for i = diag_idx[k]
  *              at scale pt_scale (pre-rotated, as the split requires)
- *   keys     : host arrays [n_keys] of step counts and device rotation keys;
- *              one is needed for every baby step b != 0 and every giant step
- *              n1 g != 0 in use (FIDES_ERR_KEY before anything is queued if not)
+ *   keys     : host array [n_keys] of rotation-key handles; a key of Galois
+ *              element 5^b mod 2N is needed for every baby step b != 0 and one
+ *              of 5^(n1 g) for every giant step n1 g != 0 in use (FIDES_ERR_KEY
+ *              before anything is queued if one is missing)
  *   work     : device scratch of fides_linear_transform_work_words() words
  *   out      : result at a's level, scale a->scale * pt_scale; may not alias a
  * The residues equal those of: hoisted rotations of a by the baby steps, a
@@ -307,8 +344,8 @@ int fides_linear_transform_work_words(fides_ctx *ctx, int n_limbs, int n_diag, c
                                       size_t *words);
 int fides_linear_transform(fides_ctx *ctx, const fides_ct *a, int n_diag, const int *diag_idx,
                            const uint64_t *const *dev_pts, double pt_scale, int n1, int n_keys,
-                           const int64_t *key_steps, const uint64_t *const *dev_keys, uint64_t *dev_work,
-                           size_t work_words, fides_ct *out, void *stream);
+                           const fides_key *const *keys, uint64_t *dev_work, size_t work_words, fides_ct *out,
+                           void *stream);
 
 /*
  * ModRaise (bootstrapping, Sec. III-F7): a ciphertext at one limb (modulo
@@ -359,20 +396,38 @@ int fides_scalar_mult(fides_ctx *ctx, const fides_ct *a, const uint64_t *k, doub
  * outputs; ops of one stage must be independent (no op writes what another
  * op of its stage reads or writes).
  *
+ * The ops of a stage run in launch groups of at most `group_limbs` ciphertext
+ * limbs (consecutive ops of the stage, at least one per group; 0 = the whole
+ * stage is one group): one launch per step of the key switch covers every op
+ * of a group, and groups run one after another, sharing one scratch pool
+ * sized for the largest group (one key switch's worth per HMult/HRotate, two
+ * limbs per Rescale).  The group size trades launch size against cache
+ * locality (the paper's limb-batch trade-off, Sec. III-F1 and Sec. IV).
+ *
  * fides_batch_create validates every op (FIDES_ERR_ARG naming the op on
- * error), sets each op's out.scale, allocates the batch's own scratch (one
- * key switch's worth per HMult/HRotate, two limbs per Rescale) and uploads
+ * error; FIDES_ERR_KEY for a key handle of another context or Galois
+ * element), sets each op's out.scale, plans one group per stage with the
+ * HMult tensor product as its own pass, allocates the scratch and uploads
  * device tables describing every launch; it synchronises.
- * fides_batch_run enqueues the whole batch on `stream`: one launch per step
- * of the key switch per stage, covering every op of the stage.  Results are
- * identical to calling fides_hmult / fides_rotate / fides_rescale op by op.
+ * fides_batch_run enqueues the whole batch on `stream`.  Results are
+ * identical to calling fides_hmult / fides_rotate / fides_rescale op by op,
+ * whatever the grouping.
  * fides_batch_capture records one run into a CUDA graph (stream must not be
  * NULL); later fides_batch_run calls launch that graph.
  * fides_batch_info reports the kernels one run launches and the device bytes
  * the batch owns.  Runs of one batch must not overlap on the GPU.
+ * fides_batch_configure re-plans with a group size and tensor_split (1: the
+ * tensor product as its own 16-byte pass where the buffers allow, 0: fused
+ * into the first INTT pass); fides_batch_autotune runs the batch on `stream`
+ * for each group size 0, 32, 64, ... below the largest stage's limbs and both
+ * tensor placements, keeps the fastest (its time per run in *best_ms, may be
+ * NULL) and shrinks the scratch to it; fides_batch_tuning reports the
+ * current choice and the number of launch groups.  Configure and autotune
+ * synchronise the device, overwrite the ops' outputs (autotune runs the
+ * batch) and drop a captured graph (capture again afterwards).
  */
-#define FIDES_OP_HMULT 1    /* out = HMult+relin(a, b) with key = relinearisation key */
-#define FIDES_OP_ROTATE 2   /* out = HRotate(a, steps) with key = rotation key of 5^steps */
+#define FIDES_OP_HMULT 1    /* out = HMult+relin(a, b) with key = relinearisation key (Galois element 0) */
+#define FIDES_OP_ROTATE 2   /* out = HRotate(a, steps) with key = rotation key of 5^steps mod 2N */
 #define FIDES_OP_RESCALE 3  /* out = Rescale(a), out.n_limbs = a.n_limbs - 1 */
 
 typedef struct {
@@ -381,7 +436,7 @@ typedef struct {
     fides_ct a;
     fides_ct b;
     fides_ct out;
-    const uint64_t *key;
+    const fides_key *key;   /* HMULT, ROTATE (FIDES_ERR_KEY at creation if it does not fit) */
     int64_t steps;
 } fides_op;
 
@@ -392,6 +447,9 @@ int fides_batch_run(fides_batch *batch, void *stream);
 int fides_batch_capture(fides_batch *batch, void *stream);
 int fides_batch_info(const fides_batch *batch, int *launches, size_t *scratch_bytes, size_t *table_bytes);
 void fides_batch_destroy(fides_batch *batch);
+int fides_batch_configure(fides_batch *batch, int group_limbs, int tensor_split);
+int fides_batch_autotune(fides_batch *batch, void *stream, double *best_ms);
+int fides_batch_tuning(const fides_batch *batch, int *group_limbs, int *tensor_split, int *groups);
 
 /*
  * Request server: continuous batching of HMult+relin, HRotate and Rescale
@@ -424,12 +482,12 @@ void fides_batch_destroy(fides_batch *batch);
  * single-operation calls on the same context may run alongside, but
  * fides_ctx_autotune must not.
  *
- * Keys: fides_server_set_relin_key / fides_server_add_rotation_key register
- * device keys ([dnum][2][L+K][N], as for fides_hmult / fides_rotate; rotation
- * keys by step count, modulo N/2).  Keys must stay valid until destroy, and
- * hold their final contents before the first request that uses them is
- * submitted (the server's lanes run on streams of their own; synchronise the
- * copy or kernel that fills a key first).
+ * Keys: fides_server_set_relin_key takes the relinearisation key and
+ * fides_server_add_rotation_key the key of rotations by `steps` (modulo N/2),
+ * both as handles (fides_key_register) of the server's context registered with
+ * Galois element 0 and 5^steps mod 2N respectively (FIDES_ERR_KEY otherwise).
+ * Handles and their buffers must stay valid until destroy.  In simulation
+ * there is no context, and handles are tokens that are never dereferenced.
  *
  * fides_server_submit validates and queues one request and returns its id:
  *   FIDES_ERR_ARG       bad type, NULL input, level outside [1, L] (Rescale:
@@ -508,8 +566,8 @@ typedef struct fides_server fides_server;
 
 int fides_server_create(fides_ctx *ctx, const fides_server_config *cfg, fides_server **out);
 void fides_server_destroy(fides_server *srv);
-int fides_server_set_relin_key(fides_server *srv, const uint64_t *dev_key);
-int fides_server_add_rotation_key(fides_server *srv, int64_t steps, const uint64_t *dev_key);
+int fides_server_set_relin_key(fides_server *srv, const fides_key *key);
+int fides_server_add_rotation_key(fides_server *srv, int64_t steps, const fides_key *key);
 int fides_server_submit(fides_server *srv, const fides_request *req, uint64_t *id_out);
 int fides_server_poll(fides_server *srv, fides_completion *out, int max, int64_t timeout_us, int *n_out);
 int fides_server_release(fides_server *srv, uint64_t id);
@@ -543,7 +601,8 @@ int64_t fides_now_ns(void);
  *         1..32 terms, each register with at least b limbs, read in place;
  *         scale = scale(r_0) * const_scale[c_0])
  * fides_program_create checks the program (operands defined before use,
- * levels consistent, keys present; FIDES_ERR_ARG naming the instruction),
+ * levels consistent, keys present; FIDES_ERR_ARG naming the instruction; a key
+ * of another context or element: FIDES_ERR_KEY),
  * copies every host table (device plaintexts and keys are referenced and must
  * outlive the program) and maps the virtual registers onto as few
  * ciphertext-sized buffers as their lifetimes allow.
@@ -592,10 +651,9 @@ typedef struct {
     int n_const;
     const uint64_t *const *consts;   /* host [n_const] arrays of L residues */
     const double *const_scale;
-    const uint64_t *dev_relin_key, *dev_conj_key;
+    const fides_key *relin_key, *conj_key;    /* NULL when the program needs none */
     int n_rot_keys;
-    const int64_t *rot_steps;
-    const uint64_t *const *dev_rot_keys;
+    const fides_key *const *rot_keys;         /* found by Galois element (5^k mod 2N for a rotation by k) */
     int n_lin;                       /* CMAC term lists */
     const int *lin_start;            /* [n_lin + 1] offsets */
     const int *lin_reg, *lin_const;  /* [lin_start[n_lin]] */
@@ -623,6 +681,9 @@ void fides_program_destroy(fides_program *prog);
  *   - The context's device must be current (FIDES_ERR_ARG otherwise).
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *     The address is kept until the process exits, so a device reset
+ *     (cudaDeviceReset) after the first call is not supported (it also
+ *     invalidates every context on that device).
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.
  *   - Every call shares the one array, which keeps the last call's contents:
  *     calls whose work overlaps on the GPU (other streams, other threads)

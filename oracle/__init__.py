@@ -54,6 +54,8 @@ def lib():
         L.or_ctx_alpha.argtypes = [ctypes.c_void_p]
         L.or_beta.restype = ctypes.c_int
         L.or_beta.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_set_threads.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_mul_mod.restype = ctypes.c_uint64
         L.or_mul_mod.argtypes = [ctypes.c_uint64] * 3
         L.or_pow_mod.restype = ctypes.c_uint64
@@ -121,6 +123,11 @@ def _i32(a) -> np.ndarray:
 
 
 # -- number theory ----------------------------------------------------------
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (timing only); returns the count in effect."""
+    return int(lib().or_set_threads(int(n)))
+
 
 def is_prime(n: int) -> bool:
     return bool(lib().or_is_prime(n))

@@ -26,6 +26,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <omp.h>
+
 typedef uint64_t u64;
 typedef int64_t i64;
 typedef unsigned __int128 u128;
@@ -162,6 +164,15 @@ typedef struct {
     u64 *ipsi_brv;   /* [np][N]: psi^-brv(k) */
     u64 *n_inv;      /* N^-1 mod prime i */
 } or_ctx;
+
+/* Thread count of the OpenMP loops over limbs and digits, for timing the
+ * oracle on one core or on all of them; no result depends on it.  Returns the
+ * count now in effect. */
+int or_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 void or_ctx_free(or_ctx *c)
 {

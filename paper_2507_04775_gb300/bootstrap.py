@@ -325,11 +325,14 @@ class DeviceProgram:
     prime of the transform's level and transformed on the device) or as
     evaluation-form residues (``lt["pts"]``, [limbs][N])."""
 
-    def __init__(self, ctx, prog, relin_key, conj_key, rot_keys: dict, in_limbs: int = 1):
+    def __init__(self, ctx, prog, relin_key, conj_key, rot_keys, in_limbs: int = 1):
+        """relin_key, conj_key: Keys (or None); rot_keys: rotation Keys (a list,
+        or a dict whose values are used), found by their Galois elements."""
         import torch
         self.ctx = ctx
         N = ctx.N
-        self._keep = [relin_key, conj_key] + list(rot_keys.values())
+        rot = list(rot_keys.values()) if isinstance(rot_keys, dict) else list(rot_keys)
+        self._keep = [relin_key, conj_key] + rot
         self._pts = []
         lt_arr = (F.fides_lt * max(1, len(prog.lts)))()
         self._lt_tabs = []
@@ -365,9 +368,7 @@ class DeviceProgram:
         self._const_rows = const_rows
         cptr = (ctypes.c_void_p * max(1, len(const_rows)))(*[r.ctypes.data for r in const_rows])
         cscale = (ctypes.c_double * max(1, len(prog.const_scale)))(*prog.const_scale)
-        steps = sorted(rot_keys)
-        st = (ctypes.c_int64 * max(1, len(steps)))(*steps)
-        kp = (ctypes.c_void_p * max(1, len(steps)))(*[rot_keys[s].data_ptr() for s in steps])
+        kp = (ctypes.c_void_p * max(1, len(rot)))(*[F._key(k) for k in rot])
         d = F.fides_program_desc()
         d.n_instr, d.instr = len(prog.instr), ctypes.cast(ins, ctypes.POINTER(F.fides_instr))
         d.n_regs, d.in_reg, d.out_reg, d.in_limbs = prog.n_regs, prog.in_reg, prog.out_reg, in_limbs
@@ -376,11 +377,10 @@ class DeviceProgram:
         d.n_const = len(const_rows)
         d.consts = ctypes.cast(cptr, ctypes.POINTER(ctypes.c_void_p))
         d.const_scale = ctypes.cast(cscale, ctypes.POINTER(ctypes.c_double))
-        d.dev_relin_key = relin_key.data_ptr() if relin_key is not None else None
-        d.dev_conj_key = conj_key.data_ptr() if conj_key is not None else None
-        d.n_rot_keys = len(steps)
-        d.rot_steps = ctypes.cast(st, ctypes.POINTER(ctypes.c_int64))
-        d.dev_rot_keys = ctypes.cast(kp, ctypes.POINTER(ctypes.c_void_p))
+        d.relin_key = F._key(relin_key) if relin_key is not None else None
+        d.conj_key = F._key(conj_key) if conj_key is not None else None
+        d.n_rot_keys = len(rot)
+        d.rot_keys = ctypes.cast(kp, ctypes.POINTER(ctypes.c_void_p))
         lins = getattr(prog, "lins", [])
         starts = [0]
         for lin in lins:
@@ -392,7 +392,7 @@ class DeviceProgram:
         d.lin_start = ctypes.cast(ls, ctypes.POINTER(ctypes.c_int))
         d.lin_reg = ctypes.cast(lr, ctypes.POINTER(ctypes.c_int))
         d.lin_const = ctypes.cast(lc, ctypes.POINTER(ctypes.c_int))
-        self._refs = (ins, lt_arr, cptr, cscale, st, kp, ls, lr, lc)
+        self._refs = (ins, lt_arr, cptr, cscale, kp, ls, lr, lc)
         h = ctypes.c_void_p()
         F._check(F.lib().fides_program_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
         self._h = h

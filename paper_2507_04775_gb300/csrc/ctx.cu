@@ -205,6 +205,57 @@ extern "C" uint64_t fides_galois_elt(const fides_ctx *c, int64_t steps)
     return hpow(5, (u64)k, 2 * (u64)c->N);
 }
 
+// ---------------------------------------------------------------------------
+// Switching-key handles
+// ---------------------------------------------------------------------------
+int fides_check_key(const fides_ctx *c, const fides_key *k, u64 g, const char *what)
+{
+    if (!k) return fides_set_error(FIDES_ERR_ARG, "%s: key handle is NULL", what);
+    if (k->ctx != c) return fides_set_error(FIDES_ERR_KEY, "%s: the key was registered with another context", what);
+    if (g != FIDES_GALOIS_ANY && k->g != g)
+        return fides_set_error(FIDES_ERR_KEY, "%s: the key switches from Galois element %llu, the operation needs %llu",
+                               what, (unsigned long long)k->g, (unsigned long long)g);
+    return FIDES_OK;
+}
+
+extern "C" int fides_key_register(fides_ctx *c, const uint64_t *dev_key, uint64_t g, fides_key **out)
+{
+    const char *fn = "fides_key_register";
+    if (!out) return fides_set_error(FIDES_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    if (!c || !dev_key) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    if ((uintptr_t)dev_key % 8) return fides_set_error(FIDES_ERR_ARG, "%s: key buffer not 8-byte aligned", fn);
+    if (g != 0 && (g % 2 == 0 || g >= 2 * (u64)c->N))
+        return fides_set_error(FIDES_ERR_ARG, "%s: Galois element %llu is neither 0 nor odd below 2N = %d", fn,
+                               (unsigned long long)g, 2 * c->N);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, dev_key) != cudaSuccess) {
+        cudaGetLastError();
+        return fides_set_error(FIDES_ERR_ARG, "%s: the key buffer is not CUDA memory", fn);
+    }
+    const bool on_dev = (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device;
+    if (!on_dev) return fides_set_error(FIDES_ERR_ARG, "%s: the key buffer is not memory of device %d", fn, c->device);
+    // whatever filled the buffer (a copy, a kernel of this library still
+    // running under programmatic launch) finishes before the key is used
+    int cur = -1;
+    if (int rc = fides_check_cuda(cudaGetDevice(&cur), fn)) return rc;
+    if (cur != c->device && fides_check_cuda(cudaSetDevice(c->device), fn)) return FIDES_ERR_CUDA;
+    int rc = fides_check_cuda(cudaDeviceSynchronize(), fn);
+    if (cur != c->device) cudaSetDevice(cur);
+    if (rc) return rc;
+    fides_key *k = (fides_key *)calloc(1, sizeof(fides_key));
+    if (!k) return fides_set_error(FIDES_ERR_NOMEM, "%s: host allocation", fn);
+    k->ctx = c;
+    k->data = dev_key;
+    k->g = g;
+    *out = k;
+    return FIDES_OK;
+}
+
+extern "C" void fides_key_destroy(fides_key *k) { free(k); }
+
+extern "C" uint64_t fides_key_galois(const fides_key *k) { return k ? k->g : 0; }
+
 // fp16 bits of an integer 0 <= k < 256 (exact: at most 8 significant bits).
 static uint16_t f16_of_byte(unsigned k)
 {
@@ -260,7 +311,7 @@ static size_t scratch_words_for(int L, int K, int dnum, int alpha, int N)
     return (size_t)N * (2 * (size_t)L + beta * ne + 2 * ne + 2 * (size_t)K + 2 * (size_t)L + 2 + 2 * (size_t)L + 4);
 }
 
-extern "C" int fides_ctx_create(int logN, int L, int K, int dnum, const uint64_t *primes, fides_ctx **out)
+extern "C" int fides_ctx_create(int logN, int L, int dnum, const uint64_t *primes, int K, fides_ctx **out)
 {
     if (!out) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_create: out is NULL");
     *out = nullptr;

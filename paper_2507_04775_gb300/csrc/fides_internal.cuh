@@ -164,6 +164,17 @@ struct fides_ctx {
     unsigned char ntt_var[4][FIDES_TUNE_MAX + 1];
 };
 
+// A registered switching key: the caller's buffer [dnum][2][L+K][N] and the
+// Galois element it switches from (0: relinearisation, s^2).
+struct fides_key {
+    const fides_ctx *ctx;
+    const u64 *data;
+    u64 g;
+};
+
+// Galois element any key is accepted for (fides_keyswitch)
+#define FIDES_GALOIS_ANY (~(u64)0)
+
 // ---------------------------------------------------------------------------
 // Device modular arithmetic
 // ---------------------------------------------------------------------------
@@ -260,6 +271,11 @@ __device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
 // ---------------------------------------------------------------------------
 int fides_set_error(int code, const char *fmt, ...);
 int fides_check_cuda(cudaError_t e, const char *what);
+
+// Checks that `k` is a key of context c registered with Galois element g
+// (FIDES_GALOIS_ANY: any element); FIDES_ERR_ARG for a NULL handle,
+// FIDES_ERR_KEY for another context or element.  `what` names the caller.
+int fides_check_key(const fides_ctx *c, const fides_key *k, u64 g, const char *what);
 
 // out = sum_t cts[t] (.) pts[t] (+ out when accumulate), ciphertexts [2][nl][N]
 // and plaintexts [nl][N] in evaluation form (elementwise.cu)

@@ -209,20 +209,23 @@ extern "C" int fides_moddown(fides_ctx *c, const uint64_t *x, int nl, uint64_t *
     return ntt_forward(c, inline_set(v), ProSrc{}, EpiSubMul{}, st);
 }
 
-extern "C" int fides_keyswitch(fides_ctx *c, const uint64_t *d, int nl, const uint64_t *evk, uint64_t *out0,
+extern "C" int fides_keyswitch(fides_ctx *c, const uint64_t *d, int nl, const fides_key *evk, uint64_t *out0,
                                uint64_t *out1, void *stream)
 {
     if (int rc = check_ctx(c, "fides_keyswitch")) return rc;
     if (int rc = check_level(c, nl, "fides_keyswitch")) return rc;
-    if (!d || !evk || !out0 || !out1) return fides_set_error(FIDES_ERR_ARG, "fides_keyswitch: NULL buffer");
+    if (!d || !out0 || !out1) return fides_set_error(FIDES_ERR_ARG, "fides_keyswitch: NULL buffer");
+    if (int rc = fides_check_key(c, evk, FIDES_GALOIS_ANY, "fides_keyswitch")) return rc;
     OpTrace op("op_keyswitch", as_stream(stream));
-    return run_keyswitch(c, ks_buffers(c, d, nl, evk, out0, out1, 0, 0, carve(c, nullptr)), as_stream(stream));
+    return run_keyswitch(c, ks_buffers(c, d, nl, evk->data, out0, out1, 0, 0, carve(c, nullptr)), as_stream(stream));
 }
 
-extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
+extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, const fides_key *rlk, fides_ct *out,
                            void *stream)
 {
-    return fides_hmult_ws(c, a, b, rlk, out, stream, nullptr);
+    if (int rc = check_ctx(c, "fides_hmult")) return rc;
+    if (int rc = fides_check_key(c, rlk, FIDES_GALOIS_RELIN, "fides_hmult")) return rc;
+    return fides_hmult_ws(c, a, b, rlk->data, out, stream, nullptr);
 }
 
 int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
@@ -256,10 +259,12 @@ int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uin
     return rc;
 }
 
-extern "C" int fides_hmult_rescale(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk,
+extern "C" int fides_hmult_rescale(fides_ctx *c, const fides_ct *a, const fides_ct *b, const fides_key *rlk,
                                    fides_ct *out, void *stream)
 {
-    return fides_hmult_rescale_ws(c, a, b, rlk, out, stream, nullptr);
+    if (int rc = check_ctx(c, "fides_hmult_rescale")) return rc;
+    if (int rc = fides_check_key(c, rlk, FIDES_GALOIS_RELIN, "fides_hmult_rescale")) return rc;
+    return fides_hmult_rescale_ws(c, a, b, rlk->data, out, stream, nullptr);
 }
 
 // Rescale(HMult(a, b)) in one key switch: the tensor product goes to scratch;
@@ -359,10 +364,12 @@ int fides_rotate_ws(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64
     return automorph_entry(c, a, fides_galois_elt(c, steps), rk, out, stream, "fides_rotate", "op_rotate", ws);
 }
 
-extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, const uint64_t *rk, fides_ct *out,
+extern "C" int fides_rotate(fides_ctx *c, const fides_ct *a, int64_t steps, const fides_key *rk, fides_ct *out,
                             void *stream)
 {
-    return fides_rotate_ws(c, a, steps, rk, out, stream, nullptr);
+    if (int rc = check_ctx(c, "fides_rotate")) return rc;
+    if (int rc = fides_check_key(c, rk, fides_galois_elt(c, steps), "fides_rotate")) return rc;
+    return fides_rotate_ws(c, a, steps, rk->data, out, stream, nullptr);
 }
 
 int fides_conjugate_ws(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fides_ct *out, void *stream, u64 *ws)
@@ -371,20 +378,31 @@ int fides_conjugate_ws(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fide
     return automorph_entry(c, a, 2 * (u64)c->N - 1, ck, out, stream, "fides_conjugate", "op_conjugate", ws);
 }
 
-extern "C" int fides_conjugate(fides_ctx *c, const fides_ct *a, const uint64_t *ck, fides_ct *out, void *stream)
+extern "C" int fides_conjugate(fides_ctx *c, const fides_ct *a, const fides_key *ck, fides_ct *out, void *stream)
 {
-    return fides_conjugate_ws(c, a, ck, out, stream, nullptr);
+    if (int rc = check_ctx(c, "fides_conjugate")) return rc;
+    if (int rc = fides_check_key(c, ck, 2 * (u64)c->N - 1, "fides_conjugate")) return rc;
+    return fides_conjugate_ws(c, a, ck->data, out, stream, nullptr);
 }
 
-extern "C" int fides_hsquare(fides_ctx *c, const fides_ct *a, const uint64_t *rlk, fides_ct *out, void *stream)
+extern "C" int fides_hsquare(fides_ctx *c, const fides_ct *a, const fides_key *rlk, fides_ct *out, void *stream)
 {
     return fides_hmult(c, a, a, rlk, out, stream);
 }
 
 extern "C" int fides_rotate_hoisted(fides_ctx *c, const fides_ct *a, int n_rot, const int64_t *steps,
-                                    const uint64_t *const *rks, fides_ct *outs, void *stream)
+                                    const fides_key *const *rks, fides_ct *outs, void *stream)
 {
-    return fides_rotate_hoisted_ws(c, a, n_rot, steps, rks, outs, stream, nullptr);
+    const char *fn = "fides_rotate_hoisted";
+    if (int rc = check_ctx(c, fn)) return rc;
+    if (!steps || !rks) return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
+    if (n_rot < 1 || n_rot > 64) return fides_set_error(FIDES_ERR_ARG, "%s: n_rot=%d outside [1, 64]", fn, n_rot);
+    const uint64_t *keys[64];
+    for (int k = 0; k < n_rot; ++k) {
+        if (int rc = fides_check_key(c, rks[k], fides_galois_elt(c, steps[k]), fn)) return rc;
+        keys[k] = rks[k]->data;
+    }
+    return fides_rotate_hoisted_ws(c, a, n_rot, steps, keys, outs, stream, nullptr);
 }
 
 int fides_rotate_hoisted_ws(fides_ctx *c, const fides_ct *a, int n_rot, const int64_t *steps,

@@ -149,10 +149,15 @@ int plan_validate(const fides_ctx *c, const fides_op &o, int i, const char *fn)
     case FIDES_OP_HMULT:
         if (!o.b.data || o.b.n_limbs != nl || o.out.n_limbs != nl || !o.key)
             return fides_set_error(FIDES_ERR_ARG, "%s: op %d: HMULT needs b, key and equal levels", fn, i);
+        if (fides_check_key(c, o.key, FIDES_GALOIS_RELIN, fn))
+            return fides_set_error(FIDES_ERR_KEY, "%s: op %d: the key is not this context's relinearisation key", fn, i);
         return FIDES_OK;
     case FIDES_OP_ROTATE:
         if (o.out.n_limbs != nl || !o.key)
             return fides_set_error(FIDES_ERR_ARG, "%s: op %d: ROTATE needs a key and equal levels", fn, i);
+        if (fides_check_key(c, o.key, fides_galois_elt(c, o.steps), fn))
+            return fides_set_error(FIDES_ERR_KEY, "%s: op %d: the key is not this context's key of Galois element %llu",
+                                   fn, i, (unsigned long long)fides_galois_elt(c, o.steps));
         return FIDES_OK;
     case FIDES_OP_RESCALE:
         if (nl < 2 || o.out.n_limbs != nl - 1)
@@ -173,7 +178,11 @@ inline size_t op_scratch_words(int N, int K, int alpha, int type, int nl)
 
 // Appends the launches of one stage: the operations ops[i] with ops[i].stage
 // == stage, each with its scratch at scratch[i].  Sets each op's out.scale.
-void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *const *scratch, Plan &P)
+// tensor_split: HMult's tensor product runs as its own 16-byte pass (where
+// the buffers allow) instead of fused into the first INTT pass; a fusion
+// boundary the batch autotuner chooses.
+void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *const *scratch, Plan &P,
+                bool tensor_split = true)
 {
     const size_t N = c->N;
     std::vector<Seg> intt, ntt, pinv, fin, rsfin;
@@ -197,10 +206,10 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
         u64 *dsrc = base;
         KsBuffers B;
         memset(&B, 0, sizeof(B));
-        B.d = dsrc; B.nl = nl; B.evk = o.key;
+        B.d = dsrc; B.nl = nl; B.evk = o.key->data;
         B.out0 = o.out.data; B.out1 = o.out.data + S;
         B.mode0 = 1; B.mode1 = hm ? 1 : 0;
-        if (hm && tensor_pass_ok(o.a.data, o.b.data, o.out.data, dsrc)) {
+        if (hm && tensor_split && tensor_pass_ok(o.a.data, o.b.data, o.out.data, dsrc)) {
             tens.push_back(TensorOp{o.a.data, o.b.data, o.out.data, dsrc, nl});   // d2 in dsrc, plain INTT
         } else {
             B.prep = hm ? 1 : 2;

@@ -40,12 +40,13 @@ int lt_plan(const fides_ctx *c, int n_diag, const int *diag_idx, int n1, LtPlan 
     return FIDES_OK;
 }
 
-const uint64_t *lt_key(const fides_ctx *c, int n_keys, const int64_t *key_steps, const uint64_t *const *keys,
-                       int64_t steps)
+// The key of the rotation by `steps` among the handles: the one registered
+// with Galois element 5^steps mod 2N (of this context), or null.
+const uint64_t *lt_key(const fides_ctx *c, int n_keys, const fides_key *const *keys, int64_t steps)
 {
-    const int64_t half = c->N / 2, want = ((steps % half) + half) % half;
+    const u64 want = fides_galois_elt(c, steps);
     for (int k = 0; k < n_keys; ++k)
-        if ((((key_steps[k] % half) + half) % half) == want) return keys[k];
+        if (keys[k] && keys[k]->ctx == c && keys[k]->g == want) return keys[k]->data;
     return nullptr;
 }
 
@@ -66,20 +67,20 @@ extern "C" int fides_linear_transform_work_words(fides_ctx *c, int n_limbs, int 
 
 extern "C" int fides_linear_transform(fides_ctx *c, const fides_ct *a, int n_diag, const int *diag_idx,
                                       const uint64_t *const *pts, double pt_scale, int n1, int n_keys,
-                                      const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
-                                      size_t work_words, fides_ct *out, void *stream)
+                                      const fides_key *const *keys, uint64_t *work, size_t work_words, fides_ct *out,
+                                      void *stream)
 {
-    return fides_linear_transform_ws(c, a, n_diag, diag_idx, pts, pt_scale, n1, n_keys, key_steps, keys, work,
-                                     work_words, out, stream, nullptr);
+    return fides_linear_transform_ws(c, a, n_diag, diag_idx, pts, pt_scale, n1, n_keys, keys, work, work_words, out,
+                                     stream, nullptr);
 }
 
 int fides_linear_transform_ws(fides_ctx *c, const fides_ct *a, int n_diag, const int *diag_idx,
                               const uint64_t *const *pts, double pt_scale, int n1, int n_keys,
-                              const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
-                              size_t work_words, fides_ct *out, void *stream, u64 *ws)
+                              const fides_key *const *keys, uint64_t *work, size_t work_words, fides_ct *out,
+                              void *stream, u64 *ws)
 {
     const char *fn = "fides_linear_transform";
-    if (!c || !a || !a->data || !out || !out->data || !pts || (n_keys > 0 && (!key_steps || !keys)))
+    if (!c || !a || !a->data || !out || !out->data || !pts || n_keys < 0 || (n_keys > 0 && !keys))
         return fides_set_error(FIDES_ERR_ARG, "%s: NULL argument", fn);
     const int nl = a->n_limbs;
     if (nl < 1 || nl > c->L || out->n_limbs != nl) return fides_set_error(FIDES_ERR_ARG, "%s: bad levels", fn);
@@ -94,14 +95,14 @@ int fides_linear_transform_ws(fides_ctx *c, const fides_ct *a, int n_diag, const
     // every key first, so that nothing is queued when one is missing
     std::vector<const uint64_t *> baby_keys;
     for (int b : P.baby) {
-        const uint64_t *k = lt_key(c, n_keys, key_steps, keys, b);
+        const uint64_t *k = lt_key(c, n_keys, keys, b);
         if (!k) return fides_set_error(FIDES_ERR_KEY, "%s: no rotation key for baby step %d", fn, b);
         baby_keys.push_back(k);
     }
     std::map<int, const uint64_t *> giant_keys;
     for (auto &kv : P.giant) {
         if (kv.first == 0) continue;
-        const uint64_t *k = lt_key(c, n_keys, key_steps, keys, (int64_t)n1 * kv.first);
+        const uint64_t *k = lt_key(c, n_keys, keys, (int64_t)n1 * kv.first);
         if (!k) return fides_set_error(FIDES_ERR_KEY, "%s: no rotation key for giant step %d", fn, n1 * kv.first);
         giant_keys[kv.first] = k;
     }

@@ -19,7 +19,7 @@
 #include <mutex>
 
 #include "fides_internal.cuh"
-#include "ntt.cuh"
+#include "plan.cuh"
 
 #define FIDES_NOALLOC_SCRATCH_WORDS (2 * 65536)
 #define FIDES_NOALLOC_MAX_DEVICES 64
@@ -32,8 +32,11 @@ std::mutex g_mu;
 u64 *g_addr[FIDES_NOALLOC_MAX_DEVICES];
 
 // Device address of the array on `dev`, looked up once per device with that
-// device current.  In host code the array's name is only a host-side stand-in,
-// so kernels must be given this address.
+// device current (the first call on the device does it).  In host code the
+// array's name is only a host-side stand-in, so kernels must be given this
+// address.  The address is kept for the life of the process: a device reset
+// (cudaDeviceReset) after the first call is not supported -- it frees every
+// context of this library on that device as well.
 int scratch_address(int dev, u64 **out)
 {
     if (dev < 0 || dev >= FIDES_NOALLOC_MAX_DEVICES)
@@ -47,15 +50,6 @@ int scratch_address(int dev, u64 **out)
     }
     *out = g_addr[dev];
     return FIDES_OK;
-}
-
-Seg make_seg(const u64 *src, u64 *dst, int count, int prime0, const u64 *aux, u64 *out, int src_step,
-             const TwPair *cst)
-{
-    Seg s;
-    s.src = src; s.dst = dst; s.aux = aux; s.out = out; s.side = nullptr; s.cst = cst; s.g = 0;
-    s.count = count; s.prime0 = prime0; s.src_step = src_step; s.mode = 0; s.pstride = 0;
-    return s;
 }
 
 }  // namespace
@@ -82,26 +76,16 @@ extern "C" int fides_rescale_noalloc(fides_ctx *c, const fides_ct *a, fides_ct *
     if (int rc = scratch_address(dev, &scr)) return rc;
 
     const int l = nl - 1;
-    const size_t N = c->N, Sin = (size_t)nl * N, Sout = (size_t)l * N;
     cudaStream_t st = (cudaStream_t)stream;
     OpTrace op("op_rescale_noalloc", st);
-    // coefficient form of the dropped limb q_l of both polynomials
-    LimbSet last;
-    memset(&last, 0, sizeof(last));
-    for (int t = 0; t < 2; ++t) {
-        last.seg[last.nseg++] = make_seg(a->data + t * Sin + (size_t)l * N, scr + t * N, 1, l, nullptr, nullptr, 1, nullptr);
-        last.total += 1;
-    }
+    // the segments of fides_rescale, built into inline limb sets (no heap use)
+    // with the static array in place of the context's scratch
+    LimbSet last = empty_set(), fin = empty_set();
+    SetSink sl{last}, sf{fin};
+    rs_intt_segs(c, a->data, nl, scr, sl);
     int rc = ntt_inverse(c, last, ProSrc{}, EpiCanon{}, st);
     if (rc) return rc;
-    // out_i = q_l^-1 (x_i - NTT_{q_i}([x_l]_{q_i})) for i < l
-    LimbSet fin;
-    memset(&fin, 0, sizeof(fin));
-    for (int t = 0; t < 2; ++t) {
-        fin.seg[fin.nseg++] = make_seg(scr + t * N, out->data + t * Sout, l, 0, a->data + t * Sin, out->data + t * Sout, 0,
-                                       c->d_rs_qlinv + (size_t)l * c->L);
-        fin.total += l;
-    }
+    rs_final_segs(c, a->data, nl, scr, out->data, sf);
     rc = ntt_forward(c, fin, ProSwitchMod{}, EpiSubMul{}, st);
     if (!rc) out->scale = a->scale / (double)c->primes[l];
     return rc;

@@ -17,7 +17,7 @@ int fides_rescale_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *strea
 int fides_modraise_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws);
 int fides_linear_transform_ws(fides_ctx *c, const fides_ct *a, int n_diag, const int *diag_idx,
                               const uint64_t *const *pts, double pt_scale, int n1, int n_keys,
-                              const int64_t *key_steps, const uint64_t *const *keys, uint64_t *work,
-                              size_t work_words, fides_ct *out, void *stream, u64 *ws);
+                              const fides_key *const *keys, uint64_t *work, size_t work_words, fides_ct *out,
+                              void *stream, u64 *ws);
 int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uint64_t *rlk, fides_ct *out,
                            void *stream, u64 *ws);

@@ -170,7 +170,10 @@ inline void ks_final_segs(const fides_ctx *c, const KsBuffers &B, std::vector<Se
 // limbs of scratch.  (a) INTT of the dropped limb of both polynomials;
 // (b) NTT under q_i of its SwitchModulo with the fused epilogue
 // out_i = q_l^-1 (x_i - .) (Sec. III-F5 "Rescale fusion").
-inline void rs_intt_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, std::vector<Seg> &v)
+// V: any sink with push_back(const Seg &) -- a std::vector, or SetSink,
+// which fills a LimbSet in place without touching the heap.
+template <class V>
+inline void rs_intt_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, V &v)
 {
     const size_t N = c->N;
     for (int t = 0; t < 2; ++t) v.push_back(seg_of(x + ((size_t)t * nl + nl - 1) * N, last + t * N, 1, nl - 1));
@@ -178,7 +181,8 @@ inline void rs_intt_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, st
 
 // nearest: round-to-nearest Rescale (the centred SwitchModulo, ProSwitchMod
 // with g = q_l) instead of floor.
-inline void rs_final_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, u64 *out, std::vector<Seg> &v,
+template <class V>
+inline void rs_final_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, u64 *out, V &v,
                           bool nearest = false)
 {
     const size_t N = c->N;
@@ -190,6 +194,12 @@ inline void rs_final_segs(const fides_ctx *c, const u64 *x, int nl, u64 *last, u
         v.push_back(g);
     }
 }
+
+// A sink for the segment builders that appends to a LimbSet (no heap use).
+struct SetSink {
+    LimbSet &S;
+    void push_back(const Seg &g) { add_seg(S, g); }
+};
 
 // Inline limb set of at most FIDES_MAX_SEG segments.
 inline LimbSet inline_set(const std::vector<Seg> &v)

@@ -35,9 +35,8 @@ struct fides_program {
     std::vector<double> const_scale;
     u64 *dconst = nullptr;                      // device copy of the constants, [n_const][L]
     std::vector<int> lin_start, lin_reg, lin_const;   // CMAC term lists
-    const uint64_t *relin, *conj;
-    std::vector<int64_t> rot_steps;
-    std::vector<const uint64_t *> rot_keys;
+    const uint64_t *relin, *conj;               // key buffers (null: none)
+    std::vector<const fides_key *> rot_keys;    // rotation-key handles, found by Galois element
     // analysis
     std::vector<int> level;     // limbs of each virtual register
     std::vector<int> phys;      // buffer of each virtual register (-1: the input)
@@ -227,8 +226,16 @@ extern "C" int fides_program_create(fides_ctx *c, const fides_program_desc *d, f
         d->in_limbs < 1 || d->in_limbs > c->L)
         return fides_set_error(FIDES_ERR_ARG, "fides_program_create: bad input/output register or limbs");
     if ((d->n_lt > 0 && !d->lt) || (d->n_const > 0 && (!d->consts || !d->const_scale)) ||
-        (d->n_rot_keys > 0 && (!d->rot_steps || !d->dev_rot_keys)))
+        d->n_rot_keys < 0 || (d->n_rot_keys > 0 && !d->rot_keys))
         return fides_set_error(FIDES_ERR_ARG, "fides_program_create: NULL table");
+    // keys: the relinearisation key of Galois element 0, the conjugation key
+    // of 2N - 1, rotation keys of this context (each found by its element)
+    if (d->relin_key)
+        if (int rc = fides_check_key(c, d->relin_key, FIDES_GALOIS_RELIN, "fides_program_create: relin_key")) return rc;
+    if (d->conj_key)
+        if (int rc = fides_check_key(c, d->conj_key, 2 * (u64)c->N - 1, "fides_program_create: conj_key")) return rc;
+    for (int k = 0; k < d->n_rot_keys; ++k)
+        if (int rc = fides_check_key(c, d->rot_keys[k], FIDES_GALOIS_ANY, "fides_program_create: rot_keys")) return rc;
     fides_program *p = new fides_program();
     p->ctx = c;
     p->instr.assign(d->instr, d->instr + d->n_instr);
@@ -275,10 +282,9 @@ extern "C" int fides_program_create(fides_ctx *c, const fides_program_desc *d, f
     } else {
         p->lin_start.assign(1, 0);
     }
-    p->relin = d->dev_relin_key;
-    p->conj = d->dev_conj_key;
-    p->rot_steps.assign(d->rot_steps, d->rot_steps + d->n_rot_keys);
-    p->rot_keys.assign(d->dev_rot_keys, d->dev_rot_keys + d->n_rot_keys);
+    p->relin = d->relin_key ? d->relin_key->data : nullptr;
+    p->conj = d->conj_key ? d->conj_key->data : nullptr;
+    p->rot_keys.assign(d->rot_keys, d->rot_keys + d->n_rot_keys);
     hoist_rescales(p);
     if (int rc = analyse(p)) {
         delete p;
@@ -386,7 +392,7 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
         case FIDES_I_LT: {
             const fides_program::Lt &t = p->lt[I.arg];
             rc = fides_linear_transform_ws(c, &a, (int)t.idx.size(), t.idx.data(), t.pts.data(), t.pt_scale, t.n1,
-                                           (int)p->rot_steps.size(), p->rot_steps.data(), p->rot_keys.data(),
+                                           (int)p->rot_keys.size(), p->rot_keys.data(),
                                            lt_work, p->lt_words, &d, stream, ws);
             break;
         }

@@ -107,7 +107,7 @@ enum ReqState { R_PENDING, R_RUNNING, R_DONE, R_ABANDONED };
 struct Req {
     uint64_t id;
     fides_request r;
-    const u64 *key;
+    const fides_key *key;
     int nl, out_limbs;
     size_t out_bytes, scr_bytes;
     size_t out_off, scr_off;
@@ -139,6 +139,7 @@ public:
         // level) times the group size, plus alignment slack per launch.
         size_t per_op = 0;
         std::vector<u64> fake(1);
+        const fides_key fake_key = {c_, fake.data(), 0};
         for (int type = FIDES_OP_HMULT; type <= FIDES_OP_RESCALE; ++type) {
             for (int nl = type == FIDES_OP_RESCALE ? 2 : 1; nl <= c_->L; ++nl) {
                 fides_op o;
@@ -146,7 +147,7 @@ public:
                 o.type = type;
                 o.a.data = o.b.data = o.out.data = fake.data();
                 o.a.n_limbs = nl;
-                o.key = fake.data();
+                o.key = &fake_key;
                 u64 *s = fake.data();
                 Plan P;
                 plan_stage(c_, &o, 1, 0, &s, P);
@@ -304,8 +305,8 @@ struct fides_server {
     std::deque<Req *> pending;
     std::deque<fides_completion> done;
     std::unordered_map<uint64_t, Req *> live;
-    std::unordered_map<int64_t, const u64 *> rot_keys;   // normalised steps -> key
-    const u64 *relin = nullptr;
+    std::unordered_map<int64_t, const fides_key *> rot_keys;   // normalised steps -> key
+    const fides_key *relin = nullptr;
     Arena arena;
     std::vector<Lane> lanes;
     bool stop = false, paused = false;
@@ -576,17 +577,22 @@ extern "C" void fides_server_destroy(fides_server *s)
     delete s;
 }
 
-extern "C" int fides_server_set_relin_key(fides_server *s, const uint64_t *key)
+extern "C" int fides_server_set_relin_key(fides_server *s, const fides_key *key)
 {
     if (!s || !key) return fides_set_error(FIDES_ERR_ARG, "fides_server_set_relin_key: NULL argument");
+    if (s->ctx)
+        if (int rc = fides_check_key(s->ctx, key, FIDES_GALOIS_RELIN, "fides_server_set_relin_key")) return rc;
     std::lock_guard<std::mutex> lk(s->mu);
     s->relin = key;
     return FIDES_OK;
 }
 
-extern "C" int fides_server_add_rotation_key(fides_server *s, int64_t steps, const uint64_t *key)
+extern "C" int fides_server_add_rotation_key(fides_server *s, int64_t steps, const fides_key *key)
 {
     if (!s || !key) return fides_set_error(FIDES_ERR_ARG, "fides_server_add_rotation_key: NULL argument");
+    if (s->ctx)
+        if (int rc = fides_check_key(s->ctx, key, fides_galois_elt(s->ctx, steps), "fides_server_add_rotation_key"))
+            return rc;
     std::lock_guard<std::mutex> lk(s->mu);
     s->rot_keys[s->norm_steps(steps)] = key;
     return FIDES_OK;
@@ -603,7 +609,7 @@ extern "C" int fides_server_submit(fides_server *s, const fides_request *r, uint
     };
     if (s->stop) return reject(FIDES_ERR_ARG, "server is stopping");
     if (!r->a.data) return reject(FIDES_ERR_ARG, "a.data is NULL");
-    const u64 *key = nullptr;
+    const fides_key *key = nullptr;
     int out_limbs = nl;
     switch (r->type) {
     case FIDES_OP_HMULT:

@@ -38,7 +38,8 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_linear_transform_work_words", "fides_modraise", "fides_mul_i", "fides_program_create",
            "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
            "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale",
-           "fides_rescale_round"]
+           "fides_rescale_round", "fides_key_register", "fides_key_destroy", "fides_key_galois",
+           "fides_batch_configure", "fides_batch_autotune", "fides_batch_tuning"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
@@ -105,9 +106,9 @@ class fides_program_desc(ctypes.Structure):
                 ("in_reg", ctypes.c_int), ("out_reg", ctypes.c_int), ("in_limbs", ctypes.c_int),
                 ("out_scale", ctypes.c_double), ("n_lt", ctypes.c_int), ("lt", ctypes.POINTER(fides_lt)),
                 ("n_const", ctypes.c_int), ("consts", ctypes.POINTER(ctypes.c_void_p)),
-                ("const_scale", ctypes.POINTER(ctypes.c_double)), ("dev_relin_key", ctypes.c_void_p),
-                ("dev_conj_key", ctypes.c_void_p), ("n_rot_keys", ctypes.c_int),
-                ("rot_steps", ctypes.POINTER(ctypes.c_int64)), ("dev_rot_keys", ctypes.POINTER(ctypes.c_void_p)),
+                ("const_scale", ctypes.POINTER(ctypes.c_double)), ("relin_key", ctypes.c_void_p),
+                ("conj_key", ctypes.c_void_p), ("n_rot_keys", ctypes.c_int),
+                ("rot_keys", ctypes.POINTER(ctypes.c_void_p)),
                 ("n_lin", ctypes.c_int), ("lin_start", ctypes.POINTER(ctypes.c_int)),
                 ("lin_reg", ctypes.POINTER(ctypes.c_int)), ("lin_const", ctypes.POINTER(ctypes.c_int))]
 
@@ -128,7 +129,7 @@ def lib():
         L.fides_last_error.restype = ctypes.c_char_p
         L.fides_version.restype = ctypes.c_char_p
         L.fides_find_primes.argtypes = [_i, _i, _i, _u64p, _i, _u64p]
-        L.fides_ctx_create.argtypes = [_i, _i, _i, _i, _u64p, ctypes.POINTER(_vp)]
+        L.fides_ctx_create.argtypes = [_i, _i, _i, _u64p, _i, ctypes.POINTER(_vp)]
         L.fides_ctx_destroy.argtypes = [_vp]
         L.fides_ctx_destroy.restype = None
         L.fides_ctx_beta.argtypes = [_vp, _i]
@@ -141,6 +142,11 @@ def lib():
         L.fides_modup.argtypes = [_vp, _vp, _i, _vp, _vp]
         L.fides_moddown.argtypes = [_vp, _vp, _i, _vp, _vp]
         L.fides_keyswitch.argtypes = [_vp, _vp, _i, _vp, _vp, _vp, _vp]
+        L.fides_key_register.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(_vp)]
+        L.fides_key_destroy.argtypes = [_vp]
+        L.fides_key_destroy.restype = None
+        L.fides_key_galois.argtypes = [_vp]
+        L.fides_key_galois.restype = ctypes.c_uint64
         ctp = ctypes.POINTER(fides_ct)
         L.fides_hmult.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
         L.fides_hmult_rescale.argtypes = [_vp, ctp, ctp, _vp, ctp, _vp]
@@ -164,6 +170,9 @@ def lib():
                                        ctypes.POINTER(ctypes.c_size_t)]
         L.fides_batch_destroy.argtypes = [_vp]
         L.fides_batch_destroy.restype = None
+        L.fides_batch_configure.argtypes = [_vp, _i, _i]
+        L.fides_batch_autotune.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
+        L.fides_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]
         L.fides_measure_modmul_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.fides_server_create.argtypes = [_vp, ctypes.POINTER(fides_server_config), ctypes.POINTER(_vp)]
         L.fides_server_destroy.argtypes = [_vp]
@@ -190,8 +199,7 @@ def lib():
         L.fides_linear_transform_work_words.argtypes = [_vp, _i, _i, ctypes.POINTER(_i), _i,
                                                         ctypes.POINTER(ctypes.c_size_t)]
         L.fides_linear_transform.argtypes = [_vp, ctp, _i, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.c_double,
-                                             _i, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp), _vp,
-                                             ctypes.c_size_t, ctp, _vp]
+                                             _i, _i, ctypes.POINTER(_vp), _vp, ctypes.c_size_t, ctp, _vp]
         L.fides_modraise.argtypes = [_vp, ctp, ctp, _vp]
         L.fides_mul_i.argtypes = [_vp, ctp, _i, ctp, _vp]
         L.fides_program_create.argtypes = [_vp, ctypes.POINTER(fides_program_desc), ctypes.POINTER(_vp)]
@@ -292,7 +300,7 @@ class Context:
         self.alpha = -(-self.L // dnum)
         arr = np.ascontiguousarray(self.q + self.p, dtype=np.uint64)
         h = ctypes.c_void_p()
-        _check(lib().fides_ctx_create(logN, self.L, self.K, dnum, arr.ctypes.data_as(_u64p), ctypes.byref(h)))
+        _check(lib().fides_ctx_create(logN, self.L, dnum, arr.ctypes.data_as(_u64p), self.K, ctypes.byref(h)))
         self._h = h
 
     def close(self):
@@ -386,13 +394,28 @@ class Context:
         _check(lib().fides_moddown(self._h, _ptr(x, (n_limbs + self.K) * self.N, "x"), n_limbs,
                                    _ptr(out, n_limbs * self.N, "out"), _stream(stream)))
 
-    def keyswitch(self, d, n_limbs: int, evk, out0, out1, stream=None):
+    def keyswitch(self, d, n_limbs: int, evk: "Key", out0, out1, stream=None):
         w = n_limbs * self.N
-        _check(lib().fides_keyswitch(self._h, _ptr(d, w, "d"), n_limbs, _ptr(evk, self.key_words(), "evk"),
+        _check(lib().fides_keyswitch(self._h, _ptr(d, w, "d"), n_limbs, _key(evk),
                                      _ptr(out0, w, "out0"), _ptr(out1, w, "out1"), _stream(stream)))
 
     def key_words(self) -> int:
         return self.dnum * 2 * (self.L + self.K) * self.N
+
+    # -- switching keys ------------------------------------------------------
+    def register_key(self, t, galois: int) -> "Key":
+        """Binds the key buffer t ([dnum][2][L+K][N]) to Galois element `galois`
+        (0: relinearisation); fides_key_register."""
+        return Key(self, t, galois)
+
+    def relin_key(self, t) -> "Key":
+        return Key(self, t, 0)
+
+    def rotation_key(self, t, steps: int) -> "Key":
+        return Key(self, t, self.galois_elt(steps))
+
+    def conjugation_key(self, t) -> "Key":
+        return Key(self, t, 2 * self.N - 1)
 
     # -- ciphertext operations ---------------------------------------------
     def _ct(self, t, n_limbs: int, scale: float, name: str):
@@ -401,8 +424,8 @@ class Context:
     def hmult(self, a, b, n_limbs: int, rlk, out, scale_a: float = 1.0, scale_b: float = 1.0, stream=None) -> float:
         ca, cb = self._ct(a, n_limbs, scale_a, "a"), self._ct(b, n_limbs, scale_b, "b")
         co = self._ct(out, n_limbs, 0.0, "out")
-        _check(lib().fides_hmult(self._h, ctypes.byref(ca), ctypes.byref(cb), _ptr(rlk, self.key_words(), "rlk"),
-                                 ctypes.byref(co), _stream(stream)))
+        _check(lib().fides_hmult(self._h, ctypes.byref(ca), ctypes.byref(cb), _key(rlk), ctypes.byref(co),
+                                 _stream(stream)))
         return co.scale
 
     def hmult_rescale(self, a, b, n_limbs: int, rlk, out, scale_a: float = 1.0, scale_b: float = 1.0,
@@ -410,14 +433,13 @@ class Context:
         """Rescale(HMult(a, b)) in one key switch; out has n_limbs - 1 limbs."""
         ca, cb = self._ct(a, n_limbs, scale_a, "a"), self._ct(b, n_limbs, scale_b, "b")
         co = self._ct(out, n_limbs - 1, 0.0, "out")
-        _check(lib().fides_hmult_rescale(self._h, ctypes.byref(ca), ctypes.byref(cb),
-                                         _ptr(rlk, self.key_words(), "rlk"), ctypes.byref(co), _stream(stream)))
+        _check(lib().fides_hmult_rescale(self._h, ctypes.byref(ca), ctypes.byref(cb), _key(rlk), ctypes.byref(co),
+                                         _stream(stream)))
         return co.scale
 
     def rotate(self, a, n_limbs: int, steps: int, rk, out, scale: float = 1.0, stream=None) -> float:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
-        _check(lib().fides_rotate(self._h, ctypes.byref(ca), steps, _ptr(rk, self.key_words(), "rk"),
-                                  ctypes.byref(co), _stream(stream)))
+        _check(lib().fides_rotate(self._h, ctypes.byref(ca), steps, _key(rk), ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def rescale(self, a, n_limbs: int, out, scale: float = 1.0, stream=None, nearest: bool = False) -> float:
@@ -429,14 +451,12 @@ class Context:
 
     def hsquare(self, a, n_limbs: int, rlk, out, scale: float = 1.0, stream=None) -> float:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
-        _check(lib().fides_hsquare(self._h, ctypes.byref(ca), _ptr(rlk, self.key_words(), "rlk"), ctypes.byref(co),
-                                   _stream(stream)))
+        _check(lib().fides_hsquare(self._h, ctypes.byref(ca), _key(rlk), ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def conjugate(self, a, n_limbs: int, ck, out, scale: float = 1.0, stream=None) -> float:
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
-        _check(lib().fides_conjugate(self._h, ctypes.byref(ca), _ptr(ck, self.key_words(), "ck"), ctypes.byref(co),
-                                     _stream(stream)))
+        _check(lib().fides_conjugate(self._h, ctypes.byref(ca), _key(ck), ctypes.byref(co), _stream(stream)))
         return co.scale
 
     def rotate_hoisted(self, a, n_limbs: int, steps, rks, outs, scale: float = 1.0, stream=None):
@@ -446,15 +466,16 @@ class Context:
             raise ValueError("steps, rks and outs must have the same length")
         ca = self._ct(a, n_limbs, scale, "a")
         st = (ctypes.c_int64 * n)(*steps)
-        keys = (_vp * n)(*[_ptr(k, self.key_words(), "rk").value for k in rks])
+        keys = (_vp * n)(*[_key(k) for k in rks])
         cts = (fides_ct * n)(*[self._ct(o, n_limbs, 0.0, "out") for o in outs])
         _check(lib().fides_rotate_hoisted(self._h, ctypes.byref(ca), n, st, keys, cts, _stream(stream)))
 
-    def linear_transform(self, a, n_limbs: int, diag_idx, pts, n1: int, keys: dict, out, scale: float = 1.0,
+    def linear_transform(self, a, n_limbs: int, diag_idx, pts, n1: int, keys, out, scale: float = 1.0,
                          pt_scale: float = 1.0, work=None, stream=None) -> float:
         """BSGS diagonal-method transform (fides_linear_transform); pts[k] is
-        the device plaintext of diagonal diag_idx[k], pre-rotated; keys maps
-        step counts to device rotation keys."""
+        the device plaintext of diagonal diag_idx[k], pre-rotated; keys are
+        rotation Keys (a list, or a dict whose values are used), found by
+        their Galois elements."""
         n = len(diag_idx)
         di = (_i * n)(*diag_idx)
         words = ctypes.c_size_t(0)
@@ -463,11 +484,10 @@ class Context:
             import torch
             work = torch.empty(max(1, words.value), dtype=torch.int64, device="cuda")
         pp = (_vp * n)(*[_ptr(p, n_limbs * self.N, "pt").value for p in pts])
-        ks = list(keys)
-        kst = (ctypes.c_int64 * max(1, len(ks)))(*ks)
-        kp = (_vp * max(1, len(ks)))(*[_ptr(keys[k], self.key_words(), "key").value for k in ks])
+        ks = list(keys.values()) if isinstance(keys, dict) else list(keys)
+        kp = (_vp * max(1, len(ks)))(*[_key(k) for k in ks])
         ca, co = self._ct(a, n_limbs, scale, "a"), self._ct(out, n_limbs, 0.0, "out")
-        _check(lib().fides_linear_transform(self._h, ctypes.byref(ca), n, di, pp, pt_scale, n1, len(ks), kst, kp,
+        _check(lib().fides_linear_transform(self._h, ctypes.byref(ca), n, di, pp, pt_scale, n1, len(ks), kp,
                                             _ptr(work, words.value, "work"), work.numel(), ctypes.byref(co),
                                             _stream(stream)))
         return co.scale
@@ -539,6 +559,38 @@ class Context:
         return co.scale
 
 
+class Key:
+    """A switching key registered with the library (``fides_key``): the device
+    buffer ``tensor`` ([dnum][2][L+K][N], kept referenced here) bound to the
+    Galois element it switches from (0: relinearisation).  Registration
+    synchronises the device; the buffer must not change while the Key lives."""
+
+    def __init__(self, ctx: "Context", t, galois: int):
+        self.ctx, self.tensor, self.galois = ctx, t, int(galois)
+        h = ctypes.c_void_p()
+        _check(lib().fides_key_register(ctx._h, _ptr(t, ctx.key_words(), "key"), self.galois, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fides_key_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def _key(k) -> int:
+    """Handle of a Key (the entry points take registered keys, not buffers)."""
+    if not isinstance(k, Key) or k._h is None:
+        raise TypeError("expected a registered Key (Context.relin_key / rotation_key / conjugation_key / "
+                        "register_key), got %s" % type(k).__name__)
+    return k._h.value
+
+
 class Op:
     """One operation of a batch: ``kind`` is OP_HMULT, OP_ROTATE or OP_RESCALE;
     a, b, out are CUDA tensors of ciphertexts [2][n_limbs][N]."""
@@ -564,7 +616,7 @@ class Batch:
             if o.b is not None:
                 arr[i].b = fides_ct(_ptr(o.b, 2 * o.n_limbs * N, "b").value, o.n_limbs, o.scale_b)
             arr[i].out = fides_ct(_ptr(o.out, 2 * out_limbs * N, "out").value, out_limbs, 0.0)
-            arr[i].key = _ptr(o.key, ctx.key_words(), "key").value if o.key is not None else None
+            arr[i].key = _key(o.key) if o.key is not None else None
             arr[i].steps = o.steps
         h = ctypes.c_void_p()
         _check(lib().fides_batch_create(ctx._h, arr, len(self.ops), ctypes.byref(h)))
@@ -582,7 +634,22 @@ class Batch:
     def info(self) -> dict:
         n, sb, tb = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
         _check(lib().fides_batch_info(self._h, ctypes.byref(n), ctypes.byref(sb), ctypes.byref(tb)))
-        return {"launches": n.value, "scratch_bytes": sb.value, "table_bytes": tb.value}
+        g, t, ng = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().fides_batch_tuning(self._h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(ng)))
+        return {"launches": n.value, "scratch_bytes": sb.value, "table_bytes": tb.value, "group_limbs": g.value,
+                "tensor_split": t.value, "groups": ng.value}
+
+    def configure(self, group_limbs: int, tensor_split: int = 1):
+        """Launch groups of at most group_limbs limbs (0: one per stage) and the
+        tensor-product placement (fides_batch_configure)."""
+        _check(lib().fides_batch_configure(self._h, group_limbs, tensor_split))
+
+    def autotune(self, stream=None) -> float:
+        """Times the candidate groupings and tensor placements on this batch and
+        keeps the fastest (fides_batch_autotune); returns its ms per run."""
+        ms = ctypes.c_double(0.0)
+        _check(lib().fides_batch_autotune(self._h, _stream(stream), ctypes.byref(ms)))
+        return ms.value
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -646,7 +713,7 @@ class Server:
         _check(lib().fides_server_create(ctx._h if ctx is not None else None, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._keep = {}     # request id -> input tensors, until completion
-        self._keys = []     # registered key tensors
+        self._keys = []     # the Keys the server uses
         self._poll_buf = {}
 
     @staticmethod
@@ -655,13 +722,21 @@ class Server:
             return t
         return _ptr(t, words, name).value
 
+    @staticmethod
+    def _key_arg(key):
+        if isinstance(key, int):  # a token (simulation: handles are never dereferenced)
+            return key
+        return _key(key)
+
     def set_relin_key(self, key):
+        """key: the relinearisation Key (an int token in simulation)."""
         self._keys.append(key)
-        _check(lib().fides_server_set_relin_key(self._h, self._addr(key, None, "key")))
+        _check(lib().fides_server_set_relin_key(self._h, self._key_arg(key)))
 
     def add_rotation_key(self, steps: int, key):
+        """key: the rotation Key of `steps` (an int token in simulation)."""
         self._keys.append(key)
-        _check(lib().fides_server_add_rotation_key(self._h, steps, self._addr(key, None, "key")))
+        _check(lib().fides_server_add_rotation_key(self._h, steps, self._key_arg(key)))
 
     def submit(self, kind: int, a, n_limbs: int, b=None, steps: int = 0, tag: int = 0, scale_a: float = 1.0,
                scale_b: float = 1.0) -> int:

@@ -51,7 +51,7 @@ def test_find_primes_agrees_with_oracle(L, logN, bits, count):
 def _create(L, logN, q, p, dnum):
     arr = np.ascontiguousarray(q + p, dtype=np.uint64)
     h = ctypes.c_void_p()
-    rc = L.fides_ctx_create(logN, len(q), len(p), dnum, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+    rc = L.fides_ctx_create(logN, len(q), dnum, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(p),
                             ctypes.byref(h))
     return rc, h
 
@@ -78,6 +78,19 @@ def test_find_primes_argument_errors(L):
         fides.find_primes(16, 62, 1)
     with pytest.raises(fides.FidesError):
         fides.find_primes(16, 10, 1)
+
+
+def test_key_handle_argument_errors_on_the_host(L):
+    """Key registration refuses missing arguments before touching a device;
+    the handle helpers accept NULL."""
+    h = ctypes.c_void_p(1)
+    assert L.fides_key_register(None, ctypes.c_void_p(4096), 0, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert L.fides_key_register(None, None, 0, None) == -1
+    assert L.fides_key_galois(None) == 0
+    L.fides_key_destroy(None)
+    assert L.fides_keyswitch(None, None, 1, None, None, None, None) == -1
+    assert L.fides_rotate(None, None, 1, None, None, None) == -1
 
 
 def test_version(L):

@@ -33,27 +33,41 @@ def zeros(o, nl):
     return torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
 
 
+class RotKeys:
+    """Rotation-key handles over one key buffer, one per rotation (parity does
+    not depend on the key's values, only on its Galois element)."""
+
+    def __init__(self, g, t):
+        self.g, self.t, self.keys = g, t, {}
+
+    def __call__(self, steps):
+        e = self.g.galois_elt(steps)
+        if e not in self.keys:
+            self.keys[e] = self.g.rotation_key(self.t, steps)
+        return self.keys[e]
+
+
 def build_case(P, levels, seed):
     """Stage 0: HMult of (a_i, b_i) at each level, HRotate of a_i, Rescale of
     a_i; stage 1: HRotate and Rescale of every stage-0 product."""
     g, o = make_pair(P)
     st = si.Stream(seed, 1)
     rlk, rk = rand_key(st, o), rand_key(st, o)
-    drlk, drk = to_device(rlk), to_device(rk)
+    drlk, drk = g.relin_key(to_device(rlk)), RotKeys(g, to_device(rk))
     host, ops = [], []
     for i, nl in enumerate(levels):
         a, b = rand_ct(st, o, nl), rand_ct(st, o, nl)
         da, db = to_device(a), to_device(b)
         steps = [1, -2, 7, 1 << (P.logN - 2)][i % 4]
         m = Op(OP_HMULT, da, nl, zeros(o, nl), b=db, key=drlk, stage=0, scale_a=2.0**40, scale_b=2.0**40)
-        r = Op(OP_ROTATE, da, nl, zeros(o, nl), key=drk, steps=steps, stage=0, scale_a=2.0**40)
+        r = Op(OP_ROTATE, da, nl, zeros(o, nl), key=drk(steps), steps=steps, stage=0, scale_a=2.0**40)
         ops += [m, r]
         entry = {"nl": nl, "a": a, "b": b, "steps": steps, "m": m, "r": r}
         if nl >= 2:
             entry["s"] = Op(OP_RESCALE, da, nl, zeros(o, nl - 1), stage=0, scale_a=2.0**40)
             entry["ms"] = Op(OP_RESCALE, m.out, nl, zeros(o, nl - 1), stage=1, scale_a=2.0**80)
             ops += [entry["s"], entry["ms"]]
-        entry["mr"] = Op(OP_ROTATE, m.out, nl, zeros(o, nl), key=drk, steps=3, stage=1, scale_a=2.0**80)
+        entry["mr"] = Op(OP_ROTATE, m.out, nl, zeros(o, nl), key=drk(3), steps=3, stage=1, scale_a=2.0**80)
         ops.append(entry["mr"])
         host.append(entry)
     return g, o, rlk, rk, drlk, drk, host, ops
@@ -67,8 +81,8 @@ def single_op_reference(g, host, drlk, drk):
         da, db = to_device(e["a"]), to_device(e["b"])
         m, r, mr = zeros(g, nl), zeros(g, nl), zeros(g, nl)
         g.hmult(da, db, nl, drlk, m)
-        g.rotate(da, nl, e["steps"], drk, r)
-        g.rotate(m, nl, 3, drk, mr)
+        g.rotate(da, nl, e["steps"], drk(e["steps"]), r)
+        g.rotate(m, nl, 3, drk(3), mr)
         d = {"m": m, "r": r, "mr": mr}
         if nl >= 2:
             s, ms = zeros(g, nl - 1), zeros(g, nl - 1)
@@ -102,6 +116,68 @@ def test_batch_matches_single_op_and_oracle(P, levels):
         assert e["m"].out_scale == 2.0**80 and e["r"].out_scale == 2.0**40
         if nl >= 2:
             assert e["ms"].out_scale == 2.0**80 / o.q[nl - 1]
+    batch.close()
+    g.close()
+
+
+@pytest.mark.parametrize("group_limbs,tensor_split", [(1, 1), (8, 0), (20, 1), (0, 0)])
+def test_batch_launch_groups_and_tensor_placement(group_limbs, tensor_split):
+    """The same batch planned as launch groups of at most group_limbs limbs
+    (one op per group at 1; several groups per stage sharing one scratch pool)
+    and with the tensor product fused or as its own pass: residues equal the
+    single-op path's and the oracle's; smaller groups need less scratch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.MID
+    g, o, rlk, rk, drlk, drk, host, ops = build_case(P, [12, 5, 1, 9, 4, 12], 503)
+    batch = Batch(g, ops)
+    whole = batch.info()
+    batch.configure(group_limbs, tensor_split)
+    info = batch.info()
+    assert info["group_limbs"] == group_limbs and info["tensor_split"] == tensor_split
+    if group_limbs:
+        assert info["groups"] > whole["groups"] and info["scratch_bytes"] < whole["scratch_bytes"]
+    for op in ops:
+        op.out.fill_(-1)
+    batch.run()
+    torch.cuda.synchronize()
+    ref = single_op_reference(g, host, drlk, drk)
+    torch.cuda.synchronize()
+    for e, r in zip(host, ref):
+        for k in ("m", "r", "mr", "s", "ms"):
+            if k in r:
+                assert np.array_equal(to_host(e[k].out), to_host(r[k])), (e["nl"], k)
+    e = host[0]
+    assert np.array_equal(to_host(e["m"].out).reshape(2, e["nl"], o.N), o.hmult(e["a"], e["b"], rlk))
+    batch.close()
+    g.close()
+
+
+def test_batch_autotune_keeps_results():
+    """The autotuner picks a grouping and tensor placement by timing them on
+    the batch; the chosen plan still computes the oracle's residues, also
+    replayed from a captured graph."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.FULL
+    g, o, rlk, rk, drlk, drk, host, ops = build_case(P, [30, 7, 4, 16], 504)
+    batch = Batch(g, ops)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ms = batch.autotune(s)
+        for op in ops:
+            op.out.zero_()
+        batch.capture(s)
+        batch.run(s)
+    s.synchronize()
+    info = batch.info()
+    assert ms > 0 and info["groups"] >= 2
+    e = host[1]
+    nl = e["nl"]
+    prod = o.hmult(e["a"], e["b"], rlk)
+    assert np.array_equal(to_host(e["m"].out).reshape(2, nl, o.N), prod)
+    assert np.array_equal(to_host(e["mr"].out).reshape(2, nl, o.N), o.rotate(prod, 3, rk))
+    assert np.array_equal(to_host(e["r"].out).reshape(2, nl, o.N), o.rotate(e["a"], e["steps"], rk))
     batch.close()
     g.close()
 

@@ -81,7 +81,7 @@ def test_one_conversion_on_the_integer_kernel(shape):
     assert not g.tensor_bconv
     st = si.Stream(1500 + nq, 1)
     rlk = np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
-    drlk = to_device(rlk)
+    drlk = g.relin_key(to_device(rlk))
     for nl in (nq, nq - 5):
         d = si.uniform_poly(st, o.q[:nl], o.N)
         x = si.uniform_poly(st, o.q[:nl] + o.p, o.N)
@@ -105,7 +105,7 @@ def test_full_size_ragged_levels_and_status():
     g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
     st = si.Stream(1510, 2)
     rlk = np.stack([np.stack([si.uniform_poly(st, o.primes, o.N) for _ in range(2)]) for _ in range(o.dnum)])
-    drlk = to_device(rlk)
+    drlk = g.relin_key(to_device(rlk))
     for nl in (21, 28):
         a = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
         b = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])

@@ -32,10 +32,11 @@ def setup(logN, seed):
     return Context(logN, q, p, 3), o, cl, q
 
 
-def dev_keys(cl, steps):
+def dev_keys(g, cl, steps):
     rlk, ck = cl.relin_key(), cl.conjugation_key()
     rks = {s: cl.rotation_key(s) for s in steps}
-    return (rlk, ck, rks), (to_device(rlk), to_device(ck), {s: to_device(k) for s, k in rks.items()})
+    return (rlk, ck, rks), (g.relin_key(to_device(rlk)), g.conjugation_key(to_device(ck)),
+                            [g.rotation_key(to_device(k), s) for s, k in rks.items()])
 
 
 def run_device(g, prog, dkeys, ct, out_limbs):
@@ -54,7 +55,7 @@ def test_oracle_program_on_the_device_is_bit_exact():
         pytest.skip("no CUDA device")
     g, o, cl, q = setup(12, si.workload_seed(4))
     prog = obt.plan(cl, q, 2.0 ** 50)
-    hkeys, dkeys = dev_keys(cl, prog.rot_steps)
+    hkeys, dkeys = dev_keys(g, cl, prog.rot_steps)
     z = cl.random_slots()
     ct = cl.encrypt(z, 1, 2.0 ** 50)
     ref = obt.run(o, prog, ct, *hkeys)
@@ -69,7 +70,7 @@ def test_planned_program_matches_oracle_and_decrypts_logN12():
         pytest.skip("no CUDA device")
     g, o, cl, q = setup(12, si.workload_seed(4) + 2)
     prog = bt.plan(g.N, q, 2.0 ** 50)
-    hkeys, dkeys = dev_keys(cl, prog.rot_steps)
+    hkeys, dkeys = dev_keys(g, cl, prog.rot_steps)
     z = cl.random_slots()
     ct = cl.encrypt(z, 1, 2.0 ** 50)
     got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)
@@ -91,7 +92,7 @@ def test_bootstrap_decrypts_at_full_size(logN):
         pytest.skip("no CUDA device")
     g, o, cl, q = setup(logN, si.workload_seed(4) + 3)
     prog = bt.plan(g.N, q, 2.0 ** 50)
-    hkeys, dkeys = dev_keys(cl, prog.rot_steps)
+    hkeys, dkeys = dev_keys(g, cl, prog.rot_steps)
     z = cl.random_slots()
     ct = cl.encrypt(z, 1, 2.0 ** 50)
     got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)

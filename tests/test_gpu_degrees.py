@@ -56,7 +56,7 @@ def test_key_switching_ops(pair):
     logN, g, o = pair
     st = si.Stream(1300 + logN)
     rlk, rk = rand_key(st, o), rand_key(st, o)
-    drlk, drk = to_device(rlk), to_device(rk)
+    drlk, drk = g.relin_key(to_device(rlk)), g.rotation_key(to_device(rk), 3)
     for nl in (NQ, 3):
         a = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])
         b = np.stack([si.uniform_poly(st, o.q[:nl], o.N) for _ in range(2)])

@@ -45,7 +45,8 @@ def test_linear_transform_matches_oracle(P, nl, idx, n1):
     ref = o.linear_transform(a, idx, pts, n1, keys)
     da = to_device(a)
     out = torch.empty_like(da)
-    sc = g.linear_transform(da, nl, idx, [to_device(p) for p in pts], n1, {k: to_device(v) for k, v in keys.items()},
+    sc = g.linear_transform(da, nl, idx, [to_device(p) for p in pts], n1,
+                            [g.rotation_key(to_device(v), k) for k, v in keys.items()],
                             out, scale=2.0 ** 40, pt_scale=2.0 ** 30)
     torch.cuda.synchronize()
     assert sc == 2.0 ** 70
@@ -61,13 +62,16 @@ def test_linear_transform_rejects_before_queueing():
     st = si.Stream(902)
     da = to_device(np.stack([si.uniform_poly(st, o.q, o.N) for _ in range(2)]))
     pt = to_device(si.uniform_poly(st, o.q, o.N))
-    key = to_device(rand_key(st, o))
+    buf = to_device(rand_key(st, o))
     out = torch.empty_like(da)
     with pytest.raises(FidesError) as e:
-        g.linear_transform(da, nl, [0, 9], [pt, pt], 8, {1: key}, out)     # giant step 8 has no key
+        g.linear_transform(da, nl, [0, 9], [pt, pt], 8, [g.rotation_key(buf, 1)], out)   # giant step 8 has no key
+    assert e.value.code == -7
+    with pytest.raises(FidesError) as e:                                 # a key of step 8 registered as step 9
+        g.linear_transform(da, nl, [0, 8], [pt, pt], 8, [g.register_key(buf, g.galois_elt(9))], out)
     assert e.value.code == -7
     with pytest.raises(FidesError):
-        g.linear_transform(da, nl, [3, 3], [pt, pt], 8, {3: key}, out)     # repeated diagonal
+        g.linear_transform(da, nl, [3, 3], [pt, pt], 8, [g.rotation_key(buf, 3)], out)   # repeated diagonal
     with pytest.raises(FidesError):
-        g.linear_transform(da, nl, [o.N // 2], [pt], 8, {}, out)         # out of range
+        g.linear_transform(da, nl, [o.N // 2], [pt], 8, [], out)         # out of range
     g.close()

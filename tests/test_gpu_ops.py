@@ -120,8 +120,8 @@ def test_hsquare_and_conjugate_match_oracle(pairs, P, nl):
     rlk, ck = rand_key(st, o), rand_key(st, o)
     da = to_device(a)
     sq, cj = torch.empty_like(da), torch.empty_like(da)
-    g.hsquare(da, nl, to_device(rlk), sq)
-    g.conjugate(da, nl, to_device(ck), cj)
+    g.hsquare(da, nl, g.relin_key(to_device(rlk)), sq)
+    g.conjugate(da, nl, g.conjugation_key(to_device(ck)), cj)
     torch.cuda.synchronize()
     assert np.array_equal(to_host(sq).reshape(a.shape), o.hsquare(a, rlk))
     assert np.array_equal(to_host(cj).reshape(a.shape), o.conjugate(a, ck))
@@ -139,7 +139,7 @@ def test_hoisted_rotations_match_oracle(pairs, P, nl, steps):
     keys = [rand_key(st, o) for _ in steps]
     da = to_device(a)
     outs = [torch.empty_like(da) for _ in steps]
-    g.rotate_hoisted(da, nl, steps, [to_device(k) for k in keys], outs)
+    g.rotate_hoisted(da, nl, steps, [g.rotation_key(to_device(k), s) for k, s in zip(keys, steps)], outs)
     torch.cuda.synchronize()
     ref = o.rotate_hoisted(a, steps, keys)
     for i in range(len(steps)):

@@ -65,7 +65,8 @@ def test_every_instruction_matches_the_oracle():
     rks = {s: rand_key(st, o) for s in (1, 4)}       # baby step 1, giant step n1 * 2 = 4
     a = np.stack([si.uniform_poly(st, o.q, o.N) for _ in range(2)])
     ref = obt.run(o, prog, a, rlk, ck, rks)
-    dp = bt.DeviceProgram(g, prog, to_device(rlk), to_device(ck), {s: to_device(k) for s, k in rks.items()},
+    dp = bt.DeviceProgram(g, prog, g.relin_key(to_device(rlk)), g.conjugation_key(to_device(ck)),
+                          [g.rotation_key(to_device(k), s) for s, k in rks.items()],
                           in_limbs=nl)
     assert dp.out_limbs == ref.shape[1] == 7
     assert dp.buffers < prog.n_regs                  # registers share buffers
@@ -116,7 +117,8 @@ def test_runs_overlap_on_two_streams_of_one_context():
     prog, nl = build(o, st)
     rlk, ck = rand_key(st, o), rand_key(st, o)
     rks = {s: rand_key(st, o) for s in (1, 4)}
-    keys = (to_device(rlk), to_device(ck), {s: to_device(k) for s, k in rks.items()})
+    keys = (g.relin_key(to_device(rlk)), g.conjugation_key(to_device(ck)),
+            [g.rotation_key(to_device(k), s) for s, k in rks.items()])
     ins = [np.stack([si.uniform_poly(st, o.q, o.N) for _ in range(2)]) for _ in range(4)]
     refs = [obt.run(o, prog, a, rlk, ck, rks) for a in ins]
     dps = [bt.DeviceProgram(g, prog, *keys, in_limbs=nl) for _ in range(2)]

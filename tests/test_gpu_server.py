@@ -45,8 +45,8 @@ class Workload:
         st = si.Stream(seed, 1)
         self.rlk = rand_key(st, self.o)
         self.rk = {k: rand_key(st, self.o) for k in STEPS}
-        self.d_rlk = to_device(self.rlk)
-        self.d_rk = {k: to_device(v) for k, v in self.rk.items()}
+        self.d_rlk = self.g.relin_key(to_device(self.rlk))
+        self.d_rk = {k: self.g.rotation_key(to_device(v), k) for k, v in self.rk.items()}
         self.pool = {nl: [rand_ct(st, self.o, nl) for _ in range(2)] for nl in levels}
         self.d_pool = {nl: [to_device(c) for c in cts] for nl, cts in self.pool.items()}
         self.reqs = []
