@@ -73,6 +73,9 @@ def lib():
         for name in ("or_ntt_limbs", "or_intt_limbs"):
             getattr(L, name).argtypes = [ctypes.c_void_p, _u64p, _intp, ctypes.c_int]
         L.or_bconv.argtypes = [ctypes.c_void_p, _u64p, _intp, ctypes.c_int, _u64p, _intp, ctypes.c_int]
+        L.or_bconv_centred.argtypes = L.or_bconv.argtypes
+        L.or_ctx_set_rounding.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_ctx_set_rounding.restype = None
         L.or_modup.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
         L.or_moddown.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p]
         L.or_keyswitch.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int, _u64p, _u64p, _u64p]
@@ -154,9 +157,10 @@ def find_primes(logN: int, bits: int, count: int, exclude=()) -> list[int]:
 
 class Context:
     """Oracle context: ``nq`` q-primes then ``nk`` special primes at ring
-    degree N = 2^logN with ``dnum`` key-switching digits."""
+    degree N = 2^logN with ``dnum`` key-switching digits.  ``nearest`` selects
+    the rounding of ModDown and Rescale (see ``set_rounding``)."""
 
-    def __init__(self, logN: int, q_primes, p_primes, dnum: int):
+    def __init__(self, logN: int, q_primes, p_primes, dnum: int, nearest: bool = False):
         self.logN = logN
         self.N = 1 << logN
         self.q = [int(x) for x in q_primes]
@@ -169,6 +173,14 @@ class Context:
             raise ValueError("invalid oracle parameters")
         self._h = ctypes.c_void_p(h)
         self.alpha = lib().or_ctx_alpha(self._h)
+        self.set_rounding(nearest)
+
+    def set_rounding(self, nearest: bool):
+        """Floor (False, the default) or round-to-nearest (True) for every
+        ModDown (centred conversion of the special limbs) and Rescale (centred
+        SwitchModulo)."""
+        self.nearest = bool(nearest)
+        lib().or_ctx_set_rounding(self._h, 1 if nearest else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -210,10 +222,12 @@ class Context:
         lib().or_intt_limbs(self._h, _p(a), _p(pi), len(pi)); return a
 
     # key-switching steps
-    def bconv(self, src, src_idx, dst_idx) -> np.ndarray:
+    def bconv(self, src, src_idx, dst_idx, centred: bool = False) -> np.ndarray:
+        """Eq. 1 from canonical residues, or (centred) from the centred ones."""
         src = _u64(src); si = _i32(src_idx); di = _i32(dst_idx)
         out = np.empty((len(di), self.N), dtype=np.uint64)
-        lib().or_bconv(self._h, _p(src), _p(si), len(si), _p(out), _p(di), len(di)); return out
+        fn = lib().or_bconv_centred if centred else lib().or_bconv
+        fn(self._h, _p(src), _p(si), len(si), _p(out), _p(di), len(di)); return out
 
     def modup(self, d) -> np.ndarray:
         d = _u64(d); nl = d.shape[0]
@@ -313,8 +327,11 @@ class Context:
     def scalar_mult(self, a, k) -> np.ndarray:
         return self._ct_op("or_scalar_mult", a, k)
 
-    def rescale(self, a, nearest: bool = False) -> np.ndarray:
-        """Rescale by the last prime: floor(x / q_l), or round(x / q_l) with nearest."""
+    def rescale(self, a, nearest: bool | None = None) -> np.ndarray:
+        """Rescale by the last prime: floor(x / q_l), or round(x / q_l) with
+        nearest (default: the context's rounding)."""
+        if nearest is None:
+            nearest = self.nearest
         a = _u64(a); nl = a.shape[1]
         out = np.empty((2, nl - 1, self.N), dtype=np.uint64)
         fn = lib().or_rescale_round if nearest else lib().or_rescale

@@ -163,6 +163,7 @@ typedef struct {
     u64 *psi_brv;    /* [np][N]: psi^brv(k) */
     u64 *ipsi_brv;   /* [np][N]: psi^-brv(k) */
     u64 *n_inv;      /* N^-1 mod prime i */
+    int nearest;     /* rounding of ModDown and Rescale: 0 floor, 1 nearest (or_ctx_set_rounding) */
 } or_ctx;
 
 /* Thread count of the OpenMP loops over limbs and digits, for timing the
@@ -219,6 +220,15 @@ or_ctx *or_ctx_create(int logN, int nq, int nk, int dnum, const u64 *primes)
 }
 
 u64 or_ctx_psi(const or_ctx *c, int pi) { return c->psi[pi]; }
+
+/*
+ * Rounding of the two divisions of the path (the paper's ModDown and Rescale
+ * fusions, Sec. III-F5, state the formulas without a rounding offset):
+ * 0 = floor, the literal reading (canonical representatives); 1 = nearest
+ * (centred representatives: ModDown converts the centred residues of the
+ * special limbs, Rescale lifts the centred residue of the dropped limb).
+ */
+void or_ctx_set_rounding(or_ctx *c, int nearest) { c->nearest = nearest ? 1 : 0; }
 int or_ctx_alpha(const or_ctx *c) { return c->alpha; }
 
 /* prime index of limb z of an extended polynomial over q_0..q_{nl-1}, p_0.. */
@@ -326,8 +336,11 @@ void or_intt_limbs(const or_ctx *c, u64 *a, const int *pidx, int n)
  *   y_p = ( sum_i [x_i * qhat_i^-1]_{q_i} * [qhat_i]_p ) mod p,
  * qhat_i = prod_{k != i} q_k over the source base.  Coefficient domain.
  * ---------------------------------------------------------------------- */
-void or_bconv(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
-              u64 *dst, const int *dst_idx, int n_dst)
+/* The conversion with each [x_i qhat_i^-1]_{q_i} taken as its canonical
+ * representative v in [0, q_i) (centred = 0) or as its centred one, v - q_i
+ * when v > (q_i - 1) / 2 (centred = 1). */
+static void bconv_impl(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
+                       u64 *dst, const int *dst_idx, int n_dst, int centred)
 {
     u64 N = c->N;
     u64 *qhat_inv = (u64 *)malloc(sizeof(u64) * n_src);
@@ -352,13 +365,27 @@ void or_bconv(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
             for (int i = 0; i < n_src; i++) {
                 u64 qi = c->primes[src_idx[i]];
                 u64 v = mul_mod(src[(u64)i * N + n], qhat_inv[i], qi);
-                acc = add_mod(acc, mul_mod(v % p, qhat_mod[i * n_dst + d], p), p);
+                u64 vp = (centred && v > (qi - 1) / 2) ? sub_mod(0, (qi - v) % p, p)   /* v - q_i, negative */
+                                                        : v % p;
+                acc = add_mod(acc, mul_mod(vp, qhat_mod[i * n_dst + d], p), p);
             }
             dst[(u64)d * N + n] = acc;
         }
     }
     free(qhat_inv);
     free(qhat_mod);
+}
+
+void or_bconv(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
+              u64 *dst, const int *dst_idx, int n_dst)
+{
+    bconv_impl(c, src, src_idx, n_src, dst, dst_idx, n_dst, 0);
+}
+
+void or_bconv_centred(const or_ctx *c, const u64 *src, const int *src_idx, int n_src,
+                      u64 *dst, const int *dst_idx, int n_dst)
+{
+    bconv_impl(c, src, src_idx, n_src, dst, dst_idx, n_dst, 1);
 }
 
 /* number of digits in use at nl limbs: beta = ceil(nl / alpha) */
@@ -409,7 +436,10 @@ void or_modup(const or_ctx *c, const u64 *d, int nl, u64 *ext)
  * ModDown (Sec. III-F3 and the "ModDown fusion" item of Sec. III-F5):
  * x has nl q-limbs then K p-limbs, evaluation form.  INTT the p-limbs,
  * base-convert P -> Q_l, NTT, and return P^-1 (x_i - conv_i) mod q_i.
- * (Floor semantics: no rounding offset is added.)
+ * Floor (the context's default): the conversion takes canonical residues, so
+ * conv = [x]_P + u P with 0 <= u < K and the result is floor(x / P) - u.
+ * Nearest: it takes centred residues, so conv = x - P r with |conv| < K P / 2
+ * and the result r is within K / 2 of x / P, with a mean error of zero.
  */
 void or_moddown(const or_ctx *c, const u64 *x, int nl, u64 *out)
 {
@@ -423,7 +453,7 @@ void or_moddown(const or_ctx *c, const u64 *x, int nl, u64 *out)
     for (int i = 0; i < nl; i++) qi[i] = i;
     or_intt_limbs(c, xp, pk, K);
     u64 *conv = (u64 *)malloc(sizeof(u64) * nl * N);
-    or_bconv(c, xp, pk, K, conv, qi, nl);
+    bconv_impl(c, xp, pk, K, conv, qi, nl, c->nearest);
     or_ntt_limbs(c, conv, qi, nl);
     #pragma omp parallel for schedule(static)
     for (int i = 0; i < nl; i++) {

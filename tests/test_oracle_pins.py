@@ -248,6 +248,79 @@ def test_moddown_is_floor_division_by_P(mid):
         assert 0 <= u < mid.nk
 
 
+def test_bconv_centred_is_x_plus_u_Q_with_centred_u(mid):
+    """The conversion from centred residues: y_p = X + u Q_src (mod p) with
+    one integer u, |u| <= |src| / 2 + 1, for every target p; and it differs
+    from the canonical conversion by exactly -c Q_src, c the number of
+    residues [x_i qhat_i^-1]_{q_i} above (q_i - 1) / 2."""
+    st = si.Stream(31)
+    src = [0, 1, 2, 3]
+    dst = list(range(4, len(mid.primes)))
+    sp = [mid.primes[i] for i in src]
+    x = si.uniform_poly(st, sp, mid.N)
+    yc = mid.bconv(x, src, dst, centred=True)
+    yf = mid.bconv(x, src, dst)
+    Qs = 1
+    for q in sp:
+        Qs *= q
+    X = oracle.crt(x, sp)
+    lo, hi = -(len(src) // 2) - 1, len(src) // 2 + 1
+    for n in range(0, mid.N, 89):
+        us = set()
+        for k, di in enumerate(dst):
+            p = mid.primes[di]
+            cand = [u for u in range(lo, hi + 1) if (X[n] + u * Qs - int(yc[k, n])) % p == 0]
+            assert len(cand) == 1
+            us.add(cand[0])
+        assert len(us) == 1
+        cnt = 0
+        for i, q in enumerate(sp):
+            qhat = Qs // q
+            v = int(x[i, n]) * pow(qhat % q, -1, q) % q
+            cnt += v > (q - 1) // 2
+        for k, di in enumerate(dst):
+            p = mid.primes[di]
+            assert (int(yf[k, n]) - cnt * Qs - int(yc[k, n])) % p == 0
+
+
+def test_moddown_nearest_is_round_within_K_over_2(mid):
+    """Nearest ModDown: out P = X - S (mod Q_l P) with S = X (mod P) and
+    |S| < K P / 2, so out is within K/2 of X / P; its error S / P has mean
+    about 0, where floor's has mean about K / 2 (the floor's 1/2 and the
+    conversion term u in [0, K) with mean (K - 1) / 2)."""
+    nl = 7
+    st = si.Stream(32)
+    ep = list(range(nl)) + [mid.nq + k for k in range(mid.nk)]
+    x = si.uniform_poly(st, [mid.primes[i] for i in ep], mid.N)
+    xc = _coeff(mid, x, ep)
+    Ql, P = 1, 1
+    for q in mid.q[:nl]:
+        Ql *= q
+    for p in mid.p:
+        P *= p
+    X = oracle.crt(xc, mid.q[:nl] + mid.p)
+    means = {}
+    for nearest in (False, True):
+        mid.set_rounding(nearest)
+        try:
+            oc = _coeff(mid, mid.moddown(x), list(range(nl)))
+        finally:
+            mid.set_rounding(False)
+        O = oracle.crt(oc, mid.q[:nl])
+        errs = []
+        for n in range(mid.N):
+            S = oracle.centered([(X[n] - O[n] * P) % (Ql * P)], Ql * P)[0]
+            assert (S - X[n]) % P == 0
+            if nearest:
+                assert abs(S) < mid.nk * P // 2
+            else:
+                assert 0 <= S < (mid.nk + 1) * P
+            errs.append(S / P)
+        means[nearest] = float(np.mean(errs))
+    assert abs(means[True]) < 0.1, means
+    assert abs(means[False] - mid.nk / 2) < 0.25, means
+
+
 def test_rescale_is_exact_floor(mid):
     nl = 9
     st = si.Stream(14)
@@ -435,6 +508,32 @@ def test_hrotate_decrypts_to_rotation(small, small_client):
     o3 = small.rotate(ct, 3, r3)
     assert _rel_err(small_client.decrypt(o12, 2.0**40), small_client.decrypt(o3, 2.0**40)) < 2.0**-20
     assert _rel_err(small_client.decrypt(o3, 2.0**40), np.roll(z, -3)) < 2.0**-20
+
+
+def test_nearest_rounding_meets_the_bound_at_logN16():
+    """At logN=16 (30 x 54-bit q, K = 10, dnum = 3, scale 2^40) floor rounding
+    leaves a same-sign error on every coefficient of the key-switch output
+    (the conversion term u in [0, K) and the floor), which the decoding sums
+    coherently into the slots whose evaluation point is near 1 (Galois
+    exponents 1, 5, ..., 2N - 3 of the slot group): the rotation misses 2^-20
+    there.  Round-to-nearest removes the mean and meets
+    it; HMult+relin at scale 2^80 meets it either way."""
+    P = si.FULL
+    o = make_ctx(P.logN, P.nq, P.q_bits, P.nk, P.p_bits, P.dnum)
+    cl = Client(o, seed=si.workload_seed(1) + 7)
+    z1, z2 = cl.random_slots(), cl.random_slots()
+    a, b = cl.encrypt(z1, P.nq, 2.0**40), cl.encrypt(z2, P.nq, 2.0**40)
+    rk, rlk = cl.rotation_key(1), cl.relin_key()
+    errs = {}
+    for nearest in (False, True):
+        o.set_rounding(nearest)
+        d = cl.decrypt(o.rotate(a, 1, rk), 2.0**40) - np.roll(z1, -1)
+        errs[nearest] = np.abs(d)
+        assert _rel_err(cl.decrypt(o.hmult(a, b, rlk), 2.0**80), z1 * z2) < 2.0**-20
+    assert errs[False].max() > 2.0**-19
+    assert errs[True].max() < 2.0**-20
+    # elsewhere the two agree to well below the bound
+    assert np.median(errs[False]) < 2.0**-22 and np.median(errs[True]) < 2.0**-22
 
 
 def test_rotation_by_half_the_ring_is_the_identity(small, small_client):
