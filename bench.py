@@ -393,6 +393,23 @@ def run_fides(args, world, rank, local):
                          "residues equal to the two calls), then HRotate",
              "value": round(ops / (ms_fused / 1e3), 2), "unit": "ops/s", "ms_per_step": round(ms_fused / args.steps, 4)}
 
+    # ------- the same steps under round-to-nearest ModDown and Rescale (the
+    # mode whose decryption error meets 2^-20 at this size) -------
+    ctx.set_rounding(True)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_rounding(False)
+    ms_near = max_over_ranks(e0.elapsed_time(e1), world)
+    nearest = {"workload": "the same steps with the context in round-to-nearest mode (centred ModDown conversion, "
+                           "centred Rescale lift)",
+               "value": round(ops / (ms_near / 1e3), 2), "unit": "ops/s", "ms_per_step": round(ms_near / args.steps, 4)}
+
     # ------- the same K steps again, every launch bracketed by events -------
     # (events between launches serialise programmatic dependent launch, so
     # this pass gives per-kernel durations, not the value above)
@@ -533,6 +550,7 @@ def run_fides(args, world, rank, local):
         "clocks": ck,
         "e2e": e2e,
         "fused_hmult_rescale": fused,
+        "round_to_nearest": nearest,
         "batched": batched,
         "serving": serving,
         "ops": ops_extra,

@@ -181,6 +181,30 @@ int fides_ctx_status(fides_ctx *ctx, int *flags);
 int fides_ctx_selftest_wait(fides_ctx *ctx, int limit_us, void *stream);
 
 /*
+ * Rounding of the two divisions of the path -- ModDown's division by P and
+ * Rescale's division by q_l -- for every operation of this context (single
+ * operations, batches, the server and programs).  The paper's ModDown and
+ * Rescale fusion formulas (Sec. III-F5) state no rounding offset.
+ *   FIDES_ROUND_FLOOR (the default): canonical residues.  Rescale gives
+ *     floor(x / q_l); ModDown gives floor(x / P) - u with the conversion term
+ *     0 <= u < K.  Both errors have a nonzero mean, which decoding sums
+ *     coherently into the slots whose evaluation point is near 1: at
+ *     logN=16, K=10, scale 2^40 a rotation decrypts within about 2^-14 there.
+ *   FIDES_ROUND_NEAREST: centred residues.  Rescale gives round(x / q_l)
+ *     (as fides_rescale_round); ModDown converts the centred residues of the
+ *     special limbs, so its result is within K/2 of x / P with a mean error
+ *     of zero (same work: the correction rides in a spare column of the
+ *     tensor-core conversion).  The same rotation decrypts within 2^-20.
+ * Affects calls issued after it returns; set it before building batches,
+ * servers or programs, which capture the mode when they plan.  Returns
+ * FIDES_OK or FIDES_ERR_ARG.  fides_ctx_rounding reads the mode.
+ */
+#define FIDES_ROUND_FLOOR 0
+#define FIDES_ROUND_NEAREST 1
+int fides_ctx_set_rounding(fides_ctx *ctx, int mode);
+int fides_ctx_rounding(const fides_ctx *ctx);
+
+/*
  * Whether base conversions of this context run on the tensor cores (1: every
  * digit and K have at most 16 primes) or on the integer pipes (0).  Results
  * are identical.
@@ -221,8 +245,9 @@ int fides_modup(fides_ctx *ctx, const uint64_t *dev_d, int n_limbs, uint64_t *de
 /*
  * ModDown (Sec. III-F3, Sec. III-F5 "ModDown fusion"): dev_x is an extended
  * polynomial [n_limbs + K][N] in evaluation form; dev_out [n_limbs][N]
- * receives P^-1 (x_i - NTT(Conv_{P->Q}(INTT(x_P))))_i mod q_i (floor, no
- * rounding offset).
+ * receives P^-1 (x_i - NTT(Conv_{P->Q}(INTT(x_P))))_i mod q_i, the conversion
+ * taking canonical residues (FIDES_ROUND_FLOOR) or centred ones
+ * (FIDES_ROUND_NEAREST), per fides_ctx_set_rounding.
  */
 int fides_moddown(fides_ctx *ctx, const uint64_t *dev_x, int n_limbs, uint64_t *dev_out, void *stream);
 
@@ -271,8 +296,10 @@ int fides_rotate(fides_ctx *ctx, const fides_ct *a, int64_t steps, const fides_k
 /*
  * Rescale (Table I, Sec. III-F5 "Rescale fusion"): drops the last limb q_l,
  * l = a->n_limbs - 1 >= 1: out_i = q_l^-1 (x_i - NTT_{q_i}([INTT(x_l)]_{q_i}))
- * mod q_i, which is floor(x / q_l) limb-wise.  out->n_limbs must equal
- * a->n_limbs - 1; out->scale = a->scale / q_l.  out may not alias a.
+ * mod q_i, which is floor(x / q_l) limb-wise (FIDES_ROUND_FLOOR), or
+ * round(x / q_l) with the centred lift (FIDES_ROUND_NEAREST, see
+ * fides_ctx_set_rounding).  out->n_limbs must equal a->n_limbs - 1;
+ * out->scale = a->scale / q_l.  out may not alias a.
  */
 int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 
@@ -281,8 +308,8 @@ int fides_rescale(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream
  * SwitchModulo takes the centred representative of each coefficient r of
  * INTT(x_l) (r - q_l when r > (q_l - 1) / 2), which gives round(x / q_l)
  * limb-wise (q_l is odd, so there are no ties; a value just below Q_l rounds
- * to Q_{l-1}, that is 0).  Same arguments, layout, errors and scale as
- * fides_rescale.  The batched, program and server paths rescale by floor.
+ * to Q_{l-1}, that is 0), whatever the context's rounding mode.  Same
+ * arguments, layout, errors and scale as fides_rescale.
  */
 int fides_rescale_round(fides_ctx *ctx, const fides_ct *a, fides_ct *out, void *stream);
 

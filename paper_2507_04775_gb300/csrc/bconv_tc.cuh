@@ -37,6 +37,15 @@
 // both exact) starts every accumulator at 2^23, so that its fp32 bits read
 // 0x4B000000 + D with no conversion.
 //
+// Centred conversion (round-to-nearest ModDown): the sources in the upper half
+// of their range stand for x - q, which adds c (-Q_src) to every target, c
+// their count.  ModDown images carry a correction block after the offset
+// column (byte b of -Q_src mod p_t in elements 0..3 of row b); each of the
+// four threads of a row puts the count among its own sources (0..4) into
+// element s0 of that column of A, so the MMA adds c (-Q_src) byte by byte.
+// It adds at most 16 x 255 to a sum, which keeps every sum below 2^23 for up
+// to 16 sources (8 x 16 x 255^2 + 4080 < 2^23).  Floor jobs put zeros there.
+//
 // Every wait is bounded (about 2 s of %globaltimer): on a timeout the CTA sets
 // FIDES_STATUS_WAIT_TIMEOUT in the context's status word, skips its outputs,
 // frees its tensor memory and returns.
@@ -264,7 +273,7 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
 
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int N = 1 << logN, ntiles = N / TC_M;
-    const int ns = B.n_src, nsp = (ns + 2) & ~1;   // sources and the offset column, even
+    const int ns = B.n_src, nsp = (ns + 2 + B.tc_corr) & ~1;   // sources, offset and correction columns, even
     int nd = 0;
     for (int r = 0; r < B.nrun; ++r) nd += B.run[r].count;
     const int ndp = (nd + 1) & ~1;
@@ -307,6 +316,12 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     const int m = t & (TC_M - 1), s0 = t / TC_M;
     unsigned char *arow = sA + (m >> 3) * (nsp * 128) + (m & 7) * 16;
     u64 xr[SPT];
+    u64 half[SPT];   // (q_s - 1) / 2 of this thread's sources (centred jobs)
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+        const int s = s0 + k * (TC_THREADS / TC_M);
+        half[k] = (B.centred && s < ns) ? (P[B.src_prime0 + s].q >> 1) : ~0ull;
+    }
     int tile = blockIdx.x;
     if (tile < ntiles) {
 #pragma unroll
@@ -319,7 +334,7 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     // m; the image holds 2^15 there for every output byte) and a zero column
     if (t < TC_M) {
         *(uint4 *)(arow + ns * 128) = make_uint4(0x5C00u, 0, 0, 0);
-        if (ns + 1 < nsp) *(uint4 *)(arow + (ns + 1) * 128) = make_uint4(0, 0, 0, 0);
+        for (int col = ns + 1; col < nsp; ++col) *(uint4 *)(arow + col * 128) = make_uint4(0, 0, 0, 0);
     }
     // one thread polls each mbarrier; the others wait at the CTA barrier
     if (t == 0) {
@@ -339,10 +354,17 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     const int q4 = w & 3, grp = w >> 2;
     constexpr int GROUPS = TC_THREADS / 128;
     for (u32 phase = 0; ok && tile < ntiles; tile += gridDim.x, phase ^= 1) {
+        u32 cnt = 0;
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             const int s = s0 + k * (TC_THREADS / TC_M);
             if (s < ns) *(uint4 *)(arow + s * 128) = bytes_f16(xr[k]);
+            cnt += xr[k] > half[k] ? 1u : 0u;   // half = ~0: never (floor jobs, missing sources)
+        }
+        if (B.centred) {
+            // fp16 of 0..4
+            const u32 f = cnt == 0 ? 0u : (cnt == 1 ? 0x3C00u : (cnt == 2 ? 0x4000u : (cnt == 3 ? 0x4200u : 0x4400u)));
+            *(uint16_t *)(arow + (ns + 1) * 128 + 2 * s0) = (uint16_t)f;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
@@ -416,7 +438,7 @@ inline int bconv_tc_smem(const BConvJob &j)
 {
     int nd = 0;
     for (int r = 0; r < j.nrun; ++r) nd += j.run[r].count;
-    const int nsp = (j.n_src + 2) & ~1, ndp = (nd + 1) & ~1;
+    const int nsp = (j.n_src + 2 + j.tc_corr) & ~1, ndp = (nd + 1) & ~1;
     return 2048 * nsp + 128 * ndp * nsp;
 }
 

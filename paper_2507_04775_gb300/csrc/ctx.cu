@@ -158,6 +158,7 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_md_scale);
     cudaFree(c->d_md_mat);
     cudaFree(c->d_md_pinv);
+    cudaFree(c->d_md_negp);
     cudaFree(c->d_rs_qlinv);
     cudaFree(c->d_hr);
     cudaFree(c->d_mu_nscale);
@@ -178,6 +179,19 @@ extern "C" int fides_ctx_status(fides_ctx *c, int *flags)
     if (!rc) rc = fides_check_cuda(cudaMemcpy(flags, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "fides_ctx_status");
     if (!rc) rc = fides_check_cuda(cudaMemset(c->d_status, 0, sizeof(int)), "fides_ctx_status");
     return rc;
+}
+
+extern "C" int fides_ctx_set_rounding(fides_ctx *c, int mode)
+{
+    if (!c || (mode != FIDES_ROUND_FLOOR && mode != FIDES_ROUND_NEAREST))
+        return fides_set_error(FIDES_ERR_ARG, "fides_ctx_set_rounding: mode must be FIDES_ROUND_FLOOR or _NEAREST");
+    c->round_nearest = mode == FIDES_ROUND_NEAREST;
+    return FIDES_OK;
+}
+
+extern "C" int fides_ctx_rounding(const fides_ctx *c)
+{
+    return c && c->round_nearest ? FIDES_ROUND_NEAREST : FIDES_ROUND_FLOOR;
 }
 
 extern "C" int fides_ctx_tensor_bconv(const fides_ctx *c)
@@ -269,15 +283,17 @@ static uint16_t f16_of_byte(unsigned k)
 // for target t (prime targets[t]) and source s (constant cst(s, z)), one 8 x 8
 // core matrix of fp16 values in 16-byte rows, row b, column a = byte b of
 // (cst(s, z) * 2^(8a) mod p_z); then, per target, the offset block (2^15 in
-// column 0 of every row, zeros elsewhere).  Targets are padded to an even count,
-// and sources plus the offset block to an even count, with zero blocks.
-// Returns the image's byte offset.
+// column 0 of every row, zeros elsewhere) and, with corr, the correction block
+// (byte b of corr[z] in columns 0..3 of row b: the conversion kernel puts up
+// to four partial counts there, see bconv_tc.cuh).  Targets are padded to an
+// even count, and the source, offset and correction blocks to an even count,
+// with zero blocks.  Returns the image's byte offset.
 template <class F>
 static size_t tc_image(const u64 *primes, const std::vector<int> &targets, int ns, F cst,
-                       std::vector<uint16_t> &img)
+                       std::vector<uint16_t> &img, const u64 *corr = nullptr)
 {
     const size_t off = img.size() * 2;
-    const int nd = (int)targets.size(), ndp = (nd + 1) & ~1, nsp = (ns + 2) & ~1;
+    const int nd = (int)targets.size(), ndp = (nd + 1) & ~1, nsp = (ns + 2 + (corr ? 1 : 0)) & ~1;
     img.resize(img.size() + (size_t)ndp * nsp * 64, 0);
     uint16_t *base = img.data() + off / 2;
     for (int t = 0; t < nd; ++t) {
@@ -294,6 +310,11 @@ static size_t tc_image(const u64 *primes, const std::vector<int> &targets, int n
         // offset column: 2^15 (fp16 0x7800) against A's 256 adds 2^23 to every sum
         uint16_t *blk = base + ((size_t)t * nsp + ns) * 64;
         for (int b = 0; b < 8; ++b) blk[b * 8] = 0x7800;
+        if (corr) {
+            uint16_t *cb = base + ((size_t)t * nsp + ns + 1) * 64;
+            for (int b = 0; b < 8; ++b)
+                for (int a = 0; a < 4; ++a) cb[b * 8 + a] = f16_of_byte((unsigned)((corr[z] >> (8 * b)) & 255));
+        }
     }
     return off;
 }
@@ -411,10 +432,15 @@ extern "C" int fides_ctx_create(int logN, int L, int dnum, const uint64_t *prime
             md_mat[(size_t)k * np + z] = h;
         }
     }
+    // md_negp[z] = -P mod prime z: the ModDown conversion from centred
+    // residues is the canonical one plus c (-P), c the number of residues in
+    // the upper half (round-to-nearest mode)
+    std::vector<u64> md_negp((size_t)np, 0);
     for (int i = 0; i < L; ++i) {
         u64 qi = primes[i], P = 1;
         for (int k = 0; k < K; ++k) P = hmul(P, primes[L + k] % qi, qi);
         md_pinv[i] = pair_of(hinv(P, qi), qi);
+        md_negp[i] = P ? qi - P : 0;
     }
 
     // Tensor-core conversion images: ModUp per (nl, j) with targets in the
@@ -444,7 +470,8 @@ extern "C" int fides_ctx_create(int logN, int L, int dnum, const uint64_t *prime
     if (c->tc_on & 2) {
         std::vector<int> tg;
         for (int z = 0; z < L; ++z) tg.push_back(z);
-        c->tc_md_off = tc_image(primes, tg, K, [&](int src, int z) { return md_mat[(size_t)src * np + z]; }, tc_img);
+        c->tc_md_off = tc_image(primes, tg, K, [&](int src, int z) { return md_mat[(size_t)src * np + z]; }, tc_img,
+                                md_negp.data());
     }
     if (tc_img.empty()) tc_img.resize(64, 0);
     std::vector<TwPair> c32((size_t)np);
@@ -500,6 +527,7 @@ extern "C" int fides_ctx_create(int logN, int L, int dnum, const uint64_t *prime
     if (!rc) rc = upload(&c->d_md_scale, md_scale, "moddown tables");
     if (!rc) rc = upload(&c->d_md_mat, md_mat, "moddown tables");
     if (!rc) rc = upload(&c->d_md_pinv, md_pinv, "moddown tables");
+    if (!rc) rc = upload(&c->d_md_negp, md_negp, "moddown tables");
     if (!rc) rc = upload(&c->d_rs_qlinv, rs, "rescale tables");
     if (!rc) rc = upload(&c->d_hr, hr, "rescale tables");
     if (!rc) rc = upload(&c->d_mu_nscale, mu_ns, "modup tables");

@@ -117,6 +117,8 @@ struct fides_ctx {
     TwPair *d_md_scale;   // [K]      Phat_k^-1 mod p_k
     u64 *d_md_mat;        // [K][L+K] [Phat_k]_{prime z}
     TwPair *d_md_pinv;    // [L]      P^-1 mod q_i
+    u64 *d_md_negp;       // [L+K]    -P mod prime z (q-primes; the special ones unused)
+    int round_nearest;    // FIDES_ROUND_NEAREST: ModDown converts centred residues, Rescale lifts the centred one
 
     // Rescale: [L][L], entry (l, i) = q_l^-1 mod q_i
     TwPair *d_rs_qlinv;

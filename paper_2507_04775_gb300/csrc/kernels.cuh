@@ -43,6 +43,9 @@ struct BConvJob {
     int nrun;
     BConvRun run[3];
     const void *tc;          // tensor-core image of the conversion matrix (bconv_tc.cuh), or null
+    int tc_corr;             // the image has the correction block (ModDown images)
+    int centred;             // convert the centred residues: add c * corr[z], c = #{i: x_i > (q_i - 1) / 2}
+    const u64 *corr;         // [prime z] the correction constant, -Q_src mod prime z (centred jobs)
 };
 
 // Jobs inline (djob == nullptr) or in device memory (djob[0..njob)).
@@ -91,6 +94,7 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
     __shared__ u64 smat[BCONV_TG * MS];
     __shared__ PrimeInfo sp[BCONV_TG];
     __shared__ u64 *sdst[BCONV_TG];
+    __shared__ u64 scorr[BCONV_TG];
     const int N = 1 << logN;
     const int ns = NS > 0 ? NS : B.n_src;
 
@@ -112,6 +116,7 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
         }
         sp[threadIdx.x] = P[pz];
         sdst[threadIdx.x] = ptr;
+        scorr[threadIdx.x] = B.centred ? B.corr[pz] : 0;
         for (int i = 0; i < ns; ++i) smat[threadIdx.x * MS + i] = B.mat[(size_t)i * B.ld + pz];
     }
     __syncthreads();
@@ -133,9 +138,21 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
             v[i] = 0;
         }
     }
+    // centred conversion: the residues in the upper half stand for v - q_i,
+    // which adds (their count) x (-Q_src) to every target
+    u64 cnt = 0;
+    if (B.centred) {
+#pragma unroll
+        for (int i = 0; i < MS; ++i)
+            if (NS > 0 || i < ns) cnt += v[i] > (P[B.src_prime0 + i].q >> 1) ? 1 : 0;
+    }
     int d = 0;
     for (; d + 1 < nd; d += 2) {
         Acc128 c0 = {0, 0, 0, 0}, c1 = {0, 0, 0, 0};
+        if (cnt) {
+            mac_wide(c0, cnt, scorr[d]);
+            mac_wide(c1, cnt, scorr[d + 1]);
+        }
         const u64 *m0 = smat + d * MS, *m1 = m0 + MS;
 #pragma unroll
         for (int i = 0; i < MS; ++i) {
@@ -149,6 +166,7 @@ __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *_
     }
     if (d < nd) {
         Acc128 c0 = {0, 0, 0, 0};
+        if (cnt) mac_wide(c0, cnt, scorr[d]);
         const u64 *m0 = smat + d * MS;
 #pragma unroll
         for (int i = 0; i < MS; ++i)

@@ -326,6 +326,7 @@ int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
         Seg g = seg_of(sc.last + t * N, cv, l, 0, B.acc + t * ne * N, out->data + (size_t)t * l * N, 0, 0,
                        c->d_hr + (size_t)l * c->L * 2);
         g.side = sc.dd + t * S;
+        g.g = c->round_nearest ? c->primes[l] : 0;   // centred lift of the dropped limb (round to nearest)
         v.push_back(g);
     }
     int rc = ntt_forward(c, inline_set(v), ProHmRs{}, EpiHmRs{}, st);
@@ -453,7 +454,8 @@ int fides_rotate_hoisted_ws(fides_ctx *c, const fides_ct *a, int n_rot, const in
 }
 
 // Rescale (Table I): floor(x / q_l), or round(x / q_l) with nearest (the
-// centred SwitchModulo of the dropped limb).
+// centred SwitchModulo of the dropped limb) -- asked for, or the context's
+// rounding mode.
 static int rescale_entry(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stream, u64 *ws, bool nearest)
 {
     const char *fn = nearest ? "fides_rescale_round" : "fides_rescale";
@@ -470,7 +472,7 @@ static int rescale_entry(fides_ctx *c, const fides_ct *a, fides_ct *out, void *s
     rs_intt_segs(c, a->data, nl, s.last, v);
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
     v.clear();
-    rs_final_segs(c, a->data, nl, s.last, out->data, v, nearest);
+    rs_final_segs(c, a->data, nl, s.last, out->data, v, nearest || c->round_nearest);
     int rc = ntt_forward(c, inline_set(v), ProSwitchMod{}, EpiSubMul{}, st);
     if (!rc) out->scale = a->scale / (double)c->primes[nl - 1];
     return rc;

@@ -198,7 +198,7 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
         u64 *base = scratch[i];
         if (o.type == FIDES_OP_RESCALE) {
             rs_intt_segs(c, o.a.data, nl, base, intt);
-            rs_final_segs(c, o.a.data, nl, base, o.out.data, rsfin);
+            rs_final_segs(c, o.a.data, nl, base, o.out.data, rsfin, c->round_nearest != 0);
             o.out.scale = o.a.scale / (double)c->primes[nl - 1];
             continue;
         }

@@ -85,7 +85,7 @@ extern "C" int fides_rescale_noalloc(fides_ctx *c, const fides_ct *a, fides_ct *
     rs_intt_segs(c, a->data, nl, scr, sl);
     int rc = ntt_inverse(c, last, ProSrc{}, EpiCanon{}, st);
     if (rc) return rc;
-    rs_final_segs(c, a->data, nl, scr, out->data, sf);
+    rs_final_segs(c, a->data, nl, scr, out->data, sf, c->round_nearest != 0);
     rc = ntt_forward(c, fin, ProSwitchMod{}, EpiSubMul{}, st);
     if (!rc) out->scale = a->scale / (double)c->primes[l];
     return rc;

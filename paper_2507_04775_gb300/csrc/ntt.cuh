@@ -256,12 +256,17 @@ struct EpiSubMulRot {
 // dropped limb l of the HMult result.  The segment's src is `last` (src_step
 // 0: one limb for every limb of the run), dst holds conv_i (the pass works in
 // place), aux = acc_i, side = d_i, out = res_i; cst holds two constants per
-// prime: cst[2i] = P^-1 mod q_i, cst[2i + 1] = q_l^-1 mod q_i.
+// prime: cst[2i] = P^-1 mod q_i, cst[2i + 1] = q_l^-1 mod q_i.  When the
+// segment's g holds q_l (round-to-nearest), `last` is lifted from its centred
+// representative, as ProSwitchMod does.
 struct ProHmRs {
     __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &p) const
     {
         const u64 x = mul_shoup(J.dst[j], J.cst[2 * J.prime], p.q);   // [0, 2q)
-        return x + reduce64_lazy(J.src[j], p);                        // [0, 4q)
+        const u64 v = J.src[j];
+        u64 r = reduce64_lazy(v, p);                                  // [0, 2q)
+        if (J.g && v > (J.g >> 1)) r = csub(r + p.q - csub(reduce64_lazy(J.g, p), p.q), p.q2);   // v - q_l, [0, 2q)
+        return x + r;                                                 // [0, 4q)
     }
 };
 struct EpiHmRs {

@@ -149,6 +149,9 @@ inline void ks_moddown_jobs(const fides_ctx *c, const KsBuffers &B, std::vector<
         J.nrun = 1;
         J.run[0] = BConvRun{B.conv + (size_t)t * B.nl * N, B.nl, 0};
         if (c->tc_on & 2) J.tc = (const unsigned char *)c->d_tc + c->tc_md_off;
+        J.tc_corr = 1;
+        J.centred = c->round_nearest;   // round-to-nearest: convert the centred residues
+        J.corr = c->d_md_negp;
         v.push_back(J);
     }
 }

@@ -39,9 +39,11 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_program_info", "fides_program_run", "fides_program_destroy", "fides_ctx_tune_table",
            "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale",
            "fides_rescale_round", "fides_key_register", "fides_key_destroy", "fides_key_galois",
-           "fides_batch_configure", "fides_batch_autotune", "fides_batch_tuning"]
+           "fides_batch_configure", "fides_batch_autotune", "fides_batch_tuning", "fides_ctx_set_rounding",
+           "fides_ctx_rounding"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
+ROUND_FLOOR, ROUND_NEAREST = 0, 1
 FAULT_LAUNCH_ERROR, FAULT_STALL = 1, 2
 STATUS_WAIT_TIMEOUT = 1      # fides_ctx_status bit: a bounded device wait ran out
 
@@ -161,6 +163,8 @@ def lib():
         L.fides_ctx_autotune.argtypes = [_vp, _i, _vp]
         L.fides_ctx_status.argtypes = [_vp, ctypes.POINTER(_i)]
         L.fides_ctx_tensor_bconv.argtypes = [_vp]
+        L.fides_ctx_set_rounding.argtypes = [_vp, _i]
+        L.fides_ctx_rounding.argtypes = [_vp]
         L.fides_ctx_selftest_wait.argtypes = [_vp, _i, _vp]
         L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
         L.fides_batch_create.argtypes = [_vp, ctypes.POINTER(fides_op), _i, ctypes.POINTER(_vp)]
@@ -325,6 +329,15 @@ class Context:
         """Runs a device wait that nothing completes, limited to limit_us; it
         sets STATUS_WAIT_TIMEOUT in the status word (see status())."""
         _check(lib().fides_ctx_selftest_wait(self._h, limit_us, _stream(stream)))
+
+    def set_rounding(self, nearest: bool):
+        """Floor (False, the default) or round-to-nearest (True) for every
+        ModDown and Rescale of this context (fides_ctx_set_rounding)."""
+        _check(lib().fides_ctx_set_rounding(self._h, ROUND_NEAREST if nearest else ROUND_FLOOR))
+
+    @property
+    def nearest(self) -> bool:
+        return lib().fides_ctx_rounding(self._h) == ROUND_NEAREST
 
     @property
     def tensor_bconv(self) -> bool:

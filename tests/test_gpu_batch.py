@@ -153,6 +153,35 @@ def test_batch_launch_groups_and_tensor_placement(group_limbs, tensor_split):
     g.close()
 
 
+def test_batch_in_round_to_nearest_mode():
+    """A batch planned in round-to-nearest mode (centred ModDown conversion,
+    centred Rescale lift) equals the single-op path and the oracle in the
+    same mode."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.MID
+    g, o, rlk, rk, drlk, drk, host, ops = build_case(P, [12, 5, 9, 2], 505)
+    g.set_rounding(True)
+    o.set_rounding(True)
+    batch = Batch(g, ops)
+    batch.configure(16, 1)
+    batch.run()
+    torch.cuda.synchronize()
+    ref = single_op_reference(g, host, drlk, drk)
+    torch.cuda.synchronize()
+    for e, r in zip(host, ref):
+        for k in ("m", "r", "mr", "s", "ms"):
+            if k in r:
+                assert np.array_equal(to_host(e[k].out), to_host(r[k])), (e["nl"], k)
+        nl = e["nl"]
+        prod = o.hmult(e["a"], e["b"], rlk)
+        assert np.array_equal(to_host(e["m"].out).reshape(2, nl, o.N), prod)
+        assert np.array_equal(to_host(e["ms"].out).reshape(2, nl - 1, o.N), o.rescale(prod))
+        assert np.array_equal(to_host(e["mr"].out).reshape(2, nl, o.N), o.rotate(prod, 3, rk))
+    batch.close()
+    g.close()
+
+
 def test_batch_autotune_keeps_results():
     """The autotuner picks a grouping and tensor placement by timing them on
     the batch; the chosen plan still computes the oracle's residues, also

@@ -92,6 +92,52 @@ def test_one_conversion_on_the_integer_kernel(shape):
         g.hmult(to_device(a), to_device(b), nl, drlk, m)
         torch.cuda.synchronize()
         assert np.array_equal(to_host(m).reshape(a.shape), o.hmult(a, b, rlk)), nl
+    # round-to-nearest: the centred ModDown conversion on the same kernels
+    g.set_rounding(True)
+    o.set_rounding(True)
+    for nl in (nq, nq - 5):
+        d = si.uniform_poly(st, o.q[:nl], o.N)
+        x = si.uniform_poly(st, o.q[:nl] + o.p, o.N)
+        check_modup_moddown(g, o, d, x, nl, "random, nearest")
+    assert g.status() == 0
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["SMALL", "FULL", "WIDE"])
+def test_centred_conversion_on_extreme_residues(name):
+    """Round-to-nearest ModDown on special limbs whose converted residues sit
+    at the centring boundary ((p - 1) / 2 and (p + 1) / 2), at p - 1 and at 0
+    (every source in the upper half: the largest correction the tensor-core
+    sums carry)."""
+    need_gpu()
+    P = getattr(si, name)
+    g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
+    g.set_rounding(True)
+    o.set_rounding(True)
+    nl = P.nq
+    st = si.Stream(1600, 2)
+    d = si.uniform_poly(st, o.q[:nl], o.N)
+    pidx = [o.nq + k for k in range(o.nk)]
+    for what in ("boundary", "all upper", "zero"):
+        x = si.uniform_poly(st, o.q[:nl] + o.p, o.N)
+        # choose the coefficient form of the special limbs so that the
+        # conversion's sources [x_k Phat_k^-1]_{p_k} take the wanted values
+        coef = np.empty((o.nk, o.N), dtype=np.uint64)
+        for k, p in enumerate(o.p):
+            Phat = 1
+            for m, pm in enumerate(o.p):
+                if m != k:
+                    Phat *= pm
+            if what == "boundary":
+                want = [(p - 1) // 2, (p + 1) // 2, p - 1, 0, 1]
+                vals = np.resize(np.array(want, dtype=object), o.N)
+            elif what == "all upper":
+                vals = np.full(o.N, p - 1, dtype=object)
+            else:
+                vals = np.zeros(o.N, dtype=object)
+            coef[k] = np.array([int(v) * (Phat % p) % p for v in vals], dtype=np.uint64)
+        x[nl:] = o.ntt_limbs(coef, pidx)
+        check_modup_moddown(g, o, d, x, nl, what)
     assert g.status() == 0
     g.close()
 

@@ -293,6 +293,54 @@ def test_hmult_rescale(pair):
         assert np.array_equal(to_host(out).reshape(2, nl - 1, o.N), ref), "hmult_rescale differs at nl=%d" % nl
 
 
+def test_round_to_nearest_mode(pair):
+    """Both contexts in round-to-nearest mode (ModDown converts centred
+    residues, Rescale lifts the centred one): ModDown, KeySwitch, HMult,
+    HRotate, Rescale and the fused HMult+Rescale equal the oracle's, at the
+    top level and a ragged one, and differ from the floor results."""
+    P, g, o = pair
+    st = si.Stream(1016, 17)
+    key = rand_key(st, o)
+    buf = to_device(key)
+    rlk = g.relin_key(buf)
+    g.set_rounding(True)
+    o.set_rounding(True)
+    try:
+        assert g.nearest
+        for nl in sorted({P.nq, max(2, P.nq - 3)}):
+            ne = nl + len(o.p)
+            x = rand_poly(st, o.q[:nl] + o.p, o.N)
+            out = torch.zeros(nl * o.N, dtype=torch.int64, device="cuda")
+            g.moddown(to_device(x), nl, out)
+            want = o.moddown(x)
+            assert np.array_equal(to_host(out).reshape(nl, o.N), want), "moddown nl=%d" % nl
+            o.set_rounding(False)
+            assert not np.array_equal(want, o.moddown(x))
+            o.set_rounding(True)
+            a, b = rand_poly(st, o.q[:nl], o.N, 2), rand_poly(st, o.q[:nl], o.N, 2)
+            da, db = to_device(a), to_device(b)
+            m = torch.zeros(2 * nl * o.N, dtype=torch.int64, device="cuda")
+            g.hmult(da, db, nl, rlk, m)
+            ref_m = o.hmult(a, b, key)
+            assert np.array_equal(to_host(m).reshape(2, nl, o.N), ref_m), "hmult nl=%d" % nl
+            r = torch.zeros_like(m)
+            g.rotate(da, nl, 3, g.rotation_key(buf, 3), r)
+            assert np.array_equal(to_host(r).reshape(2, nl, o.N), o.rotate(a, 3, key)), "rotate nl=%d" % nl
+            o0, o1 = (torch.zeros(nl * o.N, dtype=torch.int64, device="cuda") for _ in range(2))
+            g.keyswitch(da, nl, rlk, o0, o1)
+            w0, w1 = o.keyswitch(a[0], key)
+            assert np.array_equal(to_host(o0).reshape(nl, o.N), w0) and np.array_equal(to_host(o1).reshape(nl, o.N), w1)
+            rs = torch.zeros(2 * (nl - 1) * o.N, dtype=torch.int64, device="cuda")
+            g.rescale(m, nl, rs)
+            assert np.array_equal(to_host(rs).reshape(2, nl - 1, o.N), o.rescale(ref_m)), "rescale nl=%d" % nl
+            fu = torch.zeros_like(rs)
+            g.hmult_rescale(da, db, nl, rlk, fu)
+            assert np.array_equal(to_host(fu).reshape(2, nl - 1, o.N), o.rescale(ref_m)), "hmult_rescale nl=%d" % nl
+    finally:
+        g.set_rounding(False)
+        o.set_rounding(False)
+
+
 def test_galois_and_psi(pair):
     P, g, o = pair
     for i in range(len(o.primes)):

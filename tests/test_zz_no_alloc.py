@@ -67,6 +67,15 @@ def test_rescale_noalloc_matches_oracle_and_rescale(P):
         want = orc.rescale(a)
         assert np.array_equal(to_host(got).reshape(2, nl - 1, N), want), "call %d differs from the oracle" % call
         assert np.array_equal(to_host(got), to_host(ref)), "call %d differs from fides_rescale" % call
+    # the context's round-to-nearest mode applies here too
+    ctx.set_rounding(True)
+    a = np.stack([si.uniform_poly(st, q, N) for _ in range(2)])
+    da = to_device(a)
+    got = torch.full((2 * (nl - 1) * N,), -1, dtype=torch.int64, device="cuda")
+    ca, cg = _ct(da, nl), _ct(got, nl - 1)
+    assert L.fides_rescale_noalloc(ctx._h, ctypes.byref(ca), ctypes.byref(cg), stream) == 0, L.fides_last_error()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(got).reshape(2, nl - 1, N), orc.rescale(a, nearest=True))
     ctx.close()
 
 
