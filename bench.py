@@ -642,7 +642,7 @@ def run_batched(args, ctx, dA, dB, rlk, rks, P, scale):
             "graph": True, "kernels_per_batch": info["launches"],
             "kernels_plain": n * 22, "scratch_gib": round(info["scratch_bytes"] / 2**30, 2),
             "autotune": {"seconds": round(t_tune, 1), "group_limbs": info["group_limbs"], "groups": info["groups"],
-                         "tensor_split": info["tensor_split"],
+                         "tensor_split": info["tensor_split"], "prime_order": info["prime_order"],
                          "one_group_per_stage": {"scratch_gib": round(info0["scratch_bytes"] / 2**30, 2),
                                                  "kernels": info0["launches"]}},
             "traced_kernels_ms": {k: round(v[1], 3) for k, v in sorted(tr.items(), key=lambda x: -x[1][1])

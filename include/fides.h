@@ -443,13 +443,17 @@ int fides_scalar_mult(fides_ctx *ctx, const fides_ct *a, const uint64_t *k, doub
  * NULL); later fides_batch_run calls launch that graph.
  * fides_batch_info reports the kernels one run launches and the device bytes
  * the batch owns.  Runs of one batch must not overlap on the GPU.
- * fides_batch_configure re-plans with a group size and tensor_split (1: the
+ * fides_batch_configure re-plans with a group size, tensor_split (1: the
  * tensor product as its own 16-byte pass where the buffers allow, 0: fused
- * into the first INTT pass); fides_batch_autotune runs the batch on `stream`
- * for each group size 0, 32, 64, ... below the largest stage's limbs and both
- * tensor placements, keeps the fastest (its time per run in *best_ms, may be
- * NULL) and shrinks the scratch to it; fides_batch_tuning reports the
- * current choice and the number of launch groups.  Configure and autotune
+ * into the first INTT pass) and prime_order (1: every NTT launch visits its
+ * limbs ordered by prime, so that the CTAs in flight share the per-prime
+ * twiddle tables in L2; 0: in plan order); fides_batch_autotune runs the
+ * batch on `stream` for each group size 0, 32, 64, ... below the largest
+ * stage's limbs and each of the four (tensor_split, prime_order) pairs, keeps
+ * the fastest (its time per run in *best_ms, may be NULL) and shrinks the
+ * scratch to it; fides_batch_tuning reports the current choice and the
+ * number of launch groups.  The inner product always visits its rows by key
+ * and key limb (the ops sharing a key read each limb while it is in L2).  Configure and autotune
  * synchronise the device, overwrite the ops' outputs (autotune runs the
  * batch) and drop a captured graph (capture again afterwards).
  */
@@ -474,9 +478,10 @@ int fides_batch_run(fides_batch *batch, void *stream);
 int fides_batch_capture(fides_batch *batch, void *stream);
 int fides_batch_info(const fides_batch *batch, int *launches, size_t *scratch_bytes, size_t *table_bytes);
 void fides_batch_destroy(fides_batch *batch);
-int fides_batch_configure(fides_batch *batch, int group_limbs, int tensor_split);
+int fides_batch_configure(fides_batch *batch, int group_limbs, int tensor_split, int prime_order);
 int fides_batch_autotune(fides_batch *batch, void *stream, double *best_ms);
-int fides_batch_tuning(const fides_batch *batch, int *group_limbs, int *tensor_split, int *groups);
+int fides_batch_tuning(const fides_batch *batch, int *group_limbs, int *tensor_split, int *prime_order,
+                       int *groups);
 
 /*
  * Request server: continuous batching of HMult+relin, HRotate and Rescale

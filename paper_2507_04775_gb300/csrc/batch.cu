@@ -16,9 +16,10 @@
 // grouped in stages: an operation of stage s may read the outputs of stages
 // < s; operations of one stage are independent.
 //
-// fides_batch_autotune times candidate group sizes and both placements of the
-// HMult tensor product (its own pass, or fused into the first INTT pass) on
-// the batch itself and keeps the fastest.
+// fides_batch_autotune times candidate group sizes, both placements of the
+// HMult tensor product (its own pass, or fused into the first INTT pass) and
+// both limb orders of the NTT launches (as planned, or by prime) on the batch
+// itself and keeps the fastest.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -32,6 +33,7 @@ struct fides_batch {
     int nstage;
     int group_limbs;             // limbs per launch group, 0: one group per stage
     int tensor_split;            // HMult tensor product as its own pass (1) or fused (0)
+    int prime_order;             // NTT launches visit their limbs by prime (1) or as planned (0)
     int groups;                  // launch groups of the current plan
     std::vector<Launch> launches;
     unsigned char *dmem;         // device tables
@@ -72,7 +74,7 @@ std::vector<std::vector<int>> batch_groups(const std::vector<fides_op> &ops, int
 // scratch pool and the table buffer when needed (shrink: also reallocates a
 // pool larger than the plan needs), uploads the tables and drops a captured
 // graph.  Synchronises the device before it frees anything.
-int batch_build(fides_batch *b, int group_limbs, int tensor_split, bool shrink = true)
+int batch_build(fides_batch *b, int group_limbs, int tensor_split, int prime_order, bool shrink = true)
 {
     const fides_ctx *c = b->ctx;
     const std::vector<std::vector<int>> gs = batch_groups(b->ops, b->nstage, group_limbs);
@@ -105,7 +107,7 @@ int batch_build(fides_batch *b, int group_limbs, int tensor_split, bool shrink =
             scr.push_back(b->scratch + off);
             off += op_scratch_words(c->N, c->K, c->alpha, b->ops[i].type, b->ops[i].a.n_limbs);
         }
-        plan_stage(c, gops.data(), (int)gops.size(), gops[0].stage, scr.data(), P, tensor_split != 0);
+        plan_stage(c, gops.data(), (int)gops.size(), gops[0].stage, scr.data(), P, tensor_split != 0, prime_order != 0);
         for (size_t k = 0; k < g.size(); ++k) b->ops[g[k]].out.scale = gops[k].out.scale;
     }
     if (P.image.size() > b->dmem_cap) {
@@ -125,6 +127,7 @@ int batch_build(fides_batch *b, int group_limbs, int tensor_split, bool shrink =
     b->scratch_bytes = b->scratch_cap * sizeof(u64);
     b->group_limbs = group_limbs;
     b->tensor_split = tensor_split;
+    b->prime_order = prime_order;
     b->groups = (int)gs.size();
     return FIDES_OK;
 }
@@ -150,7 +153,7 @@ extern "C" int fides_batch_create(fides_ctx *c, fides_op *ops, int n_ops, fides_
     b->scratch = nullptr;
     b->scratch_cap = 0;
     b->exec = nullptr;
-    if (int rc = batch_build(b, 0, 1)) {
+    if (int rc = batch_build(b, 0, 1, 0)) {
         fides_batch_destroy(b);
         return rc;
     }
@@ -210,19 +213,22 @@ extern "C" int fides_batch_info(const fides_batch *b, int *launches, size_t *scr
     return FIDES_OK;
 }
 
-extern "C" int fides_batch_configure(fides_batch *b, int group_limbs, int tensor_split)
+extern "C" int fides_batch_configure(fides_batch *b, int group_limbs, int tensor_split, int prime_order)
 {
     if (!b) return fides_set_error(FIDES_ERR_ARG, "fides_batch_configure: NULL batch");
-    if (group_limbs < 0 || (tensor_split != 0 && tensor_split != 1))
-        return fides_set_error(FIDES_ERR_ARG, "fides_batch_configure: group_limbs >= 0, tensor_split 0 or 1");
-    return batch_build(b, group_limbs, tensor_split);
+    if (group_limbs < 0 || (tensor_split != 0 && tensor_split != 1) || (prime_order != 0 && prime_order != 1))
+        return fides_set_error(FIDES_ERR_ARG,
+                               "fides_batch_configure: group_limbs >= 0, tensor_split and prime_order 0 or 1");
+    return batch_build(b, group_limbs, tensor_split, prime_order);
 }
 
-extern "C" int fides_batch_tuning(const fides_batch *b, int *group_limbs, int *tensor_split, int *groups)
+extern "C" int fides_batch_tuning(const fides_batch *b, int *group_limbs, int *tensor_split, int *prime_order,
+                                  int *groups)
 {
     if (!b) return fides_set_error(FIDES_ERR_ARG, "fides_batch_tuning: NULL batch");
     if (group_limbs) *group_limbs = b->group_limbs;
     if (tensor_split) *tensor_split = b->tensor_split;
+    if (prime_order) *prime_order = b->prime_order;
     if (groups) *groups = b->groups;
     return FIDES_OK;
 }
@@ -245,10 +251,11 @@ extern "C" int fides_batch_autotune(fides_batch *b, void *stream, double *best_m
     if (!rc) rc = fides_check_cuda(cudaEventCreate(&e1), "fides_batch_autotune: event");
     const int was = fides_trace_set(0);
     float best = 0.f;
-    int best_g = b->group_limbs, best_t = b->tensor_split;
+    int best_g = b->group_limbs, best_t = b->tensor_split, best_o = b->prime_order;
     for (size_t k = 0; !rc && k < sizes.size(); ++k) {
-        for (int ts = 1; !rc && ts >= 0; --ts) {
-            rc = batch_build(b, sizes[k], ts, false);
+        for (int cand = 0; !rc && cand < 4; ++cand) {
+            const int ts = 1 - (cand & 1), po = cand >> 1;
+            rc = batch_build(b, sizes[k], ts, po, false);
             if (!rc) rc = plan_run(b->ctx, b->launches, st);   // warm-up
             if (!rc) rc = fides_check_cuda(cudaEventRecord(e0, st), "fides_batch_autotune: event");
             for (int r = 0; !rc && r < 2; ++r) rc = plan_run(b->ctx, b->launches, st);
@@ -261,6 +268,7 @@ extern "C" int fides_batch_autotune(fides_batch *b, void *stream, double *best_m
                 best = ms;
                 best_g = sizes[k];
                 best_t = ts;
+                best_o = po;
             }
         }
     }
@@ -269,5 +277,5 @@ extern "C" int fides_batch_autotune(fides_batch *b, void *stream, double *best_m
     if (e1) cudaEventDestroy(e1);
     if (rc) return rc;
     if (best_ms) *best_ms = best;
-    return batch_build(b, best_g, best_t);
+    return batch_build(b, best_g, best_t, best_o);
 }

@@ -76,6 +76,7 @@ struct Seg {
 struct LimbSet {
     int nseg;
     int total;
+    int modes;          // OR of the segments' modes (0: every inverse prologue is the plain load)
     const Seg *dseg;
     const int *dpre;
     Seg seg[FIDES_MAX_SEG];
@@ -252,6 +253,7 @@ __device__ __forceinline__ Job job_of(const Seg &g, int z, int N)
 
 __device__ __forceinline__ Job get_job(const LimbSet &S, int z, int N)
 {
+    if (S.dseg && S.nseg == S.total) return job_of(S.dseg[z], 0, N);   // one limb per segment
     if (S.dseg) {
         int lo = 0, hi = S.nseg - 1;
         while (lo < hi) {

@@ -297,10 +297,13 @@ struct IPOp {
 };
 
 // One op inline (dop == nullptr; grid.y = its ne limbs) or a device table of
-// ops with exclusive prefix sums of their ne (grid.y = the total).
+// ops with a row table: row r (grid.y) computes limb drow[r] & 127 of op
+// drow[r] >> 7 (an op has at most FIDES_MAX_PRIMES limbs).  The batched path orders the rows by key and key limb, so
+// that the ops sharing a key (every HMult of a batch shares the
+// relinearisation key) read each key limb while it is in L2.
 struct IPArgs {
     const IPOp *dop;
-    const int *dpre;
+    const int *drow;
     int nop;
     IPOp one;
 };
@@ -421,8 +424,8 @@ __global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const
     pdl_trigger();   // inner_body waits after issuing its key loads
     const int z = blockIdx.y;
     if (A.dop) {
-        const int k = find_op(A.dpre, A.nop, z);
-        inner_body<MAXB, V2>(A.dop[k], z - __ldg(A.dpre + k), L, nfull, P, logN);
+        const int r = __ldg(A.drow + z);
+        inner_body<MAXB, V2>(A.dop[r >> 7], r & 127, L, nfull, P, logN);
     } else {
         inner_body<MAXB, V2>(A.one, z, L, nfull, P, logN);
     }
@@ -542,11 +545,27 @@ inline Seg seg_of(const u64 *src, u64 *dst, int count, int prime0, const u64 *au
     return s;
 }
 
+// limb k of a segment as a segment of its own (the pointers job_of would
+// compute for it, ring degree N)
+inline Seg limb_of(const Seg &g, int k, size_t N)
+{
+    Seg s = g;
+    s.src = g.src + (size_t)k * g.src_step * N;
+    s.dst = g.dst ? g.dst + (size_t)k * N : nullptr;
+    s.aux = g.aux ? g.aux + (size_t)k * N : nullptr;
+    s.out = g.out ? g.out + (size_t)k * N : nullptr;
+    s.side = g.side ? g.side + (size_t)k * N : nullptr;
+    s.prime0 = g.prime0 + k;
+    s.count = 1;
+    return s;
+}
+
 inline void add_seg(LimbSet &S, const Seg &g)
 {
     if (g.count <= 0) return;
     S.seg[S.nseg++] = g;
     S.total += g.count;
+    S.modes |= g.mode;
 }
 
 inline LimbSet empty_set()

@@ -32,7 +32,7 @@ struct Launch {
 // table image; the device addresses are patched in once the image has a home.
 struct Pending {
     int launch;
-    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.dpre, 5: tp.dop, 6: tp.dpre
+    int which;        // 0: set.dseg, 1: set.dpre, 2: bc.djob, 3: ip.dop, 4: ip.drow, 5: tp.dop, 6: tp.dpre
     size_t off;
 };
 
@@ -50,20 +50,32 @@ struct Plan {
     }
 };
 
-void plan_ntt(Plan &P, LaunchKind kind, const std::vector<Seg> &segs)
+// One launch for the segments.  prime_major: every limb becomes a segment of
+// its own and the limbs are ordered by prime, so that the CTAs in flight work
+// on few primes and their row twiddle tables stay in L2 (a table per prime
+// and direction, 16 N bytes); the kernels then index the table directly.
+void plan_ntt(Plan &P, LaunchKind kind, const std::vector<Seg> &segs, size_t N, bool prime_major = false)
 {
     if (segs.empty()) return;
+    std::vector<Seg> v;
+    if (prime_major) {
+        for (const Seg &g : segs)
+            for (int k = 0; k < g.count; ++k) v.push_back(limb_of(g, k, N));
+        std::stable_sort(v.begin(), v.end(), [](const Seg &a, const Seg &b) { return a.prime0 < b.prime0; });
+    } else {
+        v = segs;
+    }
     Launch l;
     memset(&l, 0, sizeof(l));
     l.kind = kind;
-    l.set.nseg = (int)segs.size();
-    std::vector<int> pre(segs.size());
+    l.set.nseg = (int)v.size();
+    std::vector<int> pre(v.size());
     int tot = 0;
-    for (size_t i = 0; i < segs.size(); ++i) { pre[i] = tot; tot += segs[i].count; }
+    for (size_t i = 0; i < v.size(); ++i) { pre[i] = tot; tot += v[i].count; l.set.modes |= v[i].mode; }
     l.set.total = tot;
     P.launches.push_back(l);
     const int id = (int)P.launches.size() - 1;
-    P.pend.push_back(Pending{id, 0, P.add(segs.data(), sizeof(Seg) * segs.size())});
+    P.pend.push_back(Pending{id, 0, P.add(v.data(), sizeof(Seg) * v.size())});
     P.pend.push_back(Pending{id, 1, P.add(pre.data(), sizeof(int) * pre.size())});
 }
 
@@ -104,10 +116,20 @@ void plan_inner(Plan &P, const std::vector<IPOp> &ops, const std::vector<int> &r
     Launch l;
     memset(&l, 0, sizeof(l));
     l.kind = L_INNER;
-    std::vector<int> pre(ops.size());
-    int tot = 0;
-    for (size_t i = 0; i < ops.size(); ++i) { pre[i] = tot; tot += rows[i]; }
-    l.total = tot;
+    // rows (op, limb) ordered by key, then by the key limb the row reads,
+    // then by op: the ops sharing a key read each of its limbs back to back
+    struct Row { const u64 *evk; int pz, op, z; };
+    std::vector<Row> order;
+    for (size_t i = 0; i < ops.size(); ++i)
+        for (int z = 0; z < rows[i]; ++z)
+            order.push_back(Row{ops[i].evk, z < ops[i].nl ? z : 1024 + (z - ops[i].nl), (int)i, z});
+    std::stable_sort(order.begin(), order.end(), [](const Row &a, const Row &b) {
+        if (a.evk != b.evk) return a.evk < b.evk;
+        return a.pz < b.pz;
+    });
+    std::vector<int> rowtab(order.size());
+    for (size_t r = 0; r < order.size(); ++r) rowtab[r] = (order[r].op << 7) | order[r].z;
+    l.total = (int)order.size();
     l.ip.nop = (int)ops.size();
     l.ip_pairs = 1;
     for (const IPOp &o : ops) {
@@ -117,7 +139,7 @@ void plan_inner(Plan &P, const std::vector<IPOp> &ops, const std::vector<int> &r
     P.launches.push_back(l);
     const int id = (int)P.launches.size() - 1;
     P.pend.push_back(Pending{id, 3, P.add(ops.data(), sizeof(IPOp) * ops.size())});
-    P.pend.push_back(Pending{id, 4, P.add(pre.data(), sizeof(int) * pre.size())});
+    P.pend.push_back(Pending{id, 4, P.add(rowtab.data(), sizeof(int) * rowtab.size())});
 }
 
 void plan_tensor(Plan &P, const std::vector<TensorOp> &ops)
@@ -182,7 +204,7 @@ inline size_t op_scratch_words(int N, int K, int alpha, int type, int nl)
 // the buffers allow) instead of fused into the first INTT pass; a fusion
 // boundary the batch autotuner chooses.
 void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *const *scratch, Plan &P,
-                bool tensor_split = true)
+                bool tensor_split = true, bool prime_major = false)
 {
     const size_t N = c->N;
     std::vector<Seg> intt, ntt, pinv, fin, rsfin;
@@ -230,14 +252,14 @@ void plan_stage(const fides_ctx *c, fides_op *ops, int n_ops, int stage, u64 *co
         o.out.scale = hm ? o.a.scale * o.b.scale : o.a.scale;
     }
     plan_tensor(P, tens);
-    plan_ntt(P, L_INTT, intt);
+    plan_ntt(P, L_INTT, intt, N, prime_major);
     plan_bconv(P, up);
-    plan_ntt(P, L_NTT, ntt);
+    plan_ntt(P, L_NTT, ntt, N, prime_major);
     plan_inner(P, ip, ip_rows);
-    plan_ntt(P, L_INTT, pinv);
+    plan_ntt(P, L_INTT, pinv, N, prime_major);
     plan_bconv(P, down);
-    plan_ntt(P, L_NTT_SUBMUL, fin);
-    plan_ntt(P, L_NTT_SWITCH_SUBMUL, rsfin);
+    plan_ntt(P, L_NTT_SUBMUL, fin, N, prime_major);
+    plan_ntt(P, L_NTT_SWITCH_SUBMUL, rsfin, N, prime_major);
 }
 
 // Points every launch at the device copy of the table image.
@@ -251,7 +273,7 @@ void plan_patch(Plan &P, unsigned char *dmem)
         case 1: l.set.dpre = (const int *)a; break;
         case 2: l.bc.djob = (const BConvJob *)a; break;
         case 3: l.ip.dop = (const IPOp *)a; break;
-        case 4: l.ip.dpre = (const int *)a; break;
+        case 4: l.ip.drow = (const int *)a; break;
         case 5: l.tp.dop = (const TensorOp *)a; break;
         case 6: l.tp.dpre = (const int *)a; break;
         }

@@ -182,6 +182,13 @@ struct ProPrep {
     }
 };
 
+// The plain inverse-NTT input (every segment of mode 0): the row pass issues
+// all sixteen of a thread's loads before it stores any of them to shared
+// memory, through the read-only path.
+struct ProPlain {
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return __ldg(J.src + j); }
+};
+
 // ---- epilogue functors ----
 // Each epilogue has a load step (the global reads it needs for element j) and
 // a store step, so that the kernel can issue the loads of several elements
@@ -400,6 +407,24 @@ __global__ void __launch_bounds__(ntt_threads<S, KIND, CT>(), MINB)
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = pro(J, gidx(cbase, kmap(u, r, b0)), pr);
         if (TWS) __syncthreads();
+    } else if constexpr (std::is_same<Pro, ProPlain>::value) {
+        // all sixteen loads in flight before the first shared-memory store
+        u64 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = t + THREADS * i;
+            const int cc = e >> S, k = e & ((1 << S) - 1);
+            const int cb = (KIND == 2) ? 0 : (int)blockIdx.x * C + cc;
+            v[i] = pro(J, gidx(cb, k), pr);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = t + THREADS * i;
+            sm[widx(e >> S, e & ((1 << S) - 1))] = v[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = sm[widx(c, kmap(u, r, 0))];
     } else if constexpr (std::is_same<Pro, ProPrep>::value) {
         // four elements' loads in flight before any of them is computed
 #pragma unroll
@@ -519,7 +544,7 @@ int ntt_fwd_switch_submul(const fides_ctx *c, const LimbSet &set, cudaStream_t s
 int ntt_fwd_submul_rot(const fides_ctx *c, const LimbSet &set, cudaStream_t st);      // ProSrc, EpiSubMulRot
 int ntt_fwd_raise(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProRaise, EpiCanon
 int ntt_fwd_hmrs(const fides_ctx *c, const LimbSet &set, cudaStream_t st);            // ProHmRs, EpiHmRs
-int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep, EpiCanon
+int ntt_inv_canon(const fides_ctx *c, const LimbSet &set, cudaStream_t st);           // ProPrep (ProPlain), EpiCanon
 
 inline int ntt_forward(const fides_ctx *c, const LimbSet &s, ProSrc, EpiCanon, cudaStream_t st)
 {

@@ -119,7 +119,7 @@ void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStr
         launch_pass_v<LOGN, 1, false, false>(v, c, set, c->d_tw, ProDst{}, EpiCanon{}, st, "k_ntt_tune");
         break;
     case INV_ROWS:
-        launch_pass_v<LOGN, 1, true, false>(v, c, set, c->d_itw, ProPrep{LOGN}, EpiLazy{}, st, "k_ntt_tune");
+        launch_pass_v<LOGN, 1, true, false>(v, c, set, c->d_itw, ProPlain{}, EpiLazy{}, st, "k_ntt_tune");
         break;
     default:
         launch_pass_v<LOGN, 0, true, true>(v, c, set, c->d_itw, ProDst{}, EpiCanon{}, st, "k_ntt_tune");
@@ -167,6 +167,7 @@ void launch_one(const fides_ctx *c, int kind, int v, const LimbSet &set, cudaStr
     }                                                                                                             \
     int ntt_inv_canon_##L(const fides_ctx *c, const LimbSet &s, cudaStream_t st)                                \
     {                                                                                                             \
+        if (s.modes == 0) return inverse<L>(c, s, ProPlain{}, EpiCanon{}, st);                                    \
         return inverse<L>(c, s, ProPrep{c->logN}, EpiCanon{}, st);                                                \
     }                                                                                                             \
     void ntt_tune_one_##L(const fides_ctx *c, int kind, int v, const LimbSet &s, cudaStream_t st)               \

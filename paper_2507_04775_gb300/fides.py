@@ -174,9 +174,10 @@ def lib():
                                        ctypes.POINTER(ctypes.c_size_t)]
         L.fides_batch_destroy.argtypes = [_vp]
         L.fides_batch_destroy.restype = None
-        L.fides_batch_configure.argtypes = [_vp, _i, _i]
+        L.fides_batch_configure.argtypes = [_vp, _i, _i, _i]
         L.fides_batch_autotune.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
-        L.fides_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]
+        L.fides_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                         ctypes.POINTER(_i)]
         L.fides_measure_modmul_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.fides_server_create.argtypes = [_vp, ctypes.POINTER(fides_server_config), ctypes.POINTER(_vp)]
         L.fides_server_destroy.argtypes = [_vp]
@@ -647,15 +648,15 @@ class Batch:
     def info(self) -> dict:
         n, sb, tb = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
         _check(lib().fides_batch_info(self._h, ctypes.byref(n), ctypes.byref(sb), ctypes.byref(tb)))
-        g, t, ng = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
-        _check(lib().fides_batch_tuning(self._h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(ng)))
+        g, t, po, ng = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().fides_batch_tuning(self._h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(po), ctypes.byref(ng)))
         return {"launches": n.value, "scratch_bytes": sb.value, "table_bytes": tb.value, "group_limbs": g.value,
-                "tensor_split": t.value, "groups": ng.value}
+                "tensor_split": t.value, "prime_order": po.value, "groups": ng.value}
 
-    def configure(self, group_limbs: int, tensor_split: int = 1):
-        """Launch groups of at most group_limbs limbs (0: one per stage) and the
-        tensor-product placement (fides_batch_configure)."""
-        _check(lib().fides_batch_configure(self._h, group_limbs, tensor_split))
+    def configure(self, group_limbs: int, tensor_split: int = 1, prime_order: int = 0):
+        """Launch groups of at most group_limbs limbs (0: one per stage), the
+        tensor-product placement and the NTT limb order (fides_batch_configure)."""
+        _check(lib().fides_batch_configure(self._h, group_limbs, tensor_split, prime_order))
 
     def autotune(self, stream=None) -> float:
         """Times the candidate groupings and tensor placements on this batch and

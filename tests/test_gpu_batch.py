@@ -120,8 +120,8 @@ def test_batch_matches_single_op_and_oracle(P, levels):
     g.close()
 
 
-@pytest.mark.parametrize("group_limbs,tensor_split", [(1, 1), (8, 0), (20, 1), (0, 0)])
-def test_batch_launch_groups_and_tensor_placement(group_limbs, tensor_split):
+@pytest.mark.parametrize("group_limbs,tensor_split,prime_order", [(1, 1, 0), (8, 0, 1), (20, 1, 1), (0, 0, 0)])
+def test_batch_launch_groups_and_tensor_placement(group_limbs, tensor_split, prime_order):
     """The same batch planned as launch groups of at most group_limbs limbs
     (one op per group at 1; several groups per stage sharing one scratch pool)
     and with the tensor product fused or as its own pass: residues equal the
@@ -132,9 +132,10 @@ def test_batch_launch_groups_and_tensor_placement(group_limbs, tensor_split):
     g, o, rlk, rk, drlk, drk, host, ops = build_case(P, [12, 5, 1, 9, 4, 12], 503)
     batch = Batch(g, ops)
     whole = batch.info()
-    batch.configure(group_limbs, tensor_split)
+    batch.configure(group_limbs, tensor_split, prime_order)
     info = batch.info()
     assert info["group_limbs"] == group_limbs and info["tensor_split"] == tensor_split
+    assert info["prime_order"] == prime_order
     if group_limbs:
         assert info["groups"] > whole["groups"] and info["scratch_bytes"] < whole["scratch_bytes"]
     for op in ops:
@@ -164,7 +165,7 @@ def test_batch_in_round_to_nearest_mode():
     g.set_rounding(True)
     o.set_rounding(True)
     batch = Batch(g, ops)
-    batch.configure(16, 1)
+    batch.configure(16, 1, 1)
     batch.run()
     torch.cuda.synchronize()
     ref = single_op_reference(g, host, drlk, drk)
