@@ -268,7 +268,7 @@ def bconv_tc_flops(nl, K, alpha, N):
     for j in range(beta):
         ns = min(alpha, nl - j * alpha)
         per_ks += 2 * N * 8 * (ne - ns) * 8 * ((ns + 2) & ~1)
-    per_ks += 2 * (2 * N * 8 * nl * 8 * ((K + 2) & ~1))
+    per_ks += 2 * (2 * N * 8 * nl * 8 * ((K + 3) & ~1))   # ModDown images carry the correction column
     return 2 * per_ks
 
 

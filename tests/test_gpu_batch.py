@@ -226,6 +226,7 @@ def test_batch_graph_capture_full_size():
     for op in ops:
         op.out.zero_()
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())   # the zeroing above runs on the current stream
     with torch.cuda.stream(s):
         batch.capture(s)
         batch.run(s)
