@@ -15,46 +15,52 @@
 // 2^80 and reduces it to [0, 4p_t), the range the forward NTT that follows
 // takes; after that NTT the residues equal the integer kernel's.
 //
-// Persistent CTAs of 512 threads, each on one job with the job's matrix image
-// resident in shared memory (one bulk TMA copy, completing on an mbarrier) and
-// one accumulator of 8 nd columns in tensor memory; the CTAs of a job take its
-// tiles of 128 coefficients (M = 128) round robin.  Per tile:
-//   1. every thread writes the bytes of its prefetched source words (row m,
-//      sources s0, s0 + 4, ...), as fp16, into the A operand;
-//   2. thread 0 issues nsp/2 MMAs (K = 16: two columns of sources each) per
-//      32 targets (N = 8 targets <= 256 per instruction) and commits them to
-//      an mbarrier;
-//   3. every thread issues the loads of its words of the next tile; thread 0
-//      polls the mbarrier while the others wait at the CTA barrier; then
-//      warp w reads accumulator lanes 32 (w mod 4) .. +31 (tcgen05.ld) for a
-//      quarter of the targets, reduces and stores (coalesced 256-byte rows).
-//      Two CTAs per SM overlap one's MMAs with the other's epilogue.
+// One CTA per SM on one job, with the job's matrix image resident in shared
+// memory (one bulk copy, completing on an mbarrier); the CTAs of a job take
+// its tiles of 128 coefficients (M = 128) round robin.  Inside a CTA, warps
+// have roles that hand tiles over through mbarriers (see bconv_tc_body): a
+// loader brings each tile's source rows in with bulk copies, ahead of use;
+// producers write their bytes as fp16 into the A operand (two buffers); one
+// thread issues nsp/2 MMAs (K = 16: two columns of sources each) per 32
+// targets (N = 8 targets <= 256 per instruction) into one of two
+// accumulators in tensor memory; and twelve epilogue warps read the
+// accumulator (tcgen05.ld), reduce and store coalesced 256-byte rows, while
+// the next tile's MMAs run.
 // Operand layout (K-major, no swizzle): 8-row x 16-byte core matrices, row r
 // of a core matrix at +16 r; core matrices adjacent along K (one source: its
 // eight bytes) 128 bytes apart (leading byte offset), adjacent 8-row groups
-// 128 nsp bytes apart (stride byte offset); nsp = ns + 1 rounded up to even:
-// after the sources, an offset column (A = 256, B = 2^15 for every output byte,
+// 128 nsp bytes apart (stride byte offset); nsp = ns + 2 (+ 1 with the
+// correction column) rounded down to even: after the sources, an offset column (A = 256, B = 2^15 for every output byte,
 // both exact) starts every accumulator at 2^23, so that its fp32 bits read
 // 0x4B000000 + D with no conversion.
 //
 // Centred conversion (round-to-nearest ModDown): the sources in the upper half
 // of their range stand for x - q, which adds c (-Q_src) to every target, c
 // their count.  ModDown images carry a correction block after the offset
-// column (byte b of -Q_src mod p_t in elements 0..3 of row b); each of the
-// four threads of a row puts the count among its own sources (0..4) into
-// element s0 of that column of A, so the MMA adds c (-Q_src) byte by byte.
+// column (byte b of -Q_src mod p_t in elements 0..3 of row b); the producer
+// thread of a row puts the count c (0..16) into element 0 of that column of A
+// (elements 1..3 stay zero), so the MMA adds c (-Q_src) byte by byte.
 // It adds at most 16 x 255 to a sum, which keeps every sum below 2^23 for up
 // to 16 sources (8 x 16 x 255^2 + 4080 < 2^23).  Floor jobs put zeros there.
 //
-// Every wait is bounded (about 2 s of %globaltimer): on a timeout the CTA sets
-// FIDES_STATUS_WAIT_TIMEOUT in the context's status word, skips its outputs,
-// frees its tensor memory and returns.
+// Every wait is bounded (about 2 s of %globaltimer): on a timeout the role
+// sets FIDES_STATUS_WAIT_TIMEOUT in the context's status word and a CTA-wide
+// abort flag, every role leaves its loop (skipping the outputs it has not
+// written), the loader and the MMA thread wait (again bounded) for their
+// copies and products in flight, and the CTA frees its tensor memory and
+// returns.
 #pragma once
 
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 512;
+constexpr int TC_PROD_WARPS = 4;                                   // warps 0-3: A rows
+constexpr int TC_LOAD_WARP = 4;                                    // bulk copies of the sources
+constexpr int TC_MMA_WARP = 5;                                     // MMA issue
+constexpr int TC_EPI_WARP0 = 6;                                    // warps 6..: epilogue
+constexpr int TC_EPI_GROUPS = 3;                                   // of four warps each
+constexpr int TC_THREADS = 32 * (TC_EPI_WARP0 + 4 * TC_EPI_GROUPS);   // 576
+constexpr int TC_MAX_DEPTH = 4;                                    // source stages
 
 __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -254,22 +260,78 @@ __device__ __forceinline__ u64 tc_reduce(const u32 *r, const TcTarget &T, const 
     }
 }
 
-// One CTA: the job's matrix image resident in shared memory and one
-// accumulator in tensor memory; tiles blockIdx.x, + gridDim.x, ... of the
-// job's N / 128.  Per tile: the source words prefetched during the previous
-// tile are written as bf16 bytes into the A operand; thread 0 issues the MMAs;
-// every thread issues the loads of the next tile's words, waits for the MMAs,
-// then reduces and stores its share of the accumulator.
+// Shape of a launch's pipeline (the same for all its CTAs).
+struct TcPipe {
+    int depth;      // source stages: tiles whose bulk copies may be in flight
+    int na;         // A operand buffers
+    int nbuf;       // accumulators in tensor memory
+    u32 acc_cols;   // tensor-memory columns of one accumulator (a power of two)
+    u32 ncols;      // columns allocated: nbuf x acc_cols
+};
+
+// mbarriers of a CTA: source stage full / empty, A buffer full / empty,
+// accumulator full / empty, matrix image
+constexpr int TB_SF = 0, TB_SE = TC_MAX_DEPTH, TB_AF = 2 * TC_MAX_DEPTH, TB_AE = TB_AF + 2, TB_CF = TB_AE + 2,
+              TB_CE = TB_CF + 2, TB_IMG = TB_CE + 2, TB_COUNT = TB_IMG + 1;
+
+__device__ __forceinline__ void mbar_arrive(u32 bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// bulk copy global -> shared completing on an mbarrier whose transaction
+// count the caller has already raised
+__device__ __forceinline__ void bulk_copy(u32 dst, const void *src, u32 bytes, u32 bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// A pipeline wait: true once the phase of `parity` has completed.  False when
+// another role has given up (abort set), or after about 2 s of %globaltimer,
+// which sets abort and the status bit, so that every role leaves its loop.
+__device__ __forceinline__ bool pipe_wait(u32 bar, u32 parity, volatile int *abort, int *status)
+{
+    if (mbar_test(bar, parity)) return true;
+    const u64 t0 = global_ns();
+    for (u32 it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort) return false;
+            if (global_ns() - t0 > 2000000000ull || it >= (1u << 26)) {
+                *abort = 1;
+                atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// One CTA on one job, over tiles blockIdx.x, + gridDim.x, ... of its N / 128.
+// Four roles run at their own pace, handing tiles over through mbarriers:
+//   warp 4, one thread:   bulk copies of a tile's ns source rows (1 KB each)
+//                         into a ring of `depth` stages;
+//   warps 0-3:            thread m writes the bytes of row m of every source
+//                         as fp16 into one of `na` A buffers;
+//   warp 5, one thread:   the MMAs of a tile into one of `nbuf` accumulators;
+//   warps 6-17:           tcgen05.ld of the accumulator (warp w reads lanes
+//                         32 (w mod 4) ..), reduction and coalesced stores,
+//                         three groups of four warps splitting the targets.
+// So a tile's epilogue overlaps the next tile's MMAs and the bulk copies of
+// the tiles after it.
 template <bool BIG>
 __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo *__restrict__ P,
-                                              const TwPair *__restrict__ c32, int logN, u32 ncols, int *status)
+                                              const TwPair *__restrict__ c32, int logN, const TcPipe &pp,
+                                              int *status)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) u64 bar[2];
+    __shared__ __align__(8) u64 bars[TB_COUNT];
     __shared__ u32 tslot;
-    __shared__ int sok;
+    __shared__ volatile int sabort;
     __shared__ TcTarget stg[FIDES_MAX_PRIMES];
     __shared__ PrimeInfo sp[BIG ? 1 : FIDES_MAX_PRIMES];
+    __shared__ u64 shalf[FIDES_TC_MAX_SRC];
 
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int N = 1 << logN, ntiles = N / TC_M;
@@ -277,13 +339,27 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     int nd = 0;
     for (int r = 0; r < B.nrun; ++r) nd += B.run[r].count;
     const int ndp = (nd + 1) & ~1;
-    unsigned char *sA = tsm;
-    unsigned char *sB = tsm + 2048 * nsp;
-    const u32 bar0 = smem_addr(&bar[0]), bar1 = smem_addr(&bar[1]);
+    const int T = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const u32 szA = 2048u * nsp, szS = 1024u * ns;
+    unsigned char *sB = tsm;
+    unsigned char *sA = tsm + (size_t)ndp * nsp * 128;
+    unsigned char *sS = sA + (size_t)pp.na * szA;
+    const u32 bar0 = smem_addr(&bars[0]);
+    auto bar = [&](int i) -> u32 { return bar0 + 8u * i; };
 
     if (t == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+        for (int d = 0; d < pp.depth; ++d) {
+            mbar_init(bar(TB_SF + d), 1);
+            mbar_init(bar(TB_SE + d), TC_PROD_WARPS);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(TB_AF + i), TC_PROD_WARPS);
+            mbar_init(bar(TB_AE + i), 1);
+            mbar_init(bar(TB_CF + i), 1);
+            mbar_init(bar(TB_CE + i), 4 * TC_EPI_GROUPS);
+        }
+        mbar_init(bar(TB_IMG), 1);
+        sabort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (t < nd) {
@@ -301,139 +377,155 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
         stg[t] = TcTarget{ptr, P[pz].q, cw.wp, cw.w};
         if (!BIG) sp[t] = P[pz];
     }
-    __syncthreads();
-    if (t == 0) bulk_load(smem_addr(sB), B.tc, (u32)ndp * nsp * 128, bar0);
-    // everything above reads only the job and the context's tables; the
-    // sources below are the previous kernel's output, and no tensor memory is
-    // taken before it has finished (an early-launched conversion must not
-    // hold it while this one waits)
-    pdl_wait();
-    __syncwarp();
-    if (w == 0) tmem_alloc(smem_addr(&tslot), ncols);
-
-    // this thread's A rows and sources: row m, sources s0, s0 + 4, ...
-    constexpr int SPT = FIDES_TC_MAX_SRC / (TC_THREADS / TC_M);
-    const int m = t & (TC_M - 1), s0 = t / TC_M;
-    unsigned char *arow = sA + (m >> 3) * (nsp * 128) + (m & 7) * 16;
-    u64 xr[SPT];
-    u64 half[SPT];   // (q_s - 1) / 2 of this thread's sources (centred jobs)
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-        const int s = s0 + k * (TC_THREADS / TC_M);
-        half[k] = (B.centred && s < ns) ? (P[B.src_prime0 + s].q >> 1) : ~0ull;
-    }
-    int tile = blockIdx.x;
-    if (tile < ntiles) {
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int s = s0 + k * (TC_THREADS / TC_M);
-            xr[k] = s < ns ? B.src[(size_t)s * N + (size_t)tile * TC_M + m] : 0;
+    // (q_s - 1) / 2 of the sources (centred jobs; ~0: never above)
+    if (t < ns) shalf[t] = B.centred ? (P[B.src_prime0 + t].q >> 1) : ~0ull;
+    // constant columns of every A buffer: the offset column (fp16 256 in
+    // element 0 of row m; the image holds 2^15 there for every output byte),
+    // the correction column (element 0 takes the row's count in centred
+    // jobs) and padding
+    if (t < TC_M) {
+        for (int b = 0; b < pp.na; ++b) {
+            unsigned char *arow = sA + b * szA + (t >> 3) * (nsp * 128) + (t & 7) * 16;
+            *(uint4 *)(arow + ns * 128) = make_uint4(0x5C00u, 0, 0, 0);
+            for (int col = ns + 1; col < nsp; ++col) *(uint4 *)(arow + col * 128) = make_uint4(0, 0, 0, 0);
         }
     }
-    // constant columns of A: the offset column (fp16 256 in element 0 of row
-    // m; the image holds 2^15 there for every output byte) and a zero column
-    if (t < TC_M) {
-        *(uint4 *)(arow + ns * 128) = make_uint4(0x5C00u, 0, 0, 0);
-        for (int col = ns + 1; col < nsp; ++col) *(uint4 *)(arow + col * 128) = make_uint4(0, 0, 0, 0);
-    }
-    // one thread polls each mbarrier; the others wait at the CTA barrier
-    if (t == 0) {
-        sok = mbar_wait(bar0, 0);
-        if (!sok) {
-            atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
-            mbar_wait(bar0, 0);   // the copy may still be in flight
+    __syncthreads();
+    if (t == 0) bulk_load(smem_addr(sB), B.tc, (u32)ndp * nsp * 128, bar(TB_IMG));
+    // everything above reads only the job and the context's tables; the
+    // sources are the previous kernel's output, and no tensor memory is taken
+    // before it has finished (an early-launched conversion must not hold it
+    // while this one waits)
+    pdl_wait();
+    __syncwarp();
+    if (w == 0) tmem_alloc(smem_addr(&tslot), pp.ncols);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the constant columns, for the MMAs
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tm = tslot;
+
+    if (w < TC_PROD_WARPS) {
+        const int m = t;
+        unsigned char *arow0 = sA + (m >> 3) * (nsp * 128) + (m & 7) * 16;
+        for (int k = 0; k < T; ++k) {
+            const int ss = k % pp.depth, sa = k % pp.na;
+            if (!pipe_wait(bar(TB_SF + ss), (u32)(k / pp.depth) & 1, &sabort, status)) break;
+            if (k >= pp.na && !pipe_wait(bar(TB_AE + sa), (u32)(k / pp.na - 1) & 1, &sabort, status)) break;
+            const u64 *src = (const u64 *)(sS + ss * szS) + m;
+            unsigned char *arow = arow0 + sa * szA;
+            u32 cnt = 0;
+#pragma unroll 4
+            for (int s = 0; s < ns; ++s) {
+                const u64 x = src[s * TC_M];
+                *(uint4 *)(arow + s * 128) = bytes_f16(x);
+                cnt += x > shalf[s] ? 1u : 0u;
+            }
+            if (B.centred) {
+                unsigned short h;   // fp16 of the count, 0..16 (exact)
+                asm("cvt.rn.f16.u32 %0, %1;" : "=h"(h) : "r"(cnt));
+                *(unsigned short *)(arow + (ns + 1) * 128) = h;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(bar(TB_AF + sa));
+                mbar_arrive(bar(TB_SE + ss));
+            }
+        }
+    } else if (w == TC_LOAD_WARP) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < T; ++k) {
+                const int ss = k % pp.depth;
+                if (k >= pp.depth && !pipe_wait(bar(TB_SE + ss), (u32)(k / pp.depth - 1) & 1, &sabort, status))
+                    break;
+                const size_t tile = (size_t)blockIdx.x + (size_t)k * gridDim.x;
+                const u32 dst = smem_addr(sS + ss * szS);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(TB_SF + ss)),
+                             "r"(szS)
+                             : "memory");
+                for (int s = 0; s < ns; ++s)
+                    bulk_copy(dst + 1024u * s, B.src + (size_t)s * N + tile * TC_M, 1024u, bar(TB_SF + ss));
+                issued = k + 1;
+            }
+            // copies still in flight land before the CTA leaves
+            for (int ss = 0; ss < pp.depth && ss < issued; ++ss) {
+                const int last = ss + ((issued - 1 - ss) / pp.depth) * pp.depth;
+                mbar_wait(bar(TB_SF + ss), (u32)(last / pp.depth) & 1);
+            }
+        }
+    } else if (w == TC_MMA_WARP) {
+        if (lane == 0) {
+            int issued = 0;
+            const bool img = pipe_wait(bar(TB_IMG), 0, &sabort, status);
+            const u32 a0 = smem_addr(sA), b0 = smem_addr(sB), sbo = (u32)nsp * 128;
+            for (int k = 0; img && k < T; ++k) {
+                const int sa = k % pp.na, sb = k % pp.nbuf;
+                if (!pipe_wait(bar(TB_AF + sa), (u32)(k / pp.na) & 1, &sabort, status)) break;
+                if (k >= pp.nbuf && !pipe_wait(bar(TB_CE + sb), (u32)(k / pp.nbuf - 1) & 1, &sabort, status))
+                    break;
+                tc_fence_after();
+                const u32 acc = tm + sb * pp.acc_cols, ab = a0 + sa * szA;
+                for (int s = 0; s < nsp / 2; ++s)
+                    for (int c = 0; 32 * c < ndp; ++c)
+                        tc_mma(acc + 256 * c, tc_desc(ab + 256 * s, 128, sbo),
+                               tc_desc(b0 + c * 32 * sbo + 256 * s, 128, sbo), tc_idesc(8 * min(32, ndp - 32 * c)),
+                               s > 0);
+                tc_commit(bar(TB_AE + sa));
+                tc_commit(bar(TB_CF + sb));
+                issued = k + 1;
+            }
+            // the image copy and the issued products finish before the
+            // tensor memory is freed and the CTA leaves
+            mbar_wait(bar(TB_IMG), 0);
+            if (issued > 0) mbar_wait(bar(TB_CF + (issued - 1) % pp.nbuf), (u32)((issued - 1) / pp.nbuf) & 1);
+        }
+    } else {
+        const int grp = (w - TC_EPI_WARP0) >> 2, q4 = w & 3;
+        const u32 lanes = (u32)(32 * q4) << 16;
+        for (int k = 0; k < T; ++k) {
+            const int sb = k % pp.nbuf;
+            if (!pipe_wait(bar(TB_CF + sb), (u32)(k / pp.nbuf) & 1, &sabort, status)) break;
+            tc_fence_after();
+            const size_t n = ((size_t)blockIdx.x + (size_t)k * gridDim.x) * TC_M + 32 * q4 + lane;
+            const u32 acc = tm + sb * pp.acc_cols + lanes;
+            for (int pr = grp; 2 * pr < nd; pr += TC_EPI_GROUPS) {
+                u32 r[16];
+                tc_ld16(acc + 16 * pr, r);
+                const int t0 = 2 * pr;
+                const TcTarget T0 = stg[t0];
+                T0.dst[n] = tc_reduce<BIG>(r, T0, sp[BIG ? 0 : t0]);
+                if (t0 + 1 < nd) {
+                    const TcTarget T1 = stg[t0 + 1];
+                    T1.dst[n] = tc_reduce<BIG>(r + 8, T1, sp[BIG ? 0 : t0 + 1]);
+                }
+            }
+            tc_fence_before();   // the accumulator's reads are done before it is handed back
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(TB_CE + sb));
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    bool ok = sok != 0;
-    const u32 tm = tslot;
-
-    const u32 a0 = smem_addr(sA), b0 = smem_addr(sB), sbo = (u32)nsp * 128;
-    const int q4 = w & 3, grp = w >> 2;
-    constexpr int GROUPS = TC_THREADS / 128;
-    for (u32 phase = 0; ok && tile < ntiles; tile += gridDim.x, phase ^= 1) {
-        u32 cnt = 0;
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int s = s0 + k * (TC_THREADS / TC_M);
-            if (s < ns) *(uint4 *)(arow + s * 128) = bytes_f16(xr[k]);
-            cnt += xr[k] > half[k] ? 1u : 0u;   // half = ~0: never (floor jobs, missing sources)
-        }
-        if (B.centred) {
-            // fp16 of 0..4
-            const u32 f = cnt == 0 ? 0u : (cnt == 1 ? 0x3C00u : (cnt == 2 ? 0x4000u : (cnt == 3 ? 0x4200u : 0x4400u)));
-            *(uint16_t *)(arow + (ns + 1) * 128 + 2 * s0) = (uint16_t)f;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (t == 0) {
-            for (int s = 0; s < nsp / 2; ++s)
-                for (int c = 0; 32 * c < ndp; ++c)
-                    tc_mma(tm + 256 * c, tc_desc(a0 + 256 * s, 128, sbo),
-                           tc_desc(b0 + c * 32 * sbo + 256 * s, 128, sbo), tc_idesc(8 * min(32, ndp - 32 * c)),
-                           s > 0);
-            tc_commit(bar1);
-        }
-        const int next = tile + gridDim.x;
-        if (next < ntiles) {
-#pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const int s = s0 + k * (TC_THREADS / TC_M);
-                xr[k] = s < ns ? B.src[(size_t)s * N + (size_t)next * TC_M + m] : 0;
-            }
-        }
-        if (t == 0) {
-            sok = mbar_wait(bar1, phase);
-            if (!sok) atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        ok = sok != 0;
-        if (!ok) break;
-        const size_t n = (size_t)tile * TC_M + 32 * q4 + lane;
-        const u32 lanes = (u32)(32 * q4) << 16;
-        for (int pr = grp; 2 * pr < nd; pr += GROUPS) {   // targets 2 pr, 2 pr + 1
-            u32 r[16];
-            tc_ld16(tm + lanes + 16 * pr, r);
-            const int t0 = 2 * pr;
-            const TcTarget T0 = stg[t0];
-            T0.dst[n] = tc_reduce<BIG>(r, T0, sp[BIG ? 0 : t0]);
-            if (t0 + 1 < nd) {
-                const TcTarget T1 = stg[t0 + 1];
-                T1.dst[n] = tc_reduce<BIG>(r + 8, T1, sp[BIG ? 0 : t0 + 1]);
-            }
-        }
-        tc_fence_before();   // the next tile's MMAs follow its conversion barrier
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (w == 0) tmem_free(tm, ncols);
+    if (w == 0) tmem_free(tm, pp.ncols);
 }
 
 template <bool BIG>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_bconv_tc(BConvArgs A, const PrimeInfo *__restrict__ P,
-                                                            const TwPair *__restrict__ c32, int logN, u32 ncols,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_bconv_tc(BConvArgs A, const PrimeInfo *__restrict__ P,
+                                                            const TwPair *__restrict__ c32, int logN, TcPipe pp,
                                                             int *status)
 {
     // the dependents may launch now; the body waits for the previous kernel
     // after staging the job's constants
     pdl_trigger();
-    if (A.djob) bconv_tc_body<BIG>(A.djob[blockIdx.y], P, c32, logN, ncols, status);
-    else bconv_tc_body<BIG>(A.job[blockIdx.y], P, c32, logN, ncols, status);
+    if (A.djob) bconv_tc_body<BIG>(A.djob[blockIdx.y], P, c32, logN, pp, status);
+    else bconv_tc_body<BIG>(A.job[blockIdx.y], P, c32, logN, pp, status);
 }
 
-// One launch for the tensor-core jobs of G (any mix of source counts up to
-// FIDES_TC_MAX_SRC).  Tensor memory per CTA: 8 nd columns rounded up to a power
-// of two (at least 32); at most as many CTAs per SM as tensor memory holds (the
-// dynamic shared memory is raised so that no more fit: a CTA beyond that would
-// wait in its allocation) and two by registers.  The CTAs of a job take its
-// N / 128 tiles round robin.
-// Dynamic shared memory of one job: A operand and matrix image.
+// Dynamic shared memory of one job with one A buffer and no source stage:
+// A operand and matrix image.
 inline int bconv_tc_smem(const BConvJob &j)
 {
     int nd = 0;
@@ -442,6 +534,14 @@ inline int bconv_tc_smem(const BConvJob &j)
     return 2048 * nsp + 128 * ndp * nsp;
 }
 
+// One launch for the tensor-core jobs of G (any mix of source counts up to
+// FIDES_TC_MAX_SRC), one CTA per SM: its tensor memory holds two
+// accumulators of 8 nd columns each (rounded up to a power of two, at least
+// 32), or one when two would exceed the 512 columns, and the dynamic shared
+// memory is raised to more than half the SM's so that no second CTA of a
+// conversion shares the SM (it would wait in its allocation).  The source
+// ring is as deep as shared memory allows, up to TC_MAX_DEPTH tiles, with two
+// A buffers, else one.  The CTAs of a job take its N / 128 tiles round robin.
 template <bool BIG>
 inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st)
 {
@@ -453,22 +553,39 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
         static_smem = (int)fa.sharedSizeBytes;
         cudaFuncSetAttribute(k_bconv_tc<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - static_smem);
     }
-    (void)max_ns;
     const int ndp = (max_dst + 1) & ~1;
-    u32 ncols = 32;
-    while (ncols < (u32)(8 * ndp)) ncols <<= 1;
-    const int cap = std::min(2, (int)(512 / ncols));          // resident CTAs per SM
-    const size_t need = (size_t)G.tc_smem;
-    if (need + static_smem > 227 * 1024)
-        return fides_set_error(FIDES_ERR_UNSUPPORTED, "bconv tc: %zu bytes of shared memory", need);
-    const size_t sm_bytes = 228 * 1024, per_cta = sm_bytes / (cap + 1) + 1;   // cap + 1 CTAs must not fit
-    size_t smem = std::max(need, per_cta > (size_t)static_smem + 1024 ? per_cta - static_smem - 1024 : 0);
-    smem = (smem + 127) & ~(size_t)127;
+    TcPipe pp;
+    pp.acc_cols = 32;
+    while (pp.acc_cols < (u32)(8 * ndp)) pp.acc_cols <<= 1;
+    pp.nbuf = 2 * pp.acc_cols <= 512 ? 2 : 1;
+    pp.ncols = pp.nbuf * pp.acc_cols;
+    // a bound on every job's layout: image + one A buffer (G.tc_smem), the
+    // second A buffer and the stages at the largest source count
+    const size_t budget = 227 * 1024 - (size_t)static_smem;
+    const size_t a_max = 2048 * (size_t)((max_ns + 3) & ~1), s_max = 1024 * (size_t)max_ns;
+    size_t need = 0;
+    pp.depth = 0;
+    pp.na = 1;
+    for (int na = 2; na >= 1 && pp.depth == 0; --na)
+        for (int depth = TC_MAX_DEPTH; depth >= 1; --depth) {
+            const size_t m = (size_t)G.tc_smem + (na - 1) * a_max + depth * s_max;
+            if (m <= budget) {
+                pp.depth = depth;
+                pp.na = na;
+                need = m;
+                break;
+            }
+        }
+    if (pp.depth == 0)
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "bconv tc: %d bytes of shared memory", G.tc_smem);
+    const size_t half_sm = 228 * 1024 / 2 + 1;   // a second CTA must not fit
+    size_t smem = std::max(need, half_sm > (size_t)static_smem + 1024 ? half_sm - static_smem - 1024 + 128 : 0);
+    smem = std::min((smem + 127) & ~(size_t)127, budget);
     const int tiles = c->N / TC_M;
-    const int per_job = std::max(1, std::min(tiles, cap * c->sms / G.njob));   // one wave
+    const int per_job = std::max(1, std::min(tiles, c->sms / G.njob));   // one wave
     dim3 grid(per_job, G.njob), block(TC_THREADS);
     FIDES_LAUNCH_SMEM("k_bconv_tc", st, k_bconv_tc<BIG>, grid, block, smem, G, (const PrimeInfo *)c->d_prime,
-                      (const TwPair *)c->d_c32, c->logN, ncols, c->d_status);
+                      (const TwPair *)c->d_c32, c->logN, pp, c->d_status);
     return fides_check_cuda(cudaGetLastError(), "bconv tc launch");
 }
 

@@ -254,7 +254,12 @@ inline int bconv_targets(const BConvJob &j)
 // k_bconv_tc launch (-1); the integer kernel gets one launch per distinct
 // source count (a ragged last digit gets its own, so every launch runs fully
 // unrolled loops).
-inline int bconv_group_key(const BConvJob &j) { return j.tc ? -1 : j.n_src; }
+// (The tensor-core kernel copies its sources in with bulk copies, which need
+// 16-byte alignment; a job whose sources lack it goes to the integer kernel.)
+inline int bconv_group_key(const BConvJob &j)
+{
+    return j.tc && ((uintptr_t)j.src & 15) == 0 ? -1 : j.n_src;
+}
 
 inline int launch_bconv(const fides_ctx *c, const BConvArgs &A, cudaStream_t st)
 {
