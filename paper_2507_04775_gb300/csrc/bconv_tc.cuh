@@ -581,8 +581,21 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
     const size_t half_sm = 228 * 1024 / 2 + 1;   // a second CTA must not fit
     size_t smem = std::max(need, half_sm > (size_t)static_smem + 1024 ? half_sm - static_smem - 1024 + 128 : 0);
     smem = std::min((smem + 127) & ~(size_t)127, budget);
+    // CTAs per job: the fewest waves x (tiles per CTA + a CTA's fixed cost,
+    // about three tiles: image copy, pipeline fill); one wave when the jobs
+    // are fewer than the SMs, and with many jobs (batches) a split whose last
+    // wave is full
     const int tiles = c->N / TC_M;
-    const int per_job = std::max(1, std::min(tiles, c->sms / G.njob));   // one wave
+    int per_job = 1;
+    long best = -1;
+    for (int pj = 1; pj <= tiles; ++pj) {
+        const long waves = ((long)G.njob * pj + c->sms - 1) / c->sms;
+        const long cost = waves * ((tiles + pj - 1) / pj + 3);
+        if (best < 0 || cost < best) {
+            best = cost;
+            per_job = pj;
+        }
+    }
     dim3 grid(per_job, G.njob), block(TC_THREADS);
     FIDES_LAUNCH_SMEM("k_bconv_tc", st, k_bconv_tc<BIG>, grid, block, smem, G, (const PrimeInfo *)c->d_prime,
                       (const TwPair *)c->d_c32, c->logN, pp, c->d_status);
