@@ -410,6 +410,43 @@ def run_fides(args, world, rank, local):
                            "centred Rescale lift)",
                "value": round(ops / (ms_near / 1e3), 2), "unit": "ops/s", "ms_per_step": round(ms_near / args.steps, 4)}
 
+    # ------- the same steps with HMult+Rescale on one registered stream and
+    # HRotate on another (fides_ctx_add_stream gives each its own scratch):
+    # the two chains' launches overlap and fill each other's dependent-launch
+    # gaps (reported beside the single-stream headline) -------
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ctx.add_stream(sa)
+    ctx.add_stream(sb)
+
+    def run_two(n):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        sa.wait_event(ev)
+        sb.wait_event(ev)
+        for k in range(n):
+            i = k % POOL
+            s = ctx.hmult(dA[i], dB[i], nl, rlk, out_m, scale, scale, stream=sa)
+            ctx.rescale(out_m, nl, out_s, s, stream=sa)
+            ctx.rotate(dA[i], nl, 1 << (k % N_ROT), rks[k % N_ROT], out_r, scale, stream=sb)
+        done_b = torch.cuda.Event()
+        done_b.record(sb)
+        sa.wait_event(done_b)
+        done_a = torch.cuda.Event()
+        done_a.record(sa)
+        stream.wait_event(done_a)
+
+    run_two(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run_two(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_two = max_over_ranks(e0.elapsed_time(e1), world)
+    two_streams = {"workload": "the same steps with HMult+relin and Rescale on one stream and HRotate on another, "
+                               "both registered with the context (fides_ctx_add_stream)",
+                   "value": round(ops / (ms_two / 1e3), 2), "unit": "ops/s",
+                   "ms_per_step": round(ms_two / args.steps, 4)}
+
     # ------- the same K steps again, every launch bracketed by events -------
     # (events between launches serialise programmatic dependent launch, so
     # this pass gives per-kernel durations, not the value above)
@@ -551,6 +588,7 @@ def run_fides(args, world, rank, local):
         "e2e": e2e,
         "fused_hmult_rescale": fused,
         "round_to_nearest": nearest,
+        "two_streams": two_streams,
         "batched": batched,
         "serving": serving,
         "ops": ops_extra,

@@ -31,10 +31,11 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every compute
  *    entry point is asynchronous with respect to the host.
  *  - Calls on one context use the context's scratch memory and must not run
- *    concurrently (issue them on one stream, or create one context per stream).
- *    Programs (fides_program_run) are the exception: each run uses the scratch
- *    inside its own work buffer, so runs with different work buffers may
- *    overlap on several streams of one context.
+ *    concurrently, except on streams registered with fides_ctx_add_stream,
+ *    which have pools of their own (or create one context per stream).
+ *    Programs (fides_program_run) need no registration: each run uses the
+ *    scratch inside its own work buffer, so runs with different work buffers
+ *    may overlap on several streams of one context.
  *  - Switching keys (relinearisation, rotation, conjugation) are passed as
  *    handles from fides_key_register, which binds a caller-owned key buffer
  *    to the Galois element it switches from.  A key's contents must be final
@@ -134,6 +135,25 @@ int fides_find_primes(int logN, int bits, int count, const uint64_t *exclude, in
  */
 int fides_ctx_create(int logN, int L, int dnum, const uint64_t *primes, int K, fides_ctx **out);
 void fides_ctx_destroy(fides_ctx *ctx);
+
+/*
+ * Gives `stream` (a cudaStream_t; NULL, the legacy default stream, is
+ * allowed) its own scratch pool, the size of the context's, allocated now on
+ * the context's device.  Single-operation calls of this context on a
+ * registered stream then use that pool, so they may overlap calls on other
+ * registered streams, or on one unregistered stream, which uses the
+ * context's pool.  The paper overlaps independent work on CUDA streams
+ * (Sec. III-F1, stream handling); this is how independent operations of one
+ * context do it.  Batches, servers and programs have scratch of their own
+ * and are unaffected.
+ *   - A stream stays registered, and its pool allocated, until the context is
+ *     destroyed; registering it again does nothing and returns FIDES_OK.
+ *   - At most 16 streams per context (FIDES_ERR_ARG beyond that, or for a
+ *     NULL ctx); FIDES_ERR_CUDA if the allocation fails.
+ *   - Call it from one host thread at a time per context, before the stream's
+ *     first call; calls on other streams may run meanwhile.
+ */
+int fides_ctx_add_stream(fides_ctx *ctx, void *stream);
 
 /*
  * Autotuner of the NTT launch shape (Sec. III-F1 tunes a limb-batch parameter

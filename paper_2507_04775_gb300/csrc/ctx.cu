@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fides_internal.cuh"
@@ -168,6 +169,7 @@ extern "C" void fides_ctx_destroy(fides_ctx *c)
     cudaFree(c->d_c32);
     cudaFree(c->d_status);
     cudaFree(c->scratch);
+    for (int i = 0; i < c->n_spool; ++i) cudaFree(c->spool[i]);
     free(c);
 }
 
@@ -179,6 +181,30 @@ extern "C" int fides_ctx_status(fides_ctx *c, int *flags)
     if (!rc) rc = fides_check_cuda(cudaMemcpy(flags, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "fides_ctx_status");
     if (!rc) rc = fides_check_cuda(cudaMemset(c->d_status, 0, sizeof(int)), "fides_ctx_status");
     return rc;
+}
+
+extern "C" int fides_ctx_add_stream(fides_ctx *c, void *stream)
+{
+    if (!c) return fides_set_error(FIDES_ERR_ARG, "fides_ctx_add_stream: ctx is NULL");
+    static std::mutex reg;   // registrations of every context, one at a time
+    std::lock_guard<std::mutex> lock(reg);
+    const int n = c->n_spool;
+    for (int i = 0; i < n; ++i)
+        if (c->spool_stream[i] == stream) return FIDES_OK;
+    if (n == FIDES_MAX_STREAMS)
+        return fides_set_error(FIDES_ERR_ARG, "fides_ctx_add_stream: at most %d streams", FIDES_MAX_STREAMS);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    u64 *pool = nullptr;
+    const int rc = fides_check_cuda(cudaMalloc((void **)&pool, c->scratch_words * sizeof(u64)),
+                                    "fides_ctx_add_stream: scratch pool");
+    if (prev != c->device) cudaSetDevice(prev);
+    if (rc) return rc;
+    c->spool_stream[n] = stream;
+    c->spool[n] = pool;
+    __atomic_store_n(&c->n_spool, n + 1, __ATOMIC_RELEASE);   // scratch_for reads the entry after this
+    return FIDES_OK;
 }
 
 extern "C" int fides_ctx_set_rounding(fides_ctx *c, int mode)

@@ -27,6 +27,7 @@ typedef uint32_t u32;
 #define FIDES_MAX_PRIMES 64
 #define FIDES_MAX_SEG 24
 #define FIDES_MAX_DIGITS 8
+#define FIDES_MAX_STREAMS 16   // streams with their own scratch pool (fides_ctx_add_stream)
 #define FIDES_MAX_SRC 32
 #define FIDES_TUNE_MAX 128   // NTT tile variants are kept per limb count up to this
 #define FIDES_MAC_TERMS 32   // products one plaintext multiply-accumulate launch sums (each < 2^122)
@@ -161,11 +162,28 @@ struct fides_ctx {
     u64 *scratch;
     size_t scratch_words;
 
+    // Streams registered with fides_ctx_add_stream, each with a scratch pool
+    // of scratch_words words; n_spool is published with a release store after
+    // its entry is written, and read with an acquire load (scratch_for).
+    int n_spool;
+    void *spool_stream[FIDES_MAX_STREAMS];
+    u64 *spool[FIDES_MAX_STREAMS];
+
     // NTT tile variant per pass kind (forward columns, forward rows, inverse
     // rows, inverse columns) and limb count (ntt.cu)
     int sms;
     unsigned char ntt_var[4][FIDES_TUNE_MAX + 1];
 };
+
+// Scratch pool of a single-operation call on `stream`: the stream's own pool
+// if it was registered, else the context's.
+inline u64 *scratch_for(const fides_ctx *c, void *stream)
+{
+    const int n = __atomic_load_n(&c->n_spool, __ATOMIC_ACQUIRE);
+    for (int i = 0; i < n; ++i)
+        if (c->spool_stream[i] == stream) return c->spool[i];
+    return c->scratch;
+}
 
 // A registered switching key: the caller's buffer [dnum][2][L+K][N] and the
 // Galois element it switches from (0: relinearisation, s^2).

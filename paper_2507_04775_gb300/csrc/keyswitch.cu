@@ -13,7 +13,7 @@
 namespace {
 
 // Scratch layout of one operation (words from the caller's pool, by default
-// the context's ctx->scratch):
+// the pool of the call's stream, scratch_for):
 //   dsrc  [L]      key-switch input of HMult (d2) or HRotate (sigma(c1))
 //   key switch     coeff, ext, acc, pc, conv at the top level (ks_carve)
 //   last  [2]      Rescale: coefficient form of the dropped limb
@@ -23,10 +23,10 @@ struct Scratch {
     u64 *dsrc, *ks, *last, *dd, *lastc;
 };
 
-Scratch carve(const fides_ctx *c, u64 *ws)
+Scratch carve(const fides_ctx *c, u64 *ws, void *stream)
 {
     Scratch s;
-    s.dsrc = ws ? ws : c->scratch;
+    s.dsrc = ws ? ws : scratch_for(c, stream);
     s.ks = s.dsrc + (size_t)c->L * c->N;
     s.last = s.ks + ks_scratch_words(c, c->L);
     s.dd = s.last + 2 * (size_t)c->N;
@@ -176,7 +176,7 @@ extern "C" int fides_modup(fides_ctx *c, const uint64_t *d, int nl, uint64_t *ex
     if (int rc = check_level(c, nl, "fides_modup")) return rc;
     if (!d || !ext) return fides_set_error(FIDES_ERR_ARG, "fides_modup: NULL buffer");
     cudaStream_t st = as_stream(stream);
-    KsBuffers B = ks_buffers(c, d, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, nullptr));
+    KsBuffers B = ks_buffers(c, d, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, nullptr, stream));
     B.ext = ext;
     if (int rc = run_modup(c, B, st)) return rc;
     // the digits' own limbs are the input's limbs
@@ -197,7 +197,7 @@ extern "C" int fides_moddown(fides_ctx *c, const uint64_t *x, int nl, uint64_t *
     if (int rc = check_level(c, nl, "fides_moddown")) return rc;
     if (!x || !out) return fides_set_error(FIDES_ERR_ARG, "fides_moddown: NULL buffer");
     cudaStream_t st = as_stream(stream);
-    KsBuffers B = ks_buffers(c, nullptr, nl, nullptr, out, nullptr, 0, 0, carve(c, nullptr));
+    KsBuffers B = ks_buffers(c, nullptr, nl, nullptr, out, nullptr, 0, 0, carve(c, nullptr, stream));
     const size_t N = c->N;
     std::vector<Seg> v(1, seg_of(x + (size_t)nl * N, B.pc, c->K, c->L, nullptr, nullptr, 1, 0, c->d_md_nscale));
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
@@ -217,7 +217,8 @@ extern "C" int fides_keyswitch(fides_ctx *c, const uint64_t *d, int nl, const fi
     if (!d || !out0 || !out1) return fides_set_error(FIDES_ERR_ARG, "fides_keyswitch: NULL buffer");
     if (int rc = fides_check_key(c, evk, FIDES_GALOIS_ANY, "fides_keyswitch")) return rc;
     OpTrace op("op_keyswitch", as_stream(stream));
-    return run_keyswitch(c, ks_buffers(c, d, nl, evk->data, out0, out1, 0, 0, carve(c, nullptr)), as_stream(stream));
+    return run_keyswitch(c, ks_buffers(c, d, nl, evk->data, out0, out1, 0, 0, carve(c, nullptr, stream)),
+                         as_stream(stream));
 }
 
 extern "C" int fides_hmult(fides_ctx *c, const fides_ct *a, const fides_ct *b, const fides_key *rlk, fides_ct *out,
@@ -244,7 +245,7 @@ int fides_hmult_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, const uin
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult", st);
-    const Scratch sc = carve(c, ws);
+    const Scratch sc = carve(c, ws, stream);
     KsBuffers B = ks_buffers(c, sc.dsrc, nl, rlk, out->data, out->data + S, 1, 1, sc);
     if (tensor_pass_ok(a->data, b->data, out->data, sc.dsrc)) {
         if (int rc = launch_tensor(c, a->data, b->data, out->data, sc.dsrc, nl, st)) return rc;
@@ -290,7 +291,7 @@ int fides_hmult_rescale_ws(fides_ctx *c, const fides_ct *a, const fides_ct *b, c
     const size_t N = c->N, S = (size_t)nl * N, ne = (size_t)nl + c->K;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_hmult_rescale", st);
-    const Scratch sc = carve(c, ws);
+    const Scratch sc = carve(c, ws, stream);
     KsBuffers B = ks_buffers(c, sc.dsrc, nl, rlk, sc.dd, sc.dd + S, 1, 1, sc);
     if (tensor_pass_ok(a->data, b->data, sc.dd, sc.dsrc)) {
         if (int rc = launch_tensor(c, a->data, b->data, sc.dd, sc.dsrc, nl, st)) return rc;
@@ -347,7 +348,7 @@ static int automorph_entry(fides_ctx *c, const fides_ct *a, u64 g, const uint64_
     const size_t S = (size_t)nl * c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op(trace, st);
-    const Scratch sc = carve(c, ws);
+    const Scratch sc = carve(c, ws, stream);
     KsBuffers B = ks_buffers(c, sc.dsrc, nl, rk, out->data, out->data + S, 1, 0, sc);
     B.prep = 2;
     B.pa = a->data;
@@ -423,7 +424,7 @@ int fides_rotate_hoisted_ws(fides_ctx *c, const fides_ct *a, int n_rot, const in
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_rotate_hoisted", st);
     // one ModUp of c1 (the INTT reads c1 itself; the digits' own limbs are c1's)
-    KsBuffers B = ks_buffers(c, a->data + S, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, ws));
+    KsBuffers B = ks_buffers(c, a->data + S, nl, nullptr, nullptr, nullptr, 0, 0, carve(c, ws, stream));
     if (int rc = run_modup(c, B, st)) return rc;
     for (int k = 0; k < n_rot; ++k) {
         B.evk = rks[k];
@@ -467,7 +468,7 @@ static int rescale_entry(fides_ctx *c, const fides_ct *a, fides_ct *out, void *s
         return fides_set_error(FIDES_ERR_ARG, "%s: needs n_limbs >= 2 and out->n_limbs = n_limbs - 1", fn);
     cudaStream_t st = as_stream(stream);
     OpTrace op(nearest ? "op_rescale_round" : "op_rescale", st);
-    Scratch s = carve(c, ws);
+    Scratch s = carve(c, ws, stream);
     std::vector<Seg> v;
     rs_intt_segs(c, a->data, nl, s.last, v);
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;
@@ -510,7 +511,7 @@ int fides_modraise_ws(fides_ctx *c, const fides_ct *a, fides_ct *out, void *stre
     const size_t N = c->N;
     cudaStream_t st = as_stream(stream);
     OpTrace op("op_modraise", st);
-    Scratch s = carve(c, ws);
+    Scratch s = carve(c, ws, stream);
     std::vector<Seg> v;
     for (int t = 0; t < 2; ++t) v.push_back(seg_of(a->data + (size_t)t * N, s.last + (size_t)t * N, 1, 0));
     if (int rc = ntt_inverse(c, inline_set(v), ProSrc{}, EpiCanon{}, st)) return rc;

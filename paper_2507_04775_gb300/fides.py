@@ -40,7 +40,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale",
            "fides_rescale_round", "fides_key_register", "fides_key_destroy", "fides_key_galois",
            "fides_batch_configure", "fides_batch_autotune", "fides_batch_tuning", "fides_ctx_set_rounding",
-           "fides_ctx_rounding"]
+           "fides_ctx_rounding", "fides_ctx_add_stream"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 ROUND_FLOOR, ROUND_NEAREST = 0, 1
@@ -164,6 +164,7 @@ def lib():
         L.fides_ctx_status.argtypes = [_vp, ctypes.POINTER(_i)]
         L.fides_ctx_tensor_bconv.argtypes = [_vp]
         L.fides_ctx_set_rounding.argtypes = [_vp, _i]
+        L.fides_ctx_add_stream.argtypes = [_vp, _vp]
         L.fides_ctx_rounding.argtypes = [_vp]
         L.fides_ctx_selftest_wait.argtypes = [_vp, _i, _vp]
         L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
@@ -330,6 +331,12 @@ class Context:
         """Runs a device wait that nothing completes, limited to limit_us; it
         sets STATUS_WAIT_TIMEOUT in the status word (see status())."""
         _check(lib().fides_ctx_selftest_wait(self._h, limit_us, _stream(stream)))
+
+    def add_stream(self, stream):
+        """Give `stream` (a torch.cuda.Stream; default the current stream) its
+        own scratch pool, so single-operation calls on it may overlap calls on
+        other streams of this context (fides_ctx_add_stream)."""
+        _check(lib().fides_ctx_add_stream(self._h, _stream(stream)))
 
     def set_rounding(self, nearest: bool):
         """Floor (False, the default) or round-to-nearest (True) for every
