@@ -201,6 +201,20 @@ int fides_ctx_status(fides_ctx *ctx, int *flags);
 int fides_ctx_selftest_wait(fides_ctx *ctx, int limit_us, void *stream);
 
 /*
+ * Self-test of the tensor-core conversion's abort path: runs the top-level
+ * ModUp conversion (Eq. 1) on the scratch pool of `stream`, with every
+ * pipeline wait limited to limit_us (1..100000) microseconds, and with the
+ * first CTA never copying its first tile's sources in.  That CTA's waits run
+ * out; it sets FIDES_STATUS_WAIT_TIMEOUT, every role of it leaves its loop,
+ * it waits for the copies and products it did issue, frees its tensor memory
+ * and returns; the other CTAs convert normally.  Its outputs are scratch
+ * only.  The context stays usable.  Asynchronous on `stream`.  Returns
+ * FIDES_ERR_UNSUPPORTED when this context's ModUp converts on the integer
+ * kernel (a digit of more than 16 primes).
+ */
+int fides_ctx_selftest_conversion(fides_ctx *ctx, int limit_us, void *stream);
+
+/*
  * Rounding of the two divisions of the path -- ModDown's division by P and
  * Rescale's division by q_l -- for every operation of this context (single
  * operations, batches, the server and programs).  The paper's ModDown and

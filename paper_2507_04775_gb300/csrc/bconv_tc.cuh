@@ -267,6 +267,8 @@ struct TcPipe {
     int nbuf;       // accumulators in tensor memory
     u32 acc_cols;   // tensor-memory columns of one accumulator (a power of two)
     u32 ncols;      // columns allocated: nbuf x acc_cols
+    u64 limit_ns;   // limit of every pipeline wait (about 2 s)
+    int stall;      // self-test: CTA (0, 0) never copies its first tile in
 };
 
 // mbarriers of a CTA: source stage full / empty, A buffer full / empty,
@@ -289,9 +291,11 @@ __device__ __forceinline__ void bulk_copy(u32 dst, const void *src, u32 bytes, u
 }
 
 // A pipeline wait: true once the phase of `parity` has completed.  False when
-// another role has given up (abort set), or after about 2 s of %globaltimer,
+// another role has given up (abort set), or after limit_ns of %globaltimer,
 // which sets abort and the status bit, so that every role leaves its loop.
-__device__ __forceinline__ bool pipe_wait(u32 bar, u32 parity, volatile int *abort, int *status)
+// Lanes of one warp may disagree (abort set as the phase completes), so warps
+// that go on to warp-wide instructions combine their lanes' results first.
+__device__ __forceinline__ bool pipe_wait(u32 bar, u32 parity, volatile int *abort, int *status, u64 limit_ns)
 {
     if (mbar_test(bar, parity)) return true;
     const u64 t0 = global_ns();
@@ -299,7 +303,7 @@ __device__ __forceinline__ bool pipe_wait(u32 bar, u32 parity, volatile int *abo
         if (mbar_test(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*abort) return false;
-            if (global_ns() - t0 > 2000000000ull || it >= (1u << 26)) {
+            if (global_ns() - t0 > limit_ns || it >= (1u << 26)) {
                 *abort = 1;
                 atomicOr(status, FIDES_STATUS_WAIT_TIMEOUT);
                 return false;
@@ -404,14 +408,16 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
     __syncthreads();
     tc_fence_after();
     const u32 tm = tslot;
+    const u64 lim = pp.limit_ns;
 
     if (w < TC_PROD_WARPS) {
         const int m = t;
         unsigned char *arow0 = sA + (m >> 3) * (nsp * 128) + (m & 7) * 16;
         for (int k = 0; k < T; ++k) {
             const int ss = k % pp.depth, sa = k % pp.na;
-            if (!pipe_wait(bar(TB_SF + ss), (u32)(k / pp.depth) & 1, &sabort, status)) break;
-            if (k >= pp.na && !pipe_wait(bar(TB_AE + sa), (u32)(k / pp.na - 1) & 1, &sabort, status)) break;
+            bool ok = pipe_wait(bar(TB_SF + ss), (u32)(k / pp.depth) & 1, &sabort, status, lim);
+            if (ok && k >= pp.na) ok = pipe_wait(bar(TB_AE + sa), (u32)(k / pp.na - 1) & 1, &sabort, status, lim);
+            if (!__all_sync(0xffffffffu, ok)) break;   // one decision per warp (it synchronises below)
             const u64 *src = (const u64 *)(sS + ss * szS) + m;
             unsigned char *arow = arow0 + sa * szA;
             u32 cnt = 0;
@@ -435,11 +441,13 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
         }
     } else if (w == TC_LOAD_WARP) {
         if (lane == 0) {
-            int issued = 0;
+            int last[TC_MAX_DEPTH];   // the last tile copied into each stage, -1: none
+            for (int d = 0; d < TC_MAX_DEPTH; ++d) last[d] = -1;
             for (int k = 0; k < T; ++k) {
                 const int ss = k % pp.depth;
-                if (k >= pp.depth && !pipe_wait(bar(TB_SE + ss), (u32)(k / pp.depth - 1) & 1, &sabort, status))
+                if (k >= pp.depth && !pipe_wait(bar(TB_SE + ss), (u32)(k / pp.depth - 1) & 1, &sabort, status, lim))
                     break;
+                if (pp.stall && k == 0 && blockIdx.x == 0 && blockIdx.y == 0) continue;   // self-test
                 const size_t tile = (size_t)blockIdx.x + (size_t)k * gridDim.x;
                 const u32 dst = smem_addr(sS + ss * szS);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(TB_SF + ss)),
@@ -447,23 +455,21 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
                              : "memory");
                 for (int s = 0; s < ns; ++s)
                     bulk_copy(dst + 1024u * s, B.src + (size_t)s * N + tile * TC_M, 1024u, bar(TB_SF + ss));
-                issued = k + 1;
+                last[ss] = k;
             }
             // copies still in flight land before the CTA leaves
-            for (int ss = 0; ss < pp.depth && ss < issued; ++ss) {
-                const int last = ss + ((issued - 1 - ss) / pp.depth) * pp.depth;
-                mbar_wait(bar(TB_SF + ss), (u32)(last / pp.depth) & 1);
-            }
+            for (int ss = 0; ss < pp.depth; ++ss)
+                if (last[ss] >= 0) mbar_wait(bar(TB_SF + ss), (u32)(last[ss] / pp.depth) & 1);
         }
     } else if (w == TC_MMA_WARP) {
         if (lane == 0) {
             int issued = 0;
-            const bool img = pipe_wait(bar(TB_IMG), 0, &sabort, status);
+            const bool img = pipe_wait(bar(TB_IMG), 0, &sabort, status, lim);
             const u32 a0 = smem_addr(sA), b0 = smem_addr(sB), sbo = (u32)nsp * 128;
             for (int k = 0; img && k < T; ++k) {
                 const int sa = k % pp.na, sb = k % pp.nbuf;
-                if (!pipe_wait(bar(TB_AF + sa), (u32)(k / pp.na) & 1, &sabort, status)) break;
-                if (k >= pp.nbuf && !pipe_wait(bar(TB_CE + sb), (u32)(k / pp.nbuf - 1) & 1, &sabort, status))
+                if (!pipe_wait(bar(TB_AF + sa), (u32)(k / pp.na) & 1, &sabort, status, lim)) break;
+                if (k >= pp.nbuf && !pipe_wait(bar(TB_CE + sb), (u32)(k / pp.nbuf - 1) & 1, &sabort, status, lim))
                     break;
                 tc_fence_after();
                 const u32 acc = tm + sb * pp.acc_cols, ab = a0 + sa * szA;
@@ -486,7 +492,8 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
         const u32 lanes = (u32)(32 * q4) << 16;
         for (int k = 0; k < T; ++k) {
             const int sb = k % pp.nbuf;
-            if (!pipe_wait(bar(TB_CF + sb), (u32)(k / pp.nbuf) & 1, &sabort, status)) break;
+            const bool ok = pipe_wait(bar(TB_CF + sb), (u32)(k / pp.nbuf) & 1, &sabort, status, lim);
+            if (!__all_sync(0xffffffffu, ok)) break;   // one decision per warp (tcgen05.ld is warp-wide)
             tc_fence_after();
             const size_t n = ((size_t)blockIdx.x + (size_t)k * gridDim.x) * TC_M + 32 * q4 + lane;
             const u32 acc = tm + sb * pp.acc_cols + lanes;
@@ -543,7 +550,8 @@ inline int bconv_tc_smem(const BConvJob &j)
 // ring is as deep as shared memory allows, up to TC_MAX_DEPTH tiles, with two
 // A buffers, else one.  The CTAs of a job take its N / 128 tiles round robin.
 template <bool BIG>
-inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st)
+inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st,
+                             u64 limit_ns, int stall)
 {
     static int static_smem = -1;
     if (static_smem < 0) {
@@ -559,6 +567,8 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
     while (pp.acc_cols < (u32)(8 * ndp)) pp.acc_cols <<= 1;
     pp.nbuf = 2 * pp.acc_cols <= 512 ? 2 : 1;
     pp.ncols = pp.nbuf * pp.acc_cols;
+    pp.limit_ns = limit_ns;
+    pp.stall = stall;
     // a bound on every job's layout: image + one A buffer (G.tc_smem), the
     // second A buffer and the stages at the largest source count
     const size_t budget = 227 * 1024 - (size_t)static_smem;
@@ -602,10 +612,13 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
     return fides_check_cuda(cudaGetLastError(), "bconv tc launch");
 }
 
-inline int launch_bconv_tc(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st)
+// limit_ns: the limit of every pipeline wait; stall: the self-test in which
+// CTA (0, 0) never copies its first tile in (fides_ctx_selftest_conversion)
+inline int launch_bconv_tc(const fides_ctx *c, const BConvArgs &G, int max_ns, int max_dst, cudaStream_t st,
+                           u64 limit_ns = 2000000000ull, int stall = 0)
 {
-    return c->tc_big ? launch_bconv_tc_t<true>(c, G, max_ns, max_dst, st)
-                     : launch_bconv_tc_t<false>(c, G, max_ns, max_dst, st);
+    return c->tc_big ? launch_bconv_tc_t<true>(c, G, max_ns, max_dst, st, limit_ns, stall)
+                     : launch_bconv_tc_t<false>(c, G, max_ns, max_dst, st, limit_ns, stall);
 }
 
 }  // namespace

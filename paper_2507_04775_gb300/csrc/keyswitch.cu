@@ -160,6 +160,30 @@ extern "C" int fides_ctx_selftest_wait(fides_ctx *c, int limit_us, void *stream)
     return fides_check_cuda(cudaGetLastError(), "fides_ctx_selftest_wait");
 }
 
+extern "C" int fides_ctx_selftest_conversion(fides_ctx *c, int limit_us, void *stream)
+{
+    if (!c || limit_us < 1 || limit_us > 100000)
+        return fides_set_error(FIDES_ERR_ARG, "fides_ctx_selftest_conversion: limit_us must be 1..100000");
+    if (!(c->tc_on & 1))
+        return fides_set_error(FIDES_ERR_UNSUPPORTED, "fides_ctx_selftest_conversion: ModUp converts on the integer "
+                                                      "kernel on this context");
+    // the top-level ModUp conversion on the scratch pool of `stream`: its
+    // sources hold whatever the pool holds, and only the status word is the
+    // result
+    KsBuffers B = ks_buffers(c, nullptr, c->L, nullptr, nullptr, nullptr, 0, 0, carve(c, nullptr, stream));
+    std::vector<BConvJob> jb;
+    ks_modup_jobs(c, B, jb);
+    BConvArgs G = inline_bconv(jb);
+    G.tc = 1;
+    int max_ns = 0, max_dst = 0;
+    for (const BConvJob &j : jb) {
+        G.tc_smem = std::max(G.tc_smem, bconv_tc_smem(j));
+        max_ns = std::max(max_ns, j.n_src);
+        max_dst = std::max(max_dst, bconv_targets(j));
+    }
+    return launch_bconv_tc(c, G, max_ns, max_dst, as_stream(stream), (u64)limit_us * 1000, 1);
+}
+
 extern "C" int fides_ntt(fides_ctx *c, uint64_t *dev, int first_prime, int n_limbs, int batch, void *stream)
 {
     return ntt_entry(c, dev, first_prime, n_limbs, batch, stream, false);

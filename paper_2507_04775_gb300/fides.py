@@ -40,7 +40,7 @@ EXPORTS = ["fides_last_error", "fides_version", "fides_find_primes", "fides_ctx_
            "fides_ctx_status", "fides_ctx_tensor_bconv", "fides_ctx_selftest_wait", "fides_hmult_rescale",
            "fides_rescale_round", "fides_key_register", "fides_key_destroy", "fides_key_galois",
            "fides_batch_configure", "fides_batch_autotune", "fides_batch_tuning", "fides_ctx_set_rounding",
-           "fides_ctx_rounding", "fides_ctx_add_stream"]
+           "fides_ctx_rounding", "fides_ctx_add_stream", "fides_ctx_selftest_conversion"]
 
 OP_HMULT, OP_ROTATE, OP_RESCALE = 1, 2, 3
 ROUND_FLOOR, ROUND_NEAREST = 0, 1
@@ -165,6 +165,7 @@ def lib():
         L.fides_ctx_tensor_bconv.argtypes = [_vp]
         L.fides_ctx_set_rounding.argtypes = [_vp, _i]
         L.fides_ctx_add_stream.argtypes = [_vp, _vp]
+        L.fides_ctx_selftest_conversion.argtypes = [_vp, _i, _vp]
         L.fides_ctx_rounding.argtypes = [_vp]
         L.fides_ctx_selftest_wait.argtypes = [_vp, _i, _vp]
         L.fides_ctx_ntt_tile.argtypes = [_vp, _i, _i]
@@ -331,6 +332,13 @@ class Context:
         """Runs a device wait that nothing completes, limited to limit_us; it
         sets STATUS_WAIT_TIMEOUT in the status word (see status())."""
         _check(lib().fides_ctx_selftest_wait(self._h, limit_us, _stream(stream)))
+
+    def selftest_conversion(self, limit_us: int = 5000, stream=None):
+        """Runs the top-level ModUp conversion with one CTA whose first tile
+        never arrives and every wait limited to limit_us; that CTA gives up,
+        sets STATUS_WAIT_TIMEOUT and frees its tensor memory
+        (fides_ctx_selftest_conversion)."""
+        _check(lib().fides_ctx_selftest_conversion(self._h, limit_us, _stream(stream)))
 
     def add_stream(self, stream):
         """Give `stream` (a torch.cuda.Stream; default the current stream) its

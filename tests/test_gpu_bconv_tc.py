@@ -180,3 +180,26 @@ def test_a_wait_that_runs_out_is_reported_and_the_context_stays_usable():
     check_modup_moddown(g, o, d, x, P.nq, "after a timeout")
     assert g.status() == 0
     g.close()
+
+
+@pytest.mark.parametrize("name", ["MID", "FULL"])
+def test_a_stalled_conversion_aborts_frees_its_tensor_memory_and_reports(name):
+    """The conversion's abort path: one CTA never receives its first tile, its
+    waits (limited to 5 ms here) run out, every role of it leaves, and it frees
+    its tensor memory; the status bit is set once.  Then two rounds of ModUp
+    and ModDown conversions, which allocate tensor memory on every SM, are
+    bit-exact with the oracle and report nothing."""
+    need_gpu()
+    P = getattr(si, name)
+    g, o = contexts(P.logN, P.nq, P.nk, P.dnum, P.q_bits, P.p_bits)
+    assert g.status() == 0
+    g.selftest_conversion(5000)
+    assert g.status() == 1            # reported once ...
+    assert g.status() == 0            # ... and cleared
+    st = si.Stream(1521, 1)
+    for rnd in range(2):
+        d = si.uniform_poly(st, o.q, o.N)
+        x = si.uniform_poly(st, o.q + o.p, o.N)
+        check_modup_moddown(g, o, d, x, P.nq, "after a stalled conversion, round %d" % rnd)
+    assert g.status() == 0
+    g.close()
