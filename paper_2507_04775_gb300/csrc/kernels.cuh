@@ -325,9 +325,9 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
     const int own = z < nl ? z / op.alpha : -1;
     const PrimeInfo pr = P[pz];
     const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * (V2 ? 2 : 1);
-    const u64 *__restrict__ ext = op.ext;
+    const u64 *ext = op.ext;     // written by the kernels before this one: coherent loads
     const u64 *__restrict__ evk = op.evk;
-    const u64 *__restrict__ dsrc = op.dsrc;
+    const u64 *dsrc = op.dsrc;
     u64 *acc = op.acc;
     if (V2) {
         // issue every load before the first product (the kernel is bound by
@@ -345,7 +345,7 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
 #pragma unroll
         for (int j = 0; j < MAXB; ++j) {
             if (j < beta) {
-                const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
+                const u64 *src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
                 e[j] = *reinterpret_cast<const ulonglong2 *>(src + n);
             }
         }
@@ -388,7 +388,7 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
 #pragma unroll
     for (int j = 0; j < MAXB; ++j) {
         if (j < beta) {
-            const u64 *__restrict__ src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
+            const u64 *src = (j == own) ? dsrc + (size_t)z * N : ext + ((size_t)j * ne + z) * N;
             e[j] = src[sn];
         }
     }

@@ -38,8 +38,8 @@ Scratch carve(const fides_ctx *c, u64 *ws, void *stream)
 // HMult result, last_t = INTT(d_t,l) + P^-1 (INTT(acc_t,l) - conv_t,l) mod q_l
 // (canonical), for t = 0, 1; lastc = [INTT(d0), INTT(d1), INTT(acc0),
 // INTT(acc1)] at limb l, conv_t,l < 4 q_l.
-__global__ void __launch_bounds__(256) k_hr_last(const u64 *__restrict__ lastc, const u64 *__restrict__ conv0,
-                                                 const u64 *__restrict__ conv1, u64 *__restrict__ last,
+__global__ void __launch_bounds__(256) k_hr_last(const u64 *lastc, const u64 *conv0,
+                                                 const u64 *conv1, u64 *__restrict__ last,
                                                  const TwPair *__restrict__ md_pinv, const PrimeInfo *__restrict__ P,
                                                  int l, int N)
 {

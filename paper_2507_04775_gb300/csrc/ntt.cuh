@@ -134,26 +134,29 @@ struct ProRaise {
 // A prologue in two steps, so that the kernel can issue the loads of several
 // elements before it computes and stores any of them (each call reads up to
 // four words and stores up to three): load() reads what element j needs,
-// apply() computes, stores the side outputs and returns the value.  The
-// operands go through the read-only path (outputs may not alias inputs).
+// apply() computes, stores the side outputs and returns the value.  Outputs
+// may not alias inputs.  The operands are read with coherent loads, not the
+// non-coherent path (ld.global.nc): PTX allows that path only for data that
+// stays unchanged for the kernel's whole lifetime, and under programmatic
+// dependent launch a kernel starts while the one before it still writes.
 struct ProPrep {
     int logN;
     __device__ __forceinline__ void load(const Job &J, u32 j, u64 (&v)[4]) const
     {
         const size_t S = (size_t)J.pstride;
         if (J.mode == 0) {
-            v[0] = __ldg(J.src + j);
+            v[0] = J.src[j];
         } else if (J.mode == 1) {
-            v[0] = __ldg(J.src + j);
-            v[1] = __ldg(J.src + S + j);
-            v[2] = __ldg(J.aux + j);
-            v[3] = __ldg(J.aux + S + j);
+            v[0] = J.src[j];
+            v[1] = J.src[S + j];
+            v[2] = J.aux[j];
+            v[3] = J.aux[S + j];
         } else {
             const u32 rj = __brev(j) >> (32 - logN);
             const u64 e = ((2 * (u64)rj + 1) * J.g) & ((2ull << logN) - 1);
             const u32 src = __brev((u32)((e - 1) >> 1)) >> (32 - logN);
-            v[0] = __ldg(J.src + src);
-            v[1] = __ldg(J.src + S + src);
+            v[0] = J.src[src];
+            v[1] = J.src[S + src];
         }
     }
     __device__ __forceinline__ u64 apply(const Job &J, u32 j, const u64 (&v)[4], const PrimeInfo &p) const
@@ -184,9 +187,9 @@ struct ProPrep {
 
 // The plain inverse-NTT input (every segment of mode 0): the row pass issues
 // all sixteen of a thread's loads before it stores any of them to shared
-// memory, through the read-only path.
+// memory (coherent loads, as for ProPrep).
 struct ProPlain {
-    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return __ldg(J.src + j); }
+    __device__ __forceinline__ u64 operator()(const Job &J, u32 j, const PrimeInfo &) const { return J.src[j]; }
 };
 
 // ---- epilogue functors ----
