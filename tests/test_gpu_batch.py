@@ -255,3 +255,35 @@ def test_batch_rejects_bad_ops():
     with pytest.raises(FidesError):
         Batch(g, [Op(OP_RESCALE, a, 1, zeros(o, 1))])
     g.close()
+
+
+def test_batch_with_more_conversion_jobs_than_sms():
+    """72 HMults at logN=12 with 12 limbs (three digits each): the batch's
+    ModUp conversion launch has 216 jobs, more than the GPU has SMs, so its
+    launcher splits each job's tiles over several CTAs in several waves.
+    Every product equals the single-op HMult's, and two equal the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P = si.MID
+    g, o = make_pair(P)
+    st = si.Stream(503, 1)
+    rlk = rand_key(st, o)
+    drlk = g.relin_key(to_device(rlk))
+    nl, n = P.nq, 72
+    pairs = [(rand_ct(st, o, nl), rand_ct(st, o, nl)) for _ in range(n)]
+    dev = [(to_device(a), to_device(b)) for a, b in pairs]
+    ops = [Op(OP_HMULT, da, nl, zeros(o, nl), b=db, key=drlk, stage=0) for da, db in dev]
+    batch = Batch(g, ops)
+    batch.run()
+    torch.cuda.synchronize()
+    for (da, db), op in zip(dev, ops):
+        ref = zeros(o, nl)
+        g.hmult(da, db, nl, drlk, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(op.out, ref)
+    for i in (0, n - 1):
+        a, b = pairs[i]
+        assert np.array_equal(to_host(ops[i].out).reshape(2, nl, o.N), o.hmult(a, b, rlk))
+    assert g.status() == 0
+    batch.close()
+    g.close()
