@@ -52,13 +52,19 @@ def build(o, st):
     return prog, nl
 
 
-def test_every_instruction_matches_the_oracle():
+@pytest.mark.parametrize("nearest", [False, True], ids=["floor", "nearest"])
+def test_every_instruction_matches_the_oracle(nearest):
+    """In both rounding modes of the context: round-to-nearest reaches the
+    program's ModDowns and Rescales (including HMULT+RESCALE pairs run as one
+    key switch)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     P = si.MID
     q = find_primes(P.logN, P.q_bits, P.nq)
     p = find_primes(P.logN, P.p_bits, P.nk, exclude=q)
     g, o = Context(P.logN, q, p, P.dnum), oracle.Context(P.logN, q, p, P.dnum)
+    g.set_rounding(nearest)
+    o.set_rounding(nearest)
     st = si.Stream(1101)
     prog, nl = build(o, st)
     rlk, ck = rand_key(st, o), rand_key(st, o)

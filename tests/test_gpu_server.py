@@ -215,3 +215,24 @@ def test_server_injected_faults_on_the_device_path():
     assert st["failed"] == 1 and st["timed_out"] == 1 and st["arena_used"] == 0
     s.close()
     w.g.close()
+
+
+def test_server_in_round_to_nearest_mode():
+    """The context's round-to-nearest mode reaches the server's launch groups:
+    every request in a mixed run equals the oracle in that mode (centred
+    ModDown conversion, centred Rescale lift) and the single-op path."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = Workload(si.MID, [12, 10, 5, 2], 24, 605)
+    w.g.set_rounding(True)
+    w.o.set_rounding(True)
+    s = w.server(256 << 20, n_lanes=2, max_batch=8)
+    mixed, got = run_mixed(w, s)
+    assert max(c.group_ops for c in got) > 1
+    for i in range(len(w.reqs)):
+        kind, nl = w.reqs[i][:2]
+        out_nl = nl - 1 if kind == OP_RESCALE else nl
+        assert np.array_equal(mixed[i].reshape(2, out_nl, w.o.N), w.oracle(i)), i
+        assert np.array_equal(mixed[i], w.single_op(i)), i
+    s.close()
+    w.g.close()
