@@ -376,3 +376,55 @@ def test_argument_errors(pair):
     # a raw buffer where a key handle belongs is refused by the binding
     with pytest.raises(TypeError):
         g.hmult(d, d, 1, key.tensor, d)
+
+
+def test_boundary_refuses_bad_descriptors_before_queueing():
+    """Through the C ABI: zero limbs, more limbs than the context has, a level
+    mismatch between operands, an output aliasing an input and a NULL
+    descriptor are each refused with FIDES_ERR_ARG, and no work is queued (a
+    sentinel output stays as it was)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_04775_gb300 import fides as F
+    P = si.SMALL
+    g, o = make_pair(P)
+    st = si.Stream(1020, 1)
+    L, N = P.nq, o.N
+    key = rand_key(st, o)
+    rlk = g.relin_key(to_device(key))
+    rk = g.rotation_key(to_device(key), 1)
+    a = to_device(rand_poly(st, o.q, N, 2))
+    b = to_device(rand_poly(st, o.q, N, 2))
+    sentinel = torch.full((2 * (L + 1) * N,), 12345, dtype=torch.int64, device="cuda")
+    lib = F.lib()
+
+    def ct(t, n):
+        return F.fides_ct(t.data_ptr(), n, 1.0)
+
+    cases = [
+        ("hmult, 0 limbs", lambda: lib.fides_hmult(g._h, ctypes.byref(ct(a, 0)), ctypes.byref(ct(b, 0)),
+                                                   rlk.handle, ctypes.byref(ct(sentinel, 0)), None)),
+        ("hmult, L + 1 limbs", lambda: lib.fides_hmult(g._h, ctypes.byref(ct(a, L + 1)), ctypes.byref(ct(b, L + 1)),
+                                                       rlk.handle, ctypes.byref(ct(sentinel, L + 1)), None)),
+        ("hmult, level mismatch", lambda: lib.fides_hmult(g._h, ctypes.byref(ct(a, L)), ctypes.byref(ct(b, L - 1)),
+                                                          rlk.handle, ctypes.byref(ct(sentinel, L)), None)),
+        ("hmult, out aliases a", lambda: lib.fides_hmult(g._h, ctypes.byref(ct(sentinel, L)),
+                                                         ctypes.byref(ct(b, L)), rlk.handle,
+                                                         ctypes.byref(ct(sentinel, L)), None)),
+        ("hmult, NULL b", lambda: lib.fides_hmult(g._h, ctypes.byref(ct(a, L)), None, rlk.handle,
+                                                  ctypes.byref(ct(sentinel, L)), None)),
+        ("rotate, out level", lambda: lib.fides_rotate(g._h, ctypes.byref(ct(a, L)), 1, rk.handle,
+                                                       ctypes.byref(ct(sentinel, L - 1)), None)),
+        ("rotate, out aliases a", lambda: lib.fides_rotate(g._h, ctypes.byref(ct(sentinel, L)), 1, rk.handle,
+                                                           ctypes.byref(ct(sentinel, L)), None)),
+        ("rescale, 1 limb", lambda: lib.fides_rescale(g._h, ctypes.byref(ct(a, 1)), ctypes.byref(ct(sentinel, 0)),
+                                                      None)),
+        ("rescale, out level", lambda: lib.fides_rescale(g._h, ctypes.byref(ct(a, L)), ctypes.byref(ct(sentinel, L)),
+                                                         None)),
+    ]
+    for name, call in cases:
+        assert call() == -1, name
+        torch.cuda.synchronize()
+        assert bool((sentinel == 12345).all()), "%s queued work" % name
+    assert g.status() == 0
+    g.close()
