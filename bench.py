@@ -1037,6 +1037,31 @@ def run_bootstrap(args):
     top_ops = {k[3:]: [v[0], round(v[1], 2)] for k, v in sorted(tr.items(), key=lambda x: -x[1][1])
                if k.startswith("op_") and k != "op_program"}
     kern = {k: [v[0], round(v[1], 2)] for k, v in sorted(tr.items(), key=lambda x: -x[1][1]) if k.startswith("k_")}
+    # sparse packing at the slot counts of the paper's Table IV below 2^15:
+    # the same batch on one stream (a trace of rotate-and-add steps after
+    # ModRaise, then slots-point transforms)
+    sparse = {}
+    for slots in (1 << 14, 512, 64):
+        t0 = time.perf_counter()
+        sp = bt.plan(N, q, 2.0 ** 50, slots=slots)
+        t_sp = time.perf_counter() - t0
+        srks = [ctx.rotation_key(key.clone(), s) for s in sp.rot_steps]
+        sdp = bt.DeviceProgram(ctx, sp, rlk, ck, srks)
+        souts = [torch.empty(2 * sdp.out_limbs * N, dtype=torch.int64, device="cuda") for _ in cts]
+        sdp.run(cts[0], souts[0], 2.0 ** 50)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for c, o in zip(cts, souts):
+            sdp.run(c, o, 2.0 ** 50)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        sparse[str(slots)] = {"ms_per_ciphertext": round(ms_s / len(cts), 2), "one_lane_ms_per_batch": round(ms_s, 2),
+                              "limbs_out": sdp.out_limbs, "rotation_keys": len(sp.rot_steps),
+                              "trace_rotations": sum(1 for ins in sp.instr if ins[0] == bt.OP["ROT"]),
+                              "plan_s": round(t_sp, 1)}
+        sdp.close()
+        del srks, souts
     counts = {}
     for ins in prog.instr:
         counts[ins[0]] = counts.get(ins[0], 0) + 1
@@ -1051,7 +1076,9 @@ def run_bootstrap(args):
            "kernels_per_bootstrap": int(per_boot_launches), "device_buffers": dp.buffers,
            "work_gib": round(dp.work_words * 8 / 2 ** 30, 2), "plan_s": round(t_plan, 1), "load_s": round(t_load, 1),
            "traced_ops_calls_ms": top_ops, "traced_kernels_launches_ms": kern,
-           "traced_note": "one traced bootstrap; nested operations (a linear transform's rotations) count in both"}
+           "traced_note": "one traced bootstrap; nested operations (a linear transform's rotations) count in both",
+           "one_lane_ms_per_ciphertext": round(ms_one / len(cts), 2),
+           "sparse_slots": sparse}
     dp.close()
     del rks, cts, outs, key
     ctx.close()

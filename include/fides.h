@@ -662,6 +662,7 @@ int64_t fides_now_ns(void);
  *   CONJ a (conjugation key)                       MULI a by i (arg = 1) or -i (arg = -1)
  *   CMULT a by constant #arg (scale times const_scale[arg])
  *   CADD constant #arg to a                        COPY a
+ *   ROT a by `arg` slots (the rotation key of Galois element 5^arg mod 2N)
  *   CMAC: dst <- sum_t const[c_t] * reg[r_t] at `b` limbs, over term list #arg
  *         (terms r_t, c_t: lin_reg / lin_const[lin_start[arg] .. lin_start[arg+1]),
  *         1..32 terms, each register with at least b limbs, read in place;
@@ -694,6 +695,7 @@ int64_t fides_now_ns(void);
 #define FIDES_I_CADD 11
 #define FIDES_I_COPY 12
 #define FIDES_I_CMAC 13
+#define FIDES_I_ROT 14
 
 typedef struct {
     int op, dst, a, b, arg;

@@ -42,7 +42,7 @@ import numpy as np
 from oracle import encode
 
 # instruction codes (shared program format)
-MODRAISE, LT, RESCALE, DROP, HADD, HSUB, HMULT, CONJ, MULI, CMULT, CADD, COPY, CMAC = range(1, 14)
+MODRAISE, LT, RESCALE, DROP, HADD, HSUB, HMULT, CONJ, MULI, CMULT, CADD, COPY, CMAC, ROT = range(1, 15)
 
 
 @dataclass
@@ -249,25 +249,49 @@ def _bsgs_n1(idx, n: int) -> int:
 
 
 def plan(client, q, in_scale: float, K: int = 25, degree: int = 119, double_angle: int = 2, budget: int = 3,
-         baby: int = 16, scale0: float = 2.0 ** 54) -> Program:
+         baby: int = 16, scale0: float = 2.0 ** 54, slots: int | None = None) -> Program:
     """Bootstrapping program for a ciphertext at one limb with scale in_scale;
-    q: the q-primes (q[0] is the one removed by ModRaise's lift)."""
+    q: the q-primes (q[0] is the one removed by ModRaise's lift).
+
+    slots: the number of slots in use, a power of two up to N/2 (default N/2).
+    With fewer (sparse packing), the message's slot vector repeats with period
+    `slots`, i.e. the message lies in Z[Y], Y = X^(N / (2 slots)).  After
+    ModRaise the trace onto that subring -- the sum of the rotations by
+    multiples of `slots`, as log2(N / (2 slots)) rotate-and-add steps --
+    multiplies its part of t = m + q_0 I by N / (2 slots) and removes the rest
+    of I.  The slot transforms are then those of a ring of degree 2 slots:
+    the DFT on `slots` points, its diagonals repeated to fill the N/2 slots
+    (a rotation by d < slots of a periodic vector is a rotation by d within
+    each period), and the trace's factor takes the place of the DFT's
+    1 / (N/2) -> 1 / slots normalisation, so the scaling constants stay."""
     N = client.ctx.N
     n = N // 2
+    ns = n if slots is None else int(slots)
+    assert 2 <= ns <= n and ns & (ns - 1) == 0, "slots must be a power of two in [2, N/2]"
+    reps = n // ns
     L = len(q)
     B = _Builder(client, q, scale0)
     x = B.reg(1, in_scale)
     B.prog.in_reg = x
     r = B.emit(MODRAISE, x, arg=L, level=L, scale=scale0)
+    # trace onto the subring: r <- r + rot(r, ns 2^k) for k < log2(reps)
+    k = 0
+    while (ns << k) < n:
+        rot = B.emit(ROT, r, arg=ns << k, level=L, scale=B.scale[r])
+        if (ns << k) not in B.prog.rot_steps:
+            B.prog.rot_steps.append(ns << k)
+        r = B.emit(HADD, r, rot, level=L, scale=B.scale[r])
+        k += 1
 
-    groups = dft_groups(n, budget)
-    # CoeffToSlot: c F^H = c G_1^H G_2^H ... (the last stages first)
+    groups = dft_groups(ns, budget)
+    # CoeffToSlot: c F^H = c G_1^H G_2^H ... (the last stages first); the
+    # trace's factor reps and the DFT's 1 / ns make 1 / n as before
     c = scale0 / (n * q[0] * 2 * K)
     f = abs(c) ** (1.0 / budget)
     w = r
     for G in reversed(groups):
-        D = {d: v * f for d, v in diag_adjoint(G, n).items()}
-        w = B.lt(w, D, _bsgs_n1(sorted(D), n))
+        D = {d: np.tile(v * f, reps) for d, v in diag_adjoint(G, ns).items()}
+        w = B.lt(w, D, _bsgs_n1(sorted(D), ns))
 
     cj = B.emit(CONJ, w, level=B.level[w], scale=B.scale[w])
     u_re = B.emit(HADD, w, cj, level=B.level[w], scale=B.scale[w])
@@ -285,8 +309,8 @@ def plan(client, q, in_scale: float, K: int = 25, degree: int = 119, double_angl
     c2 = q[0] / (2 * np.pi * in_scale)
     f2 = c2 ** (1.0 / budget)
     for G in groups:
-        D = {d: v * f2 for d, v in G.items()}
-        y = B.lt(y, D, _bsgs_n1(sorted(D), n))
+        D = {d: np.tile(v * f2, reps) for d, v in G.items()}
+        y = B.lt(y, D, _bsgs_n1(sorted(D), ns))
     B.prog.out_reg = y
     B.prog.out_scale = B.scale[y]
     B.prog.rot_steps.sort()
@@ -373,6 +397,8 @@ def run(ctx, prog: Program, ct, relin_key, conj_key, rot_keys: dict, registers: 
             y = ctx.hmult(x, R[b], relin_key)
         elif op == CONJ:
             y = ctx.conjugate(x, conj_key)
+        elif op == ROT:
+            y = ctx.rotate(x, arg, rot_keys[arg])
         elif op == MULI:
             y = ctx.mul_monomial(x, N // 2 if arg > 0 else 3 * N // 2)
         elif op == CMULT:

@@ -38,7 +38,7 @@ import numpy as np
 from . import fides as F
 
 OP = {"MODRAISE": 1, "LT": 2, "RESCALE": 3, "DROP": 4, "HADD": 5, "HSUB": 6, "HMULT": 7, "CONJ": 8, "MULI": 9,
-      "CMULT": 10, "CADD": 11, "COPY": 12, "CMAC": 13}
+      "CMULT": 10, "CADD": 11, "COPY": 12, "CMAC": 13, "ROT": 14}
 
 
 class BootProgram:
@@ -163,6 +163,7 @@ class _Plan:
         self.lv, self.sc = [], []
         self.sigma = {}
         self.lowered = {}
+        self.period = N // 2    # slots in use: transforms act on vectors of this period
 
     def new(self, lv, sc):
         self.lv.append(lv)
@@ -226,7 +227,7 @@ class _Plan:
         for i in idx:
             stride = math.gcd(stride, i)
         stride = stride or n
-        n1 = min(n, stride * (1 << max(0, math.ceil(0.5 * math.log2(len(idx))))))
+        n1 = min(self.period, stride * (1 << max(0, math.ceil(0.5 * math.log2(len(idx))))))
         coeffs = [encode_coeffs(np.roll(diags[i], n1 * (i // n1)), ql) for i in idx]
         self.p.lts.append({"diag_idx": idx, "coeffs": coeffs, "n1": n1, "pt_scale": ql, "level": l})
         for i in idx:
@@ -237,19 +238,38 @@ class _Plan:
 
 
 def plan(N: int, q, in_scale: float, K: int = 25, degree: int = 119, double_angle: int = 2, budget: int = 3,
-         baby: int = 16, scale0: float = 2.0 ** 54) -> BootProgram:
+         baby: int = 16, scale0: float = 2.0 ** 54, slots: int | None = None) -> BootProgram:
     """Bootstrapping program for a ciphertext at one limb (modulo q[0]) with
-    scale in_scale, in a context with q-primes q (len(q) = L)."""
+    scale in_scale, in a context with q-primes q (len(q) = L).
+
+    slots: slots in use, a power of two up to N/2 (default).  A sparse
+    message (slot vector periodic with that period) is a polynomial in
+    X^(N / 2 slots); after ModRaise, adding the rotations by slots, 2 slots,
+    4 slots, ... (each step doubling the sum) projects t = m + q_0 I onto that
+    subring, times N / (2 slots).  The transforms are the slots-point DFT
+    with each diagonal repeated over the N/2 slots, and the trace's factor
+    with the DFT's 1 / slots gives the 1 / (N/2) the constants already use."""
     n = N // 2
+    ns = n if slots is None else int(slots)
+    if not (2 <= ns <= n and ns & (ns - 1) == 0):
+        raise ValueError("slots must be a power of two in [2, N/2]")
     L = len(q)
     P = _Plan(N, q)
+    P.period = ns
     x = P.new(1, in_scale)
     P.p.in_reg = x
     t = P.op("MODRAISE", x, arg=L, lv=L, sc=scale0)
-    groups = slot_dft_groups(n, budget)
+    step = ns
+    while step < n:
+        t = P.op("HADD", t, P.op("ROT", t, arg=step))
+        if step not in P.p.rot_steps:
+            P.p.rot_steps.append(step)
+        step *= 2
+    groups = slot_dft_groups(ns, budget)
     f = (scale0 / (n * q[0] * 2 * K)) ** (1.0 / budget)
+    tile = n // ns
     for G in groups[::-1]:
-        t = P.transform(t, {d: f * v for d, v in _adjoint(G, n).items()})
+        t = P.transform(t, {d: np.tile(f * v, tile) for d, v in _adjoint(G, ns).items()})
     c = P.op("CONJ", t)
     u_re = P.op("HADD", t, c)
     u_im = P.op("MULI", P.op("HSUB", t, c), arg=-1)
@@ -260,7 +280,7 @@ def plan(N: int, q, in_scale: float, K: int = 25, degree: int = 119, double_angl
     y = P.op("HADD", e_re, P.op("MULI", e_im, arg=1))
     f2 = (q[0] / (2 * np.pi * in_scale)) ** (1.0 / budget)
     for G in groups:
-        y = P.transform(y, {d: f2 * v for d, v in G.items()})
+        y = P.transform(y, {d: np.tile(f2 * v, tile) for d, v in G.items()})
     P.p.out_reg = y
     P.p.out_scale = P.sc[y]
     P.p.rot_steps.sort()

@@ -51,6 +51,16 @@ namespace {
 
 bool reads_b(int op) { return op == FIDES_I_HADD || op == FIDES_I_HSUB || op == FIDES_I_HMULT; }
 
+// The key of the rotation by `steps` among the program's handles: the one
+// registered with Galois element 5^steps mod 2N, or null.
+const uint64_t *rot_key(const fides_program *p, int64_t steps)
+{
+    const u64 want = fides_galois_elt(p->ctx, steps);
+    for (const fides_key *k : p->rot_keys)
+        if (k && k->g == want) return k->data;
+    return nullptr;
+}
+
 // registers an instruction reads
 std::vector<int> operands(const fides_program *p, const fides_instr &I)
 {
@@ -152,6 +162,9 @@ int analyse(fides_program *p)
             break;
         case FIDES_I_CONJ:
             if (!p->conj) return bad("no conjugation key");
+            break;
+        case FIDES_I_ROT:
+            if (!rot_key(p, I.arg)) return bad("no rotation key for the step");
             break;
         case FIDES_I_MULI:
             if (I.arg != 1 && I.arg != -1) return bad("MULI takes +1 or -1");
@@ -414,6 +427,7 @@ extern "C" int fides_program_run(fides_program *p, const fides_ct *in, fides_ct 
         case FIDES_I_HSUB: rc = fides_hsub(c, &a, &b, &d, stream); break;
         case FIDES_I_HMULT: rc = fides_hmult_ws(c, &a, &b, p->relin, &d, stream, ws); break;
         case FIDES_I_CONJ: rc = fides_conjugate_ws(c, &a, p->conj, &d, stream, ws); break;
+        case FIDES_I_ROT: rc = fides_rotate_ws(c, &a, I.arg, rot_key(p, I.arg), &d, stream, ws); break;
         case FIDES_I_MULI: rc = fides_mul_i(c, &a, I.arg, &d, stream); break;
         case FIDES_I_CMULT:
             rc = fides_scalar_mult(c, &a, p->consts[I.arg].data(), p->const_scale[I.arg], &d, stream);

@@ -88,3 +88,44 @@ def test_planned_bootstrap_refreshes_a_ciphertext():
     out = obt.run(ctx, ev, ct, cl.relin_key(), cl.conjugation_key(), rks)
     err = np.max(np.abs(cl.decrypt(out, prog.out_scale) - z)) / max(1.0, np.max(np.abs(z)))
     assert err < 2.0 ** -12, err
+
+
+def _sparse_setup(seed):
+    q0 = oracle.find_primes(12, 60, 1)
+    q = q0 + oracle.find_primes(12, 54, 29, exclude=q0)
+    p = oracle.find_primes(12, 60, 10, exclude=q)
+    ctx = oracle.Context(12, q, p, 3)
+    return ctx, Client(ctx, seed=seed, hamming=192), q
+
+
+@pytest.mark.parametrize("slots", [256, 16])
+def test_oracle_sparse_bootstrap_refreshes_a_ciphertext(slots):
+    """The oracle planner with fewer slots than N/2: a message whose slot
+    vector repeats with period `slots` comes back within 2^-12, after the
+    trace (log2(N / 2 slots) rotate-and-add steps) and slots-point transforms."""
+    ctx, cl, q = _sparse_setup(si.workload_seed(4) + 11)
+    prog = obt.plan(cl, q, 2.0 ** 50, slots=slots)
+    n = ctx.N // 2
+    reps = n // slots
+    assert sum(1 for ins in prog.instr if ins[0] == obt.ROT) == reps.bit_length() - 1
+    assert [s for s in prog.rot_steps if s % slots == 0 and s >= slots] == [slots << k for k in range(reps.bit_length() - 1)]
+    rks = {s: cl.rotation_key(s) for s in prog.rot_steps}
+    z = np.tile(cl.random_slots()[:slots], reps)
+    ct = cl.encrypt(z, 1, 2.0 ** 50)
+    out = obt.run(ctx, prog, ct, cl.relin_key(), cl.conjugation_key(), rks)
+    got = cl.decrypt(out, prog.out_scale)
+    err = np.max(np.abs(got - z)) / max(1.0, np.max(np.abs(z)))
+    assert err < 2.0 ** -12, err
+
+
+def test_library_sparse_plan_refreshes_a_ciphertext():
+    """The library planner's program with 64 slots, run by the oracle."""
+    ctx, cl, q = _sparse_setup(si.workload_seed(4) + 12)
+    prog = bt.plan(ctx.N, q, 2.0 ** 50, slots=64)
+    ev = as_eval_form(ctx, prog)
+    rks = {s: cl.rotation_key(s) for s in prog.rot_steps}
+    z = np.tile(cl.random_slots()[:64], ctx.N // 2 // 64)
+    ct = cl.encrypt(z, 1, 2.0 ** 50)
+    out = obt.run(ctx, ev, ct, cl.relin_key(), cl.conjugation_key(), rks)
+    err = np.max(np.abs(cl.decrypt(out, prog.out_scale) - z)) / max(1.0, np.max(np.abs(z)))
+    assert err < 2.0 ** -12, err

@@ -1,7 +1,9 @@
 """GPU bootstrapping through the program executor: the oracle's program run on
-the device equals the oracle's own run residue for residue (logN=12); the
-library's planned program equals the oracle's execution of the same program
-and refreshes a ciphertext within 2^-12 (logN=12, 15 and 16, h = 192)."""
+the device equals the oracle's own run residue for residue (logN=12, all
+slots and 256 of 2048); the library's planned program equals the oracle's
+execution of the same program and refreshes a ciphertext within 2^-12
+(logN=12, 15 and 16, h = 192), also with 2^14, 512 and 64 slots at logN=16
+(sparse packing: the message's slot vector repeats with that period)."""
 import numpy as np
 import pytest
 
@@ -98,6 +100,45 @@ def test_bootstrap_decrypts_at_full_size(logN):
     got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)
     err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
     print("bootstrap logN=%d relative slot error 2^%.2f" % (logN, np.log2(err)))
+    assert err < 2.0 ** -12, err
+    g.close()
+
+
+def test_oracle_sparse_program_on_the_device_is_bit_exact():
+    """256 of 2048 slots: the trace (three ROT + HADD steps) and 256-point
+    transforms, run by the executor, equal the oracle's run residue for
+    residue, and the result decrypts to the repeated message."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o, cl, q = setup(12, si.workload_seed(4) + 5)
+    prog = obt.plan(cl, q, 2.0 ** 50, slots=256)
+    assert sum(1 for ins in prog.instr if ins[0] == obt.ROT) == 3
+    hkeys, dkeys = dev_keys(g, cl, prog.rot_steps)
+    z = np.tile(cl.random_slots()[:256], 8)
+    ct = cl.encrypt(z, 1, 2.0 ** 50)
+    ref = obt.run(o, prog, ct, *hkeys)
+    got, sc = run_device(g, prog, dkeys, ct, ref.shape[1])
+    assert np.array_equal(got, ref)
+    err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
+    assert err < 2.0 ** -12, err
+    g.close()
+
+
+@pytest.mark.parametrize("slots", [1 << 14, 512, 64])
+def test_sparse_bootstrap_decrypts_at_full_size(slots):
+    """logN=16 with the slot counts of the paper's Table IV below 2^15: the
+    library's planned program refreshes a message repeated with that period
+    within 2^-12 (h = 192, L = 30, K = 10, dnum = 3)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, o, cl, q = setup(16, si.workload_seed(4) + 6)
+    prog = bt.plan(g.N, q, 2.0 ** 50, slots=slots)
+    hkeys, dkeys = dev_keys(g, cl, prog.rot_steps)
+    z = np.tile(cl.random_slots()[:slots], (g.N // 2) // slots)
+    ct = cl.encrypt(z, 1, 2.0 ** 50)
+    got, sc = run_device(g, prog, dkeys, ct, len(q) - 15)
+    err = np.max(np.abs(cl.decrypt(got, sc) - z)) / max(1.0, np.max(np.abs(z)))
+    print("sparse bootstrap logN=16, %d slots: relative slot error 2^%.2f" % (slots, np.log2(err)))
     assert err < 2.0 ** -12, err
     g.close()
 
