@@ -652,8 +652,10 @@ int64_t fides_now_ns(void);
  * residues, one per q-limb; entries beyond an instruction's level unused) and
  * keys.  Bootstrapping is the program ModRaise -> three linear transforms
  * (CoeffToSlot) -> conjugation split -> EvalMod polynomial and double-angle
- * steps -> three linear transforms (SlotToCoeff); its tables are the
- * precomputation the paper takes from OpenFHE (Sec. III-B).
+ * steps -> three linear transforms (SlotToCoeff); with fewer slots than N/2
+ * (sparse packing, Table IV) ModRaise is followed by a trace of ROT and HADD
+ * steps.  Its tables are the precomputation the paper takes from OpenFHE
+ * (Sec. III-B).
  *
  * Instructions (dst <- ...):
  *   MODRAISE a to `arg` limbs (a has one limb)     LT #arg of a
