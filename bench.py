@@ -932,6 +932,45 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
     res["hmult_logN12_L3"] = {"us": round(t_small * 1e3, 2), "launches": int(fides.kernel_launches() - l0),
                               "note": "one call at a time; latency bound (each launch covers 3 to 4 limbs of 32 KiB)"}
     sctx.close()
+    # HMult+relin latency at every level of the bench context (one call at a
+    # time): the key switch gets cheaper each time a digit is dropped
+    rlk = ctx.relin_key(dK[0])
+    by_level = {}
+    for lv in range(1, nl + 1):
+        la = dA[0].view(2, nl, N)[:, :lv].contiguous().view(-1)
+        lb = dB[0].view(2, nl, N)[:, :lv].contiguous().view(-1)
+        lo = torch.empty(2 * lv * N, dtype=torch.int64, device="cuda")
+        by_level[lv] = round(timed(lambda: ctx.hmult(la, lb, lv, rlk, lo, scale, scale), 10) * 1e3, 1)
+    res["hmult_us_by_level"] = by_level
+    # HMult+relin at the top level across ring degrees, with sets whose key
+    # sizes are those the paper quotes for its parameter-set comparison (2.3,
+    # 7.7, 20, 152 and 360 MB; the sets themselves are in a figure whose
+    # values the text does not give); logN=16 is the paper's Table III set
+    # [2^16, 29, 59, 4] (30 limbs of 59 bits, K = 8)
+    by_set = {}
+    for logN, L, dnum, qb in ((13, 6, 2, 54), (14, 7, 3, 54), (15, 14, 2, 54), (16, 30, 4, 59), (17, 36, 4, 54)):
+        K = -(-L // dnum)
+        pq = fides.find_primes(logN, qb, L)
+        pp = fides.find_primes(logN, 60, K, exclude=pq)
+        pctx = fides.Context(logN, pq, pp, dnum)
+        if not args.no_autotune:
+            pctx.autotune(2 * (L + K))
+        pN = pctx.N
+        st3 = si.Stream(si.workload_seed(1), 22 + logN)
+        pa = fides.to_device(np.stack([si.uniform_poly(st3, pq, pN) for _ in range(2)]))
+        pb = fides.to_device(np.stack([si.uniform_poly(st3, pq, pN) for _ in range(2)]))
+        kbuf = fides.to_device(np.stack([np.stack([si.uniform_poly(st3, pq + pp, pN) for _ in range(2)])
+                                         for _ in range(dnum)]))
+        pk = pctx.relin_key(kbuf)
+        po = torch.empty_like(pa)
+        t_set = timed(lambda: pctx.hmult(pa, pb, L, pk, po, scale, scale), 20)
+        by_set["logN%d_L%d_dnum%d" % (logN, L, dnum)] = {
+            "us": round(t_set * 1e3, 1), "K": K, "key_mib": round(kbuf.numel() * 8 / 2 ** 20, 1),
+            "ops_per_s": round(1e3 / t_set, 1)}
+        pk.close()
+        del pa, pb, po, kbuf
+        pctx.close()
+    res["hmult_by_parameter_set"] = by_set
     # forward + inverse NTT of 32 limbs at every ring degree (butterflies per second)
     by_degree = {}
     for logN in range(12, 18):
