@@ -987,6 +987,17 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
                            "gbutterfly_per_s": round(bfly / (t / 1e3) / 1e9, 1)}
         dctx.close()
     res["ntt_by_degree"] = by_degree
+    # forward + inverse NTT at logN=16 by limb count (working set 0.5 MiB per
+    # limb): time per limb as the launches grow
+    by_limbs = {}
+    for n_l in (1, 2, 4, 8, 16, 32, 64, 128):
+        per, bat = (n_l, 1) if n_l <= 16 else (16, n_l // 16)   # batches of 16 q-limbs
+        x = fides.to_device(np.stack([si.uniform_poly(st2, ctx.q[:per], N) for _ in range(bat)]))
+        t = timed(lambda: (ctx.ntt(x, 0, per, bat), ctx.intt(x, 0, per, bat)), 20)
+        by_limbs[n_l] = {"us_fwd_inv": round(t * 1e3, 1), "us_per_limb": round(t * 1e3 / n_l, 2),
+                         "working_set_mib": n_l * N * 8 / 2 ** 20}
+        del x
+    res["ntt_logN16_by_limbs"] = by_limbs
     res["elementwise_note"] = ("device time of the kernel (CUDA events around each launch), L2 flushed before each "
                                "launch; 30-limb operands; bytes = operands read + result written once")
     return res
