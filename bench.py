@@ -942,6 +942,17 @@ def run_ops(args, ctx, dA, dB, dK, P, scale):
         lo = torch.empty(2 * lv * N, dtype=torch.int64, device="cuda")
         by_level[lv] = round(timed(lambda: ctx.hmult(la, lb, lv, rlk, lo, scale, scale), 10) * 1e3, 1)
     res["hmult_us_by_level"] = by_level
+    # PtMult followed by Rescale at several levels (the paper's PtMult+Rescale
+    # figure, one call of each at a time)
+    pr_level = {}
+    for lv in (2, 5, 10, 15, 20, 25, 30):
+        la = dA[0].view(2, nl, N)[:, :lv].contiguous().view(-1)
+        lpt = fides.to_device(si.uniform_poly(st, ctx.q[:lv], N))
+        lm = torch.empty(2 * lv * N, dtype=torch.int64, device="cuda")
+        lr = torch.empty(2 * (lv - 1) * N, dtype=torch.int64, device="cuda")
+        pr_level[lv] = round(timed(lambda: (ctx.ptmult(la, lpt, lv, lm, scale), ctx.rescale(lm, lv, lr, scale)),
+                                   20) * 1e3, 1)
+    res["ptmult_rescale_us_by_level"] = pr_level
     # HMult+relin at the top level across ring degrees, with sets whose key
     # sizes are those the paper quotes for its parameter-set comparison (2.3,
     # 7.7, 20, 152 and 360 MB; the sets themselves are in a figure whose
