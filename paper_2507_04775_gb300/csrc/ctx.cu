@@ -405,7 +405,8 @@ extern "C" int fides_ctx_create(int logN, int L, int dnum, const uint64_t *prime
         P.r64p = shoup_of(P.r64, q);
         P.ninv = hinv((u64)N % q, q);
         P.ninvp = shoup_of(P.ninv, q);
-        P.ninvw = P.ninvwp = P.pad = 0;   // after the twiddles
+        P.ninvw = P.ninvwp = 0;   // after the twiddles
+        P.bmu = (u64)(((u128)1 << (63 + (64 - __builtin_clzll(q)))) / q);
         // powers in natural order, then scattered to bit-reversed positions
         u64 x = 1, y = 1;
         for (int k = 0; k < N; ++k) {

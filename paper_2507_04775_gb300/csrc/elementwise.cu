@@ -33,7 +33,7 @@ __device__ __forceinline__ u64 elem(u64 x, u64 y, int poly, const TwPair &k, con
     case E_HADD: return csub(x + y, p.q);
     case E_HSUB: return csub(x + p.q - y, p.q);
     case E_PTADD: return poly == 0 ? csub(x + y, p.q) : x;
-    case E_PTMULT: return mul_mod(x, y, p);
+    case E_PTMULT: return mul_mod_small(x, y, p);
     case E_SCALAR_ADD: return poly == 0 ? csub(x + k.w, p.q) : x;
     default: return csub(mul_shoup(x, k, p.q), p.q);   // E_SCALAR_MULT, E_MULI
     }

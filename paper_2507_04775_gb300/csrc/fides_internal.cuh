@@ -49,7 +49,7 @@ struct __align__(16) PrimeInfo {
     u64 ninvp;  // Shoup companion of ninv
     u64 ninvw;  // N^-1 w1 mod q, w1 the twiddle of the last inverse stage (psi^-N/2)
     u64 ninvwp; // Shoup companion of ninvw
-    u64 pad;
+    u64 bmu;    // floor(2^(63+k) / q), k the bit length of q (reduce_prod)
 };
 
 // One contiguous run of limbs processed by a kernel: limb k of the run reads
@@ -238,6 +238,27 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const PrimeInfo &p)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeInfo &p)
 {
     return reduce128(mulhi64(a, b), a * b, p);
+}
+
+// x mod q in [0, 3q) for x = hi * 2^64 + lo below 2^(k+63), k the bit length
+// of q: a product of two values below 2q, or the sum of two products of
+// canonical residues (primes below 2^61).  Barrett reduction whose quotient is
+// the high word of one 64 x 64 product: q1 = floor(x / 2^(k-1)) fits in 64
+// bits, and with bmu = floor(2^(63+k) / q) (below 2^64, since q > 2^(k-1))
+// mulhi(q1, bmu) falls short of floor(x / q) by at most 2 -- one from each
+// floor and one from truncating x.  Against reduce128 it drops the Shoup
+// product by 2^64 mod q and one of the two high products.
+__device__ __forceinline__ u64 reduce_prod(u64 hi, u64 lo, const PrimeInfo &p)
+{
+    const int s = 63 - __clzll((long long)p.q);   // k - 1, at least 1
+    const u64 q1 = (hi << (64 - s)) | (lo >> s);
+    return lo - mulhi64(q1, p.bmu) * p.q;
+}
+
+// a * b mod q, canonical, for a, b below 2q.
+__device__ __forceinline__ u64 mul_mod_small(u64 a, u64 b, const PrimeInfo &p)
+{
+    return csub(csub(reduce_prod(mulhi64(a, b), a * b, p), p.q2), p.q);
 }
 
 // 128-bit accumulator

@@ -87,6 +87,12 @@ __device__ __forceinline__ u64 reduce_acc(const Acc128 &c, const PrimeInfo &p)
     return reduce128(((u64)c.w3 << 32) | c.w2, ((u64)c.w1 << 32) | c.w0, p);
 }
 
+// the same for a sum of at most two products of canonical residues
+__device__ __forceinline__ u64 reduce_acc2(const Acc128 &c, const PrimeInfo &p)
+{
+    return csub(csub(reduce_prod(((u64)c.w3 << 32) | c.w2, ((u64)c.w1 << 32) | c.w0, p), p.q2), p.q);
+}
+
 template <int NS>
 __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *__restrict__ P, int logN, int tg)
 {
@@ -469,10 +475,12 @@ inline int launch_inner(const fides_ctx *c, const IPArgs &A, int total_limbs, in
 // ---------------------------------------------------------------------------
 // Tensor product of HMult (Table I) in evaluation form, as its own pass:
 // d0 = a0 b0 and d1 = a0 b1 + a1 b0 into out, d2 = a1 b1 into d2 (the
-// key-switch input), two words per thread with 16-byte accesses.  The pass is
-// bound by HBM (four words read, three written per coefficient); the INTT of
-// d2 that follows runs without a prologue.  One op inline, or a device table
-// of ops with exclusive prefix sums of their limb counts (grid.y = the total).
+// key-switch input), two words per thread with 16-byte accesses: four words
+// read and three written per coefficient, and three 128-bit reductions, which
+// take the Barrett form of reduce_prod (the operands are canonical residues);
+// with reduce128 the multiply pipe bounded the pass.  The INTT of d2 that
+// follows runs without a prologue.  One op inline, or a device table of ops
+// with exclusive prefix sums of their limb counts (grid.y = the total).
 // ---------------------------------------------------------------------------
 struct TensorOp {
     const u64 *a, *b;   // [2][nl][N]
@@ -500,9 +508,9 @@ __device__ __forceinline__ void tensor_body(const TensorOp &o, int limb, const P
     mac_wide(mx, a1.x, b0.x);
     mac_wide(my, a0.y, b1.y);
     mac_wide(my, a1.y, b0.y);
-    *reinterpret_cast<ulonglong2 *>(o.out + i) = make_ulonglong2(mul_mod(a0.x, b0.x, p), mul_mod(a0.y, b0.y, p));
-    *reinterpret_cast<ulonglong2 *>(o.out + S + i) = make_ulonglong2(reduce_acc(mx, p), reduce_acc(my, p));
-    *reinterpret_cast<ulonglong2 *>(o.d2 + i) = make_ulonglong2(mul_mod(a1.x, b1.x, p), mul_mod(a1.y, b1.y, p));
+    *reinterpret_cast<ulonglong2 *>(o.out + i) = make_ulonglong2(mul_mod_small(a0.x, b0.x, p), mul_mod_small(a0.y, b0.y, p));
+    *reinterpret_cast<ulonglong2 *>(o.out + S + i) = make_ulonglong2(reduce_acc2(mx, p), reduce_acc2(my, p));
+    *reinterpret_cast<ulonglong2 *>(o.d2 + i) = make_ulonglong2(mul_mod_small(a1.x, b1.x, p), mul_mod_small(a1.y, b1.y, p));
 }
 
 __global__ void __launch_bounds__(256) k_tensor(TensorArgs A, const PrimeInfo *__restrict__ P, int logN)

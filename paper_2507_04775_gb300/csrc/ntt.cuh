@@ -164,12 +164,12 @@ struct ProPrep {
         if (J.mode == 0) return v[0];
         const size_t S = (size_t)J.pstride;
         if (J.mode == 1) {
-            J.out[j] = mul_mod(v[0], v[2], p);
+            J.out[j] = mul_mod_small(v[0], v[2], p);
             U128 m = {0, 0};
             mac128(m, v[0], v[3]);
             mac128(m, v[1], v[2]);
-            J.out[S + j] = reduce128(m.hi, m.lo, p);
-            const u64 d2 = mul_mod(v[1], v[3], p);
+            J.out[S + j] = csub(csub(reduce_prod(m.hi, m.lo, p), p.q2), p.q);
+            const u64 d2 = mul_mod_small(v[1], v[3], p);
             J.side[j] = d2;
             return d2;
         }
