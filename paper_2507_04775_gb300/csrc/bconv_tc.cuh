@@ -273,8 +273,9 @@ struct TcPipe {
 
 // mbarriers of a CTA: source stage full / empty, A buffer full / empty,
 // accumulator full / empty, matrix image
+constexpr int TC_MAX_ACC = 4;   // accumulators in tensor memory (four of at most 128 columns)
 constexpr int TB_SF = 0, TB_SE = TC_MAX_DEPTH, TB_AF = 2 * TC_MAX_DEPTH, TB_AE = TB_AF + 2, TB_CF = TB_AE + 2,
-              TB_CE = TB_CF + 2, TB_IMG = TB_CE + 2, TB_COUNT = TB_IMG + 1;
+              TB_CE = TB_CF + TC_MAX_ACC, TB_IMG = TB_CE + TC_MAX_ACC, TB_COUNT = TB_IMG + 1;
 
 __device__ __forceinline__ void mbar_arrive(u32 bar)
 {
@@ -359,6 +360,8 @@ __device__ __forceinline__ void bconv_tc_body(const BConvJob &B, const PrimeInfo
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar(TB_AF + i), TC_PROD_WARPS);
             mbar_init(bar(TB_AE + i), 1);
+        }
+        for (int i = 0; i < pp.nbuf; ++i) {
             mbar_init(bar(TB_CF + i), 1);
             mbar_init(bar(TB_CE + i), 4 * TC_EPI_GROUPS);
         }
@@ -565,7 +568,7 @@ inline int launch_bconv_tc_t(const fides_ctx *c, const BConvArgs &G, int max_ns,
     TcPipe pp;
     pp.acc_cols = 32;
     while (pp.acc_cols < (u32)(8 * ndp)) pp.acc_cols <<= 1;
-    pp.nbuf = 2 * pp.acc_cols <= 512 ? 2 : 1;
+    pp.nbuf = std::min<int>(TC_MAX_ACC, 512 / pp.acc_cols);
     pp.ncols = pp.nbuf * pp.acc_cols;
     pp.limit_ns = limit_ns;
     pp.stall = stall;

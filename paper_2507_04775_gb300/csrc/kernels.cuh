@@ -93,6 +93,19 @@ __device__ __forceinline__ u64 reduce_acc2(const Acc128 &c, const PrimeInfo &p)
     return csub(csub(reduce_prod(((u64)c.w3 << 32) | c.w2, ((u64)c.w1 << 32) | c.w0, p), p.q2), p.q);
 }
 
+// The same for a sum of m products of canonical residues: the Barrett form
+// where its bound holds, m q^2 < 2^(k+63) for m at most 2^(63-k) (k the bit
+// length of q: m <= 4 at 61-bit primes, 8 at 60-bit), reduce128 otherwise.
+__device__ __forceinline__ bool reduce_prod_ok(int m, const PrimeInfo &p)
+{
+    return (u64)m <= (1ull << (__clzll((long long)p.q) - 1));   // 2^(63-k), k = 64 - clz(q)
+}
+__device__ __forceinline__ u64 reduce_accm(const Acc128 &c, const PrimeInfo &p, bool barrett)
+{
+    const u64 hi = ((u64)c.w3 << 32) | c.w2, lo = ((u64)c.w1 << 32) | c.w0;
+    return barrett ? csub(csub(reduce_prod(hi, lo, p), p.q2), p.q) : reduce128(hi, lo, p);
+}
+
 template <int NS>
 __device__ __forceinline__ void bconv_body(const BConvJob &B, const PrimeInfo *__restrict__ P, int logN, int tg)
 {
@@ -367,9 +380,11 @@ __device__ __forceinline__ void inner_body(const IPOp &op, int z, int L, int nfu
                 mac_wide(b1, e[j].y, k1[j].y);
             }
         }
-        *reinterpret_cast<ulonglong2 *>(acc + (size_t)z * N + n) = make_ulonglong2(reduce_acc(a0, pr), reduce_acc(b0, pr));
+        const bool bar = reduce_prod_ok(beta, pr);
+        *reinterpret_cast<ulonglong2 *>(acc + (size_t)z * N + n) =
+            make_ulonglong2(reduce_accm(a0, pr, bar), reduce_accm(b0, pr, bar));
         *reinterpret_cast<ulonglong2 *>(acc + ((size_t)ne + z) * N + n) =
-            make_ulonglong2(reduce_acc(a1, pr), reduce_acc(b1, pr));
+            make_ulonglong2(reduce_accm(a1, pr, bar), reduce_accm(b1, pr, bar));
         return;
     }
     // hoisted rotation: the digits are read through sigma_g (evaluation form:
@@ -428,9 +443,12 @@ __device__ __forceinline__ int find_op(const int *__restrict__ pre, int nop, int
 }
 
 // MAXB: the largest digit count of the ops in the launch (loads for digits
-// >= an op's own count are predicated off).
+// >= an op's own count are predicated off).  Up to three digits the kernel
+// keeps to 64 registers, so that four CTAs share an SM and keep their loads
+// in flight.
 template <int MAXB, bool V2>
-__global__ void __launch_bounds__(256) k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
+__global__ void __launch_bounds__(256, (MAXB <= 3 ? 4 : 1))
+    k_inner(IPArgs A, int L, int nfull, const PrimeInfo *__restrict__ P, int logN)
 {
     pdl_trigger();   // inner_body waits after issuing its key loads
     const int z = blockIdx.y;

@@ -81,16 +81,25 @@ void plan_ntt(Plan &P, LaunchKind kind, const std::vector<Seg> &segs, size_t N, 
 
 // One launch for the tensor-core jobs, one per distinct source count of the
 // others (the integer conversion kernel is templated on it).
+// Tensor-core jobs go to two launches by target count: with at most 16
+// targets an accumulator has at most 128 tensor-memory columns, and a launch
+// of such jobs keeps four of them per CTA instead of two (bconv_tc.cuh).
+inline int plan_bconv_key(const BConvJob &j)
+{
+    const int key = bconv_group_key(j);
+    return key < 0 && bconv_targets(j) > 16 ? -2 : key;
+}
+
 void plan_bconv(Plan &P, const std::vector<BConvJob> &jobs)
 {
     std::vector<bool> done(jobs.size(), false);
     for (size_t j = 0; j < jobs.size(); ++j) {
         if (done[j]) continue;
-        const int key = bconv_group_key(jobs[j]);
+        const int key = plan_bconv_key(jobs[j]);
         std::vector<BConvJob> g;
         int max_dst = 0, ns = 0;
         for (size_t k = j; k < jobs.size(); ++k) {
-            if (done[k] || bconv_group_key(jobs[k]) != key) continue;
+            if (done[k] || plan_bconv_key(jobs[k]) != key) continue;
             done[k] = true;
             g.push_back(jobs[k]);
             max_dst = std::max(max_dst, bconv_targets(jobs[k]));

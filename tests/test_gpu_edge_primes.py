@@ -2,11 +2,11 @@
 the bound its lazy ranges rely on (8q < 2^64 in the NTT butterflies; products
 of residues below 2q, or sums of two products of canonical residues, below
 2^(k+63) in the Barrett reduction of the tensor product and PtMult, k the bit
-length of q; 128-bit sums of up to eight digit products in the key inner
-product).  At logN=12 (one-pass NTT) and logN=14 (two passes), with residues
-drawn uniformly and with every residue at q - 1 (the largest products), the
-NTT round trip, HMult+relin, PtMult, Rescale and HRotate give the oracle's
-residues exactly.
+length of q; in the key inner product sums of up to 2^(63-k) digit products
+take it, more take the 128-bit reduction).  At logN=12 (one-pass NTT) and
+logN=14 (two passes), with residues drawn uniformly and with every residue at
+q - 1 (the largest products), the NTT round trip, HMult+relin, PtMult,
+Rescale and HRotate give the oracle's residues exactly.
 """
 import numpy as np
 import pytest
@@ -19,7 +19,9 @@ pytestmark = pytest.mark.gpu
 
 from paper_2507_04775_gb300 import Context, find_primes, to_device, to_host  # noqa: E402
 
-# (logN, q limbs, special primes, dnum); the third set has six digits
+# (logN, q limbs, special primes, dnum); at 61-bit primes the inner product of
+# the first two sets (two and three digits) takes the Barrett form, the six
+# digits of the third the 128-bit reduction
 SETS = [(12, 4, 2, 2), (14, 3, 1, 3), (12, 6, 1, 6)]
 
 
