@@ -6,7 +6,8 @@ length of q; in the key inner product sums of up to 2^(63-k) digit products
 take it, more take the 128-bit reduction).  At logN=12 (one-pass NTT) and
 logN=14 (two passes), with residues drawn uniformly and with every residue at
 q - 1 (the largest products), the NTT round trip, HMult+relin, PtMult,
-Rescale and HRotate give the oracle's residues exactly.
+Rescale and HRotate give the oracle's residues exactly.  HMult+relin and
+PtMult are also checked at prime sizes from 20 to 49 bits.
 """
 import numpy as np
 import pytest
@@ -101,3 +102,34 @@ def test_hmult_ptmult_rescale_rotate(pair, extreme):
         torch.cuda.synchronize()
         assert np.array_equal(to_host(rot).reshape(shape), o.rotate(a, step, key)), "step %d" % step
     assert g.status() == 0
+
+
+# the Barrett reduction shifts by k - 1 and its constant depends on k: one
+# context per prime size, q and p primes of the same bit length, so that the
+# tensor product, PtMult and the inner product see every shift; 48 and 49
+# bits straddle the tensor-core conversion's two epilogues
+@pytest.mark.parametrize("bits", [20, 31, 32, 33, 47, 48, 49])
+def test_prime_sizes(bits):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    logN, nq, nk, dnum = 12, 4, 2, 2
+    q = find_primes(logN, bits, nq)
+    p = find_primes(logN, bits, nk, exclude=q)
+    g, o = Context(logN, q, p, dnum), oracle.Context(logN, q, p, dnum)
+    try:
+        for extreme in (False, True):
+            st = si.Stream(1103, bits)
+            a, b, key, pt = _inputs(o, st, extreme, nq)
+            da = to_device(a)
+            shape = (2, nq, o.N)
+            out = torch.zeros(2 * nq * o.N, dtype=torch.int64, device="cuda")
+            g.hmult(da, to_device(b), nq, g.relin_key(to_device(key)), out, 1.0, 1.0)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(out).reshape(shape), o.hmult(a, b, key)), "hmult, %d bits" % bits
+            pm = torch.zeros(2 * nq * o.N, dtype=torch.int64, device="cuda")
+            g.ptmult(da, to_device(pt), nq, pm)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(pm).reshape(shape), o.ptmult(a, pt)), "ptmult, %d bits" % bits
+        assert g.status() == 0
+    finally:
+        g.close()
